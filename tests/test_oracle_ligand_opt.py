@@ -1,0 +1,359 @@
+"""Pins of the oracle's ligand model, kinematics, gradient, optimisers and Philox (CPU)."""
+import math
+import os
+import subprocess
+import sys
+
+import networkx as nx
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle
+from paper_2303_09916_gb300 import synth
+
+
+def _lig(n=12, t=3, seed=1):
+    s = synth.ligand(n, t, seed)
+    return s, oracle.Ligand(s.xyz.astype(np.float64), s.xs_type, s.bonds, s.rotatable)
+
+
+def _random_conf(lig, rng, center=(0, 0, 0), spread=1.0):
+    c = np.zeros(lig.nx)
+    c[:3] = np.asarray(center) + rng.uniform(-spread, spread, 3)
+    q = rng.normal(size=4)
+    c[3:7] = q / np.linalg.norm(q)
+    c[7:] = rng.uniform(-math.pi, math.pi, lig.T)
+    return c
+
+
+def test_identity_conformation_reproduces_reference():
+    for seed in range(5):
+        s, lig = _lig(15, 4, seed)
+        assert np.allclose(lig.coords(lig.identity_conf()), s.xyz, atol=1e-12)
+
+
+def test_bodies_and_pairs_follow_the_graph_rules():
+    for seed in range(4):
+        s, lig = _lig(14, 4, seed)
+        G = nx.Graph()
+        G.add_nodes_from(range(s.n_atoms))
+        G.add_edges_from(map(tuple, s.bonds))
+        rigid = nx.Graph()
+        rigid.add_nodes_from(range(s.n_atoms))
+        rigid.add_edges_from(tuple(b) for b, r in zip(s.bonds, s.rotatable) if not r)
+        comps = list(nx.connected_components(rigid))
+        body_of, parent, tb = lig.bodies()
+        assert lig.n_bodies == len(comps) and lig.T == int(s.rotatable.sum())
+        for comp in comps:
+            assert len({body_of[a] for a in comp}) == 1
+        sizes = [len(c) for c in comps]
+        root_comp = [c for c in comps if body_of[next(iter(c))] == lig.root_body][0]
+        assert len(root_comp) == max(sizes)
+        spl = dict(nx.all_pairs_shortest_path_length(G))
+        expected = {(i, j) for i in range(s.n_atoms) for j in range(i + 1, s.n_atoms)
+                    if body_of[i] != body_of[j] and spl[i].get(j, 99) > 3}
+        got = {tuple(p) for p in lig.pairs()}
+        assert got == expected
+
+
+def test_rigid_ligand_rotation_matches_scipy():
+    s, lig = _lig(10, 0, 3)
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        c = _random_conf(lig, rng)
+        w, x, y, z = c[3:7]
+        R = Rotation.from_quat([x, y, z, w]).as_matrix()
+        x0 = s.xyz[lig.root_atom].astype(np.float64)
+        expected = (s.xyz - x0) @ R.T + c[:3]
+        assert np.allclose(lig.coords(c), expected, atol=1e-12)
+
+
+def _dihedral(a, b, c, d):
+    b0, b1, b2 = a - b, c - b, d - c
+    b1n = b1 / np.linalg.norm(b1)
+    v = b0 - b0.dot(b1n) * b1n
+    w = b2 - b2.dot(b1n) * b1n
+    return math.atan2(np.cross(b1n, v).dot(w), v.dot(w))
+
+
+def test_torsion_changes_the_dihedral_by_theta():
+    s, lig = _lig(12, 3, 5)
+    body_of, parent, tb = lig.bodies()
+    G = nx.Graph()
+    G.add_edges_from(map(tuple, s.bonds))
+    rot_bonds = [tuple(b) for b, r in zip(s.bonds, s.rotatable) if r]
+    c0 = lig.identity_conf()
+    x0 = lig.coords(c0)
+    for k, (i, j) in enumerate(rot_bonds):
+        # orient the bond parent-side -> child-side
+        child = tb[k]
+        a_par, a_ch = (i, j) if body_of[j] == child else (j, i)
+        n_par = [n for n in G[a_par] if n != a_ch][0]
+        n_ch = [n for n in G[a_ch] if n != a_par][0]
+        theta = 0.7
+        c = c0.copy()
+        c[7 + k] = theta
+        x1 = lig.coords(c)
+        d0 = _dihedral(x0[n_par], x0[a_par], x0[a_ch], x0[n_ch])
+        d1 = _dihedral(x1[n_par], x1[a_par], x1[a_ch], x1[n_ch])
+        diff = (d1 - d0 + math.pi) % (2 * math.pi) - math.pi
+        assert diff == pytest.approx(theta, abs=1e-10)
+        c[7 + k] = 2 * math.pi
+        assert np.allclose(lig.coords(c), x0, atol=1e-10)
+
+
+def test_internal_geometry_invariant_under_any_conformation():
+    s, lig = _lig(16, 5, 7)
+    body_of, _, _ = lig.bodies()
+    rng = np.random.default_rng(1)
+    x0 = s.xyz.astype(np.float64)
+    for _ in range(5):
+        x = lig.coords(_random_conf(lig, rng, spread=5))
+        for i, j in s.bonds:
+            assert np.linalg.norm(x[i] - x[j]) == pytest.approx(np.linalg.norm(x0[i] - x0[j]), abs=1e-10)
+        for i in range(s.n_atoms):
+            for j in range(i + 1, s.n_atoms):
+                if body_of[i] == body_of[j]:
+                    assert np.linalg.norm(x[i] - x[j]) == pytest.approx(np.linalg.norm(x0[i] - x0[j]), abs=1e-10)
+
+
+def _tiny_complex(seed=0, n_lig=7, T=2, n_rec=45):
+    s = synth.ligand(n_lig, T, seed)
+    lig = oracle.Ligand(s.xyz.astype(np.float64), s.xs_type, s.bonds, s.rotatable)
+    rng = np.random.default_rng(seed + 100)
+    # receptor atoms on a shell 3.5-7 A around the ligand, so every term is active
+    d = rng.normal(size=(n_rec, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rec_xyz = d * rng.uniform(3.5, 7.0, size=(n_rec, 1))
+    rec_t = rng.integers(0, 9, size=n_rec)
+    return s, lig, rec_xyz, rec_t
+
+
+def _fd_grad(fn, lig, c, h=1e-6):
+    g = np.zeros(lig.nd)
+    for a in range(lig.nd):
+        s = np.zeros(lig.nd)
+        s[a] = h
+        cp = lig.apply_step(c, s)
+        s[a] = -h
+        cm = lig.apply_step(c, s)
+        g[a] = (fn(cp) - fn(cm)) / (2 * h)
+    return g
+
+
+def _near_kink(lig, rec_xyz, rec_t, s, c, margin=2e-3):
+    R = [1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0, 1.8]
+    x = lig.coords(c)
+    pts = [(x[i], s.xs_type[i], rec_xyz[j], rec_t[j]) for i in range(len(x)) for j in range(len(rec_t))]
+    pts += [(x[i], s.xs_type[i], x[j], s.xs_type[j]) for i, j in lig.pairs()]
+    for a, ta, b, tb in pts:
+        r = np.linalg.norm(a - b)
+        kinks = [R[ta] + R[tb] + k for k in (-0.7, 0.0, 0.5, 1.5)] + [8.0]
+        if min(abs(r - k) for k in kinks) < margin:
+            return True
+    return False
+
+
+def test_exact_gradient_matches_central_difference():
+    checked = 0
+    for seed in range(6):
+        s, lig, rec_xyz, rec_t = _tiny_complex(seed)
+        rng = np.random.default_rng(seed)
+        for _ in range(4):
+            c = _random_conf(lig, rng, spread=0.5)
+            if _near_kink(lig, rec_xyz, rec_t, s, c):
+                continue
+            _, g = lig.score_exact(rec_xyz, rec_t, c)
+            fd = _fd_grad(lambda cc: lig.score_exact(rec_xyz, rec_t, cc)[0].sum(), lig, c)
+            assert np.allclose(g, fd, rtol=1e-5, atol=1e-6), (g, fd)
+            checked += 1
+    assert checked >= 12
+
+
+def test_grid_eq3_gradient_matches_central_difference():
+    checked = 0
+    for seed in range(4):
+        s, lig, rec_xyz, rec_t = _tiny_complex(seed)
+        grid = oracle.grid_build(rec_xyz, rec_t, np.zeros(3), np.array([9.0, 9.0, 9.0]), 0.5)
+        rng = np.random.default_rng(seed + 7)
+        for _ in range(4):
+            c = _random_conf(lig, rng, spread=0.5)
+            x = lig.coords(c)
+            frac = ((x - grid.origin) / grid.h) % 1.0
+            if np.any(np.minimum(frac, 1 - frac) < 1e-3) or _near_kink(lig, x, s.xs_type, s, c):
+                continue
+            _, g = lig.score_grid(grid, 1, c)
+            fd = _fd_grad(lambda cc: lig.score_grid(grid, 1, cc)[0].sum(), lig, c)
+            assert np.allclose(g, fd, rtol=1e-5, atol=1e-6), (g, fd)
+            checked += 1
+    assert checked >= 6
+
+
+def test_exact_score_invariant_under_rigid_motion_of_the_complex():
+    s, lig, rec_xyz, rec_t = _tiny_complex(3, n_lig=9, T=3)
+    rng = np.random.default_rng(4)
+    c = _random_conf(lig, rng, spread=0.5)
+    t0, _ = lig.score_exact(rec_xyz, rec_t, c)
+    R = Rotation.from_rotvec([0.3, -1.1, 0.7]).as_matrix()
+    shift = np.array([4.0, -2.5, 11.0])
+    # moving the receptor and the ligand's pose together: rotate the root about the origin
+    c2 = c.copy()
+    c2[:3] = R @ c[:3] + shift
+    qr = Rotation.from_matrix(R).as_quat()  # x, y, z, w
+    qw = np.array([qr[3], qr[0], qr[1], qr[2]])
+    w1, x1, y1, z1 = qw
+    w2, x2, y2, z2 = c[3:7]
+    c2[3:7] = [w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+               w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2]
+    assert np.allclose(lig.coords(c2), lig.coords(c) @ R.T + shift, atol=1e-10)
+    t1, _ = lig.score_exact(rec_xyz @ R.T + shift, rec_t, c2)
+    assert np.allclose(t0, t1, rtol=1e-12, atol=1e-12)
+
+
+def test_exact_score_is_a_brute_force_pair_sum():
+    s, lig, rec_xyz, rec_t = _tiny_complex(2, n_lig=6, T=1, n_rec=20)
+    c = _random_conf(lig, np.random.default_rng(1), spread=0.3)
+    x = lig.coords(c)
+    inter = sum(oracle.pair(int(s.xs_type[i]), int(rec_t[j]), float(np.linalg.norm(x[i] - rec_xyz[j])))[0]
+                for i in range(len(x)) for j in range(len(rec_t)))
+    intra = sum(oracle.pair(int(s.xs_type[i]), int(s.xs_type[j]), float(np.linalg.norm(x[i] - x[j])))[0]
+                for i, j in lig.pairs())
+    t, _ = lig.score_exact(rec_xyz, rec_t, c)
+    assert t[0] == pytest.approx(inter, rel=1e-12) and t[1] == pytest.approx(intra, rel=1e-12, abs=1e-15)
+
+
+# ---------------------------------------------------------------- optimisers
+
+def test_bfgs_quadratic_reaches_the_solution():
+    rng = np.random.default_rng(0)
+    for n in (3, 8, 21):
+        M = rng.normal(size=(n, n))
+        A = M @ M.T + n * np.eye(n)
+        b = rng.normal(size=n)
+        x, e, evals, iters = oracle.opt_test(0, 0, np.zeros(n), A, b, opt=dict(max_iters=200, min_curvature=0.0))
+        assert np.allclose(x, np.linalg.solve(A, b), atol=1e-8)
+
+
+def test_bfgs_update_satisfies_the_secant_equation():
+    rng = np.random.default_rng(1)
+    n = 9
+    M = rng.normal(size=(n, n))
+    H = M @ M.T + np.eye(n)
+    s = rng.normal(size=n)
+    y = s + 0.3 * rng.normal(size=n)
+    assert s @ y > 0
+    H1 = oracle.bfgs_update(H, s, y)
+    assert np.allclose(H1 @ y, s, atol=1e-10)
+    assert np.allclose(H1, H1.T, atol=1e-12)
+    assert np.linalg.eigvalsh(H1).min() > 0
+
+
+def test_bfgs_rosenbrock():
+    x, e, evals, iters = oracle.opt_test(1, 0, np.array([-1.2, 1.0, -0.5, 0.8]),
+                                         opt=dict(max_iters=2000, max_trials=40, min_curvature=0.0))
+    assert np.allclose(x, np.ones(4), atol=1e-6)
+
+
+def test_bb_single_eigenvalue_quadratic_converges_in_two_steps():
+    lam = 2.5
+    n = 5
+    A = lam * np.eye(n)
+    x0 = np.array([1.0, -2.0, 0.5, 3.0, -1.0])
+    x, e, evals, iters = oracle.opt_test(0, 1, x0, A, np.zeros(n),
+                                         opt=dict(max_iters=2, bb_alpha0=0.1, bb_alpha_min=0.0, bb_alpha_max=1e9))
+    # first step x1 = (1 - 0.1 lam) x0; the BB1 step is then exactly 1/lam, so x2 = 0
+    assert np.allclose(x, 0.0, atol=1e-14)
+    assert evals == 3
+
+
+def test_bb_diagonal_quadratic_converges():
+    d = np.array([1.0, 2.0, 5.0, 10.0])
+    x, e, evals, iters = oracle.opt_test(0, 1, np.ones(4), np.diag(d), np.zeros(4),
+                                         opt=dict(max_iters=200, bb_alpha0=0.05, bb_alpha_min=0.0, bb_alpha_max=1e9))
+    assert np.abs(x).max() < 1e-8
+
+
+def test_docking_local_opt_lowers_the_energy():
+    s, lig, rec_xyz, rec_t = _tiny_complex(1, n_lig=9, T=3, n_rec=120)
+    grid = oracle.grid_build(rec_xyz, rec_t, np.zeros(3), np.array([12.0, 12.0, 12.0]), 0.5)
+    rng = np.random.default_rng(2)
+    for opt in (0, 1):
+        for _ in range(3):
+            c0 = _random_conf(lig, rng, spread=1.0)
+            e0 = lig.score_grid(grid, 0, c0)[0].sum()
+            c, e, evals, iters = lig.local_opt(grid, 0, opt, c0, opt=dict(max_iters=50))
+            assert e <= e0
+            assert e == pytest.approx(lig.score_grid(grid, 0, c)[0].sum(), rel=1e-12)
+            assert np.linalg.norm(c[3:7]) == pytest.approx(1.0, abs=1e-12)
+            assert np.all(np.abs(c[7:]) <= math.pi + 1e-12)
+
+
+# ---------------------------------------------------------------- Philox
+
+_TRITON_PHILOX = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def k(ctr_ptr, seed_lo, seed_hi, out_ptr, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(ctr_ptr + 4 * i + 0).to(tl.uint32, bitcast=True)
+    c1 = tl.load(ctr_ptr + 4 * i + 1).to(tl.uint32, bitcast=True)
+    c2 = tl.load(ctr_ptr + 4 * i + 2).to(tl.uint32, bitcast=True)
+    c3 = tl.load(ctr_ptr + 4 * i + 3).to(tl.uint32, bitcast=True)
+    seed = (seed_hi.to(tl.uint64) << 32) | seed_lo.to(tl.uint64)
+    a, b, c, d = tl.random.philox(seed, c0, c1, c2, c3)
+    tl.store(out_ptr + 4 * i + 0, a.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + 4 * i + 1, b.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + 4 * i + 2, c.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + 4 * i + 3, d.to(tl.int32, bitcast=True))
+
+data = json.loads(sys.stdin.read())
+res = []
+for key, ctrs in data:
+    ctr = torch.tensor(np.array(ctrs, dtype=np.uint32).view(np.int32).reshape(-1))
+    out = torch.zeros_like(ctr)
+    k[(1,)](ctr, key[0], key[1], out, N=len(ctrs))
+    res.append(out.numpy().view(np.uint32).reshape(-1, 4).tolist())
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_a_library_implementation():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(11)
+    cases = []
+    for _ in range(4):
+        key = [int(x) for x in rng.integers(0, 2 ** 31, size=2)]
+        ctrs = rng.integers(0, 2 ** 32, size=(8, 4), dtype=np.uint64).tolist()
+        cases.append((key, ctrs))
+    cases.append(([0, 0], [[0, 0, 0, 0]] * 8))
+    cases.append(([0xFFFFFFF, 0x7FFFFFFF], [[0xFFFFFFFF] * 4] * 8))
+    import json
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", _TRITON_PHILOX], input=json.dumps(cases), capture_output=True,
+                         text=True, env=env, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    ref = json.loads(out.stdout.strip().splitlines()[-1])
+    for (key, ctrs), r in zip(cases, ref):
+        for ctr, expected in zip(ctrs, r):
+            assert oracle.philox(ctr, key).tolist() == expected
+
+
+def test_philox_uniforms_are_uniform():
+    vals = np.array([oracle.philox([i, 7, 0, 0], [1, 2]) for i in range(4000)]).reshape(-1)
+    u = (vals >> 8) / 2.0 ** 24
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.005
+    hist = np.histogram(u, bins=16, range=(0, 1))[0]
+    chi2 = ((hist - len(u) / 16) ** 2 / (len(u) / 16)).sum()
+    assert chi2 < 45  # 15 dof, p ~ 1e-4
+
+
+def test_unit_ball_points():
+    pts = np.array([oracle.unit_ball(3, c, s) for c in range(50) for s in range(1, 21)])
+    r2 = (pts ** 2).sum(1)
+    assert r2.max() <= 1.0
+    assert abs(r2.mean() - 3 / 5) < 0.03  # E|b|^2 = 3/5 for the uniform ball
+    assert np.abs(pts.mean(0)).max() < 0.06
