@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Throughput of the docking hot path on GB300 (one JSON line on rank 0).
+
+Workload "typical-4k": each docked system is a 4,000-atom synthetic receptor
+with a 30 A box at 0.375 A (80^3 x 8 FP32 score+gradient maps) and a 30-atom
+ligand with 8 torsions, docked by 384 Monte Carlo chains x 40 steps of BFGS
+(100 iterations) and rescored in FP64 (top 9).  One step = `--batch` such
+systems, each with its own receptor, end to end: grid build, chains, FP64
+rescoring and top-k.
+
+  value  systems/s with inputs resident on the device (device-pointer API,
+         caller-owned memory), timed with CUDA events over exactly K steps
+  e2e    systems/s through the host API (dsdp_grid_build / dsdp_dock_submit /
+         dsdp_dock_poll) with host arrays, copies included
+  --impl reference   the FP64 CPU oracle on the host cores (whole systems)
+
+N > 1 (torchrun): independent replicas, one per GPU; value sums all ranks'
+systems over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_REC, BOX, SPACING, N_LIG, T_LIG = 4000, 30.0, 0.375, 30, 8
+N_CHAINS, N_STEPS, N_ITERS, TOP_K = 384, 40, 100, 9
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=16, help="systems per step")
+    p.add_argument("--optimizer", default="bfgs", choices=["bfgs", "bb"])
+    p.add_argument("--map-dtype", default="f32", choices=["f32", "bf16", "f16"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def systems(rank, batch):
+    from paper_2303_09916_gb300 import synth
+
+    out = []
+    for b in range(batch):
+        seed = 1000 * rank + b
+        rec = synth.receptor(N_REC, seed)
+        lig = synth.ligand(N_LIG, T_LIG, seed, center=rec.pocket_center)
+        out.append((seed, rec, lig))
+    return out
+
+
+def flops_per_eval(n_atoms, n_pairs, n_bodies):
+    # algorithmic work of one score+gradient evaluation: trilinear gather and
+    # weights 45 FMA per atom, kinematics + back-propagation 30 flop per atom and
+    # 40 per body, 40 flop per intra pair
+    return n_atoms * (2 * 45 + 30) + n_pairs * 40 + n_bodies * 40
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power))}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------- device-resident path
+def run_device(args, rank, world, dev, dist):
+    import torch
+    from paper_2303_09916_gb300 import dsdp
+
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
+    opt = dsdp.DSDP_OPT_BFGS if args.optimizer == "bfgs" else dsdp.DSDP_OPT_BB
+    sysl = systems(rank, args.batch)
+    keep = []
+    jobs = []
+    boxes = []
+    lig_info = []
+    for seed, rec, lig in sysl:
+        box = dsdp.make_box(rec.pocket_center, BOX, SPACING)
+        boxes.append(box)
+        nbytes = dsdp.dsdp_grid_map_bytes(box, dtype, dsdp.DSDP_GRID_EQ4)
+        d_maps = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        d_xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
+        d_type = torch.from_numpy(rec.xs_type.copy()).to(dev)
+        blob = dsdp.dsdp_ligand_pack(lig)
+        info = dsdp.dsdp_ligand_blob_info(blob)
+        lig_info.append(info)
+        d_blob = torch.from_numpy(blob.copy()).to(dev)
+        nx = 7 + info["n_torsions"]
+        outs = dict(conf=torch.empty((N_CHAINS, nx), dtype=torch.float32, device=dev),
+                    e=torch.empty(N_CHAINS, dtype=torch.float32, device=dev),
+                    evals=torch.zeros(N_CHAINS, dtype=torch.int32, device=dev),
+                    n=torch.zeros(1, dtype=torch.int32, device=dev),
+                    chain=torch.zeros(TOP_K, dtype=torch.int32, device=dev),
+                    score=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                    inter=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                    intra=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                    oconf=torch.zeros((TOP_K, nx), dtype=torch.float64, device=dev),
+                    coords=torch.zeros((TOP_K, N_LIG, 3), dtype=torch.float32, device=dev))
+        n = [int(np.ceil(BOX / SPACING))] * 3
+        origin = [rec.pocket_center[a] - (n[a] - 1) * SPACING / 2 for a in range(3)]
+        j = dsdp.dsdp_job_device()
+        j.grid = dsdp.grid_view(d_maps.data_ptr(), n, origin, SPACING, dtype, dsdp.DSDP_GRID_EQ4)
+        j.receptor = dsdp.dsdp_receptor(N_REC, d_xyz.data_ptr(), d_type.data_ptr())
+        j.h_blob = blob.ctypes.data
+        j.d_blob = d_blob.data_ptr()
+        j.params = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=N_STEPS, n_opt_iters=N_ITERS, optimizer=opt,
+                                    seed=seed, top_k=TOP_K)
+        for a in range(3):
+            j.box_lo[a] = rec.pocket_center[a] - BOX / 2
+            j.box_size[a] = BOX
+        j.d_chain_best_conf = outs["conf"].data_ptr()
+        j.d_chain_best_e = outs["e"].data_ptr()
+        j.d_chain_evals = outs["evals"].data_ptr()
+        j.d_out_n = outs["n"].data_ptr()
+        j.d_out_chain = outs["chain"].data_ptr()
+        j.d_out_score = outs["score"].data_ptr()
+        j.d_out_inter = outs["inter"].data_ptr()
+        j.d_out_intra = outs["intra"].data_ptr()
+        j.d_out_conf = outs["oconf"].data_ptr()
+        j.d_out_coords = outs["coords"].data_ptr()
+        jobs.append(j)
+        keep.append((d_maps, d_xyz, d_type, blob, d_blob, outs))
+    plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
+    n_plan_kernels = dsdp.dsdp_plan_kernel_count(plan)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        for (d_maps, d_xyz, d_type, *_), box in zip(keep, boxes):
+            dsdp.dsdp_grid_build_device(N_REC, d_xyz.data_ptr(), d_type.data_ptr(), box, dtype, dsdp.DSDP_GRID_EQ4,
+                                        d_maps.data_ptr(), d_maps.numel(), sptr)
+        if evs:
+            evs[1].record(stream)
+        dsdp.dsdp_plan_launch_stage(plan, dsdp.DSDP_STAGE_CHAINS, sptr)
+        if evs:
+            evs[2].record(stream)
+        dsdp.dsdp_plan_launch_stage(plan, dsdp.DSDP_STAGE_RESCORE, sptr)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if dist:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    grid_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    chain_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    rescore_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
+    evals = [int(o["evals"].sum().item()) for *_, o in keep]
+    total_evals = sum(evals)
+    flops = sum(ev * flops_per_eval(li["n_atoms"], li["n_pairs"], li["n_bodies"]) for ev, li in zip(evals, lig_info))
+    gather_bytes = sum(ev * li["n_atoms"] * (128 if dtype == 0 else 64) for ev, li in zip(evals, lig_info))
+    results_ok = all(int(o["n"].item()) >= 1 and bool(torch.isfinite(o["score"][: int(o["n"].item())]).all())
+                     for *_, o in keep)
+    # gather microbenchmark on the first system's maps (the L2-gather roofline)
+    g_view = jobs[0].grid
+    npts = 1 << 20
+    rng = np.random.default_rng(0)
+    pts = (np.array(g_view.origin) + rng.uniform(0, (np.array(g_view.n) - 1) * SPACING, size=(npts, 3))).astype(
+        np.float32)
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_ty = torch.from_numpy(rng.integers(0, 8, npts).astype(np.uint8)).to(dev)
+    d_out = torch.empty(npts, dtype=torch.float32, device=dev)
+    reps = 16
+    for _ in range(3):
+        dsdp.dsdp_gather_bench_device(g_view, d_pts.data_ptr(), d_ty.data_ptr(), npts, reps, d_out.data_ptr(), sptr)
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ga.record(stream)
+    for _ in range(5):
+        dsdp.dsdp_gather_bench_device(g_view, d_pts.data_ptr(), d_ty.data_ptr(), npts, reps, d_out.data_ptr(), sptr)
+    gb.record(stream)
+    torch.cuda.synchronize()
+    gather_gbs = 5 * npts * reps * (128 if dtype == 0 else 64) / (ga.elapsed_time(gb) * 1e-3) / 1e9
+    dsdp.dsdp_plan_destroy(None, plan)
+    return dict(elapsed_ms=elapsed_ms, grid_ms=grid_ms, chain_ms=chain_ms, rescore_ms=rescore_ms,
+                total_evals=total_evals, flops=flops, gather_bytes=gather_bytes, clocks=clk,
+                launches_per_step=args.batch + n_plan_kernels, results_ok=results_ok, gather_gbs=gather_gbs)
+
+
+# ---------------------------------------------------------------- host API (end to end)
+def run_e2e(args, rank, dev):
+    import torch
+    from paper_2303_09916_gb300 import dsdp
+
+    dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
+    opt = dsdp.DSDP_OPT_BFGS if args.optimizer == "bfgs" else dsdp.DSDP_OPT_BB
+    sysl = systems(rank, args.batch)
+    ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, args.batch))
+    h2d = d2h = 0
+    latencies = []
+    try:
+        def one_step(count):
+            nonlocal h2d, d2h
+            t_sub = {}
+            grids, jids, bufs = [], [], []
+            for seed, rec, lig in sysl:
+                box = dsdp.make_box(rec.pocket_center, BOX, SPACING)
+                t_sub[seed] = time.perf_counter()
+                g = dsdp.dsdp_grid_build(ctx, rec.xyz, rec.xs_type, box, dtype, dsdp.DSDP_GRID_EQ4)
+                params = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=N_STEPS, n_opt_iters=N_ITERS, optimizer=opt,
+                                          seed=seed, top_k=TOP_K)
+                jids.append(dsdp.dsdp_dock_submit(ctx, g, lig, params))
+                grids.append(g)
+                bufs.append(dsdp.result_buffers(lig.n_atoms, lig.n_torsions, params))
+                if count:
+                    h2d += rec.xyz.nbytes + rec.xs_type.nbytes + len(dsdp.dsdp_ligand_pack(lig))
+            for (seed, *_), j, b in zip(sysl, jids, bufs):
+                r = dsdp.dsdp_dock_poll(ctx, j, b, wait_ms=-1)
+                if count:
+                    latencies.append(time.perf_counter() - t_sub[seed])
+                    d2h += sum(v.nbytes for k, v in b.items()) + 8
+                assert r["n_out"] >= 1
+            for g in grids:
+                dsdp.dsdp_grid_free(ctx, g)
+
+        one_step(False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            one_step(True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+    finally:
+        dsdp.dsdp_destroy(ctx)
+    return dict(value=args.e2e_steps * args.batch / dt, h2d=h2d // args.e2e_steps, d2h=d2h // args.e2e_steps,
+                p50_ms=1e3 * float(np.percentile(latencies, 50)), p99_ms=1e3 * float(np.percentile(latencies, 99)))
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_system(seed, rec, lig, n_threads, optimizer):
+    """One whole system on the FP64 oracle: full grid maps, all chains, rescoring."""
+    import oracle
+
+    ol = oracle.Ligand(lig.xyz.astype(np.float64), lig.xs_type, lig.bonds, lig.rotatable)
+    size = np.array([BOX] * 3)
+    t = time.perf_counter()
+    g = oracle.grid_build(rec.xyz.astype(np.float64), rec.xs_type, rec.pocket_center, size, SPACING,
+                          n_threads=n_threads)
+    t_grid = time.perf_counter() - t
+    dp = oracle.dock_params_array(N_STEPS, 0 if optimizer == "bfgs" else 1, 1.2, rec.pocket_center - BOX / 2, size)
+    t = time.perf_counter()
+    best, e_best, evals = oracle.dock(ol, g, 0, dp, seed, N_CHAINS, n_threads=n_threads,
+                                      opt=dict(max_iters=N_ITERS))
+    oracle.rescore_topk(ol, rec.xyz.astype(np.float64), rec.xs_type, best, TOP_K)
+    t_dock = time.perf_counter() - t
+    return t_grid, t_dock, float(evals.sum())
+
+
+def cpu_baseline(args):
+    cores = os.cpu_count() or 1
+    (seed, rec, lig), = systems(0, 1)
+    t_grid, t_dock, evals = oracle_system(seed, rec, lig, cores, args.optimizer)
+    return {"value": 1.0 / (t_grid + t_dock), "unit": "systems/s", "cores": cores, "kind": "oracle",
+            "sample": f"one whole typical-4k system (80^3 x 8 FP64 maps, {N_CHAINS} chains x {N_STEPS} steps, "
+                      f"rescoring), threads over vertices and chains",
+            "grid_s": t_grid, "dock_s": t_dock, "evals_per_s": evals / t_dock}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    sysl = systems(0, 1)
+    seed, rec, lig = sysl[0]
+    for _ in range(args.warmup):
+        oracle_system(seed, rec, lig, cores, args.optimizer)
+    times, evals_s = [], []
+    for _ in range(args.steps):
+        tg, td, ev = oracle_system(seed, rec, lig, cores, args.optimizer)
+        times.append(tg + td)
+        evals_s.append(ev / td)
+    v = len(times) / sum(times)
+    line = {"metric": "docked systems/s (typical-4k: 4k-atom receptor, 80^3 maps, 30-atom ligand, 384x40 MC+BFGS)",
+            "value": v, "unit": "systems/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "typical-4k", "systems_per_step": 1, "runs_on": "host cores"},
+            "cpu_baseline": {"value": v, "unit": "systems/s", "cores": cores, "kind": "oracle",
+                             "sample": "one whole typical-4k system per step"},
+            "evals_per_s": float(np.mean(evals_s)),
+            "e2e": {"value": v, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    import torch
+
+    if world > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    r = run_device(args, rank, world, local, dist)
+    e2e = run_e2e(args, rank, local) if args.e2e_steps > 0 else None
+    if dist:
+        t = torch.tensor([e2e["value"] if e2e else 0.0], dtype=torch.float64, device=local)
+        dist.all_reduce(t)
+        if e2e:
+            e2e["value"] = float(t.item())
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, peaks_src = measured_peaks()
+    value = world * args.batch * args.steps / (r["elapsed_ms"] * 1e-3)
+    per_launch_s = r["chain_ms"] * 1e-3
+    achieved_tflops = r["flops"] / per_launch_s / 1e12
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = fp32_peak_tflops(sm_mhz)
+    line = {
+        "metric": "docked systems/s (typical-4k: 4k-atom receptor, 80^3 maps, 30-atom ligand, 384x40 MC+BFGS)",
+        "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["elapsed_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "typical-4k", "systems_per_step": args.batch, "receptor_atoms": N_REC,
+                   "grid": "80^3 x 8", "map_dtype": args.map_dtype, "ligand": f"{N_LIG} atoms / {T_LIG} torsions",
+                   "chains": N_CHAINS, "mc_steps": N_STEPS, "opt_iters": N_ITERS, "optimizer": args.optimizer,
+                   "top_k": TOP_K, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "evals_per_s": world * r["total_evals"] * args.steps / (r["elapsed_ms"] * 1e-3),
+        "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
+        "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
+                     "traffic": None,
+                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
+                                    f"(clock from MEASURED_PEAKS.json, {peaks_src})"},
+        "l2_gather": {"achieved_gbs": r["gather_bytes"] / per_launch_s / 1e9, "microbench_gbs": r["gather_gbs"],
+                      "frac": (r["gather_bytes"] / per_launch_s / 1e9) / r["gather_gbs"]},
+        "gpu_launches": r["launches_per_step"] * args.steps,
+        "clocks": r["clocks"],
+        "results_ok": r["results_ok"],
+    }
+    if e2e:
+        line["e2e"] = {"value": e2e["value"], "unit": "systems/s", "h2d_bytes_per_step": e2e["h2d"],
+                       "d2h_bytes_per_step": e2e["d2h"], "latency_p50_ms": e2e["p50_ms"],
+                       "latency_p99_ms": e2e["p99_ms"]}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

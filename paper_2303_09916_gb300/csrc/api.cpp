@@ -1,0 +1,822 @@
+// Host side of the C ABI: contexts, grid handles, scoring and the docking job
+// queue.  The queue realises the paper's asynchronous pipeline (Sec. 2 /
+// Fig. 4: copies prepared on the host, uploaded, run independently on the
+// GPU, results postprocessed) as a continuously batched service: a progress
+// thread admits queued jobs whenever device memory and job slots free up,
+// launches each on one of several streams so that jobs overlap on the device,
+// and retires finished jobs through CUDA events.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dsdp_internal.h"
+
+using namespace dsdp;
+
+struct dsdp_grid {
+  dsdp_ctx* ctx = nullptr;
+  dsdp_box box{};
+  int n[3] = {0, 0, 0};
+  double origin[3] = {0, 0, 0};
+  int dtype = 0, mode = 0;
+  void* d_maps = nullptr;
+  uint64_t map_bytes = 0;
+  int n_rec = 0;
+  float* d_rec_xyz = nullptr;
+  uint8_t* d_rec_type = nullptr;
+  uint64_t rec_bytes = 0;
+  std::atomic<int> users{0};  // jobs referencing the grid
+};
+
+namespace {
+
+enum class JobState { Queued, Running, Done, Failed, Cancelled };
+
+struct Job {
+  uint64_t id = 0;
+  JobState state = JobState::Queued;
+  dsdp_status err = DSDP_OK;
+  std::string msg;
+  const dsdp_grid* grid = nullptr;
+  std::vector<uint8_t> blob;
+  dsdp_dock_params params{};
+  int n_atoms = 0, T = 0;
+  // device memory: [blob | results]; results copied back with one D2H
+  void* d_mem = nullptr;
+  uint64_t d_bytes = 0;
+  uint64_t plan_bytes = 0;
+  size_t res_off = 0, res_bytes = 0;
+  // offsets inside the results region
+  size_t o_n, o_chain, o_score, o_inter, o_intra, o_conf, o_coords, o_cbe, o_cbc, o_evals, o_trace;
+  void* h_res = nullptr;  // pinned
+  dsdp_plan* plan = nullptr;
+  int stream = 0;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  float device_ms = 0.f;
+};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct dsdp_ctx {
+  int device = 0;
+  int sms = 148;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+  int max_inflight = 16;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t sync_stream = nullptr;   // synchronous calls
+  cudaStream_t alloc_stream = nullptr;  // allocations done outside a job stream
+  int next_stream = 0;
+  dsdp_alloc_fn alloc = nullptr;
+  dsdp_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::map<uint64_t, Job*> jobs;
+  std::deque<uint64_t> queue;
+  uint64_t next_id = 1;
+  int running = 0;
+  bool stop = false;
+  std::thread progress;
+  dsdp_stats stats{};
+};
+
+namespace dsdp {
+
+int ctx_sm_count(dsdp_ctx* ctx) {
+  if (ctx) return ctx->sms;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+void* ctx_alloc(dsdp_ctx* ctx, size_t bytes, void* stream) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (!ctx) return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+  if (ctx->alloc) {
+    p = ctx->alloc(bytes, stream ? stream : (void*)ctx->alloc_stream, ctx->alloc_user);
+    if (p && !stream) cudaStreamSynchronize(ctx->alloc_stream);
+    return p;
+  }
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->alloc_stream;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (!stream) cudaStreamSynchronize(ctx->alloc_stream);
+  return p;
+}
+
+void ctx_free(dsdp_ctx* ctx, void* p, size_t bytes, void* stream) {
+  if (!p) return;
+  if (!ctx) {
+    cudaFree(p);
+    return;
+  }
+  if (ctx->free_fn) {
+    ctx->free_fn(p, bytes, stream ? stream : (void*)ctx->alloc_stream, ctx->alloc_user);
+    return;
+  }
+  cudaFreeAsync(p, stream ? (cudaStream_t)stream : ctx->alloc_stream);
+}
+
+}  // namespace dsdp
+
+// ------------------------------------------------------------------ status
+extern "C" const char* dsdp_status_string(dsdp_status s) {
+  switch (s) {
+    case DSDP_OK: return "DSDP_OK";
+    case DSDP_PENDING: return "DSDP_PENDING";
+    case DSDP_ERR_INVALID_ARG: return "DSDP_ERR_INVALID_ARG";
+    case DSDP_ERR_OUT_OF_MEMORY: return "DSDP_ERR_OUT_OF_MEMORY";
+    case DSDP_ERR_NOT_FOUND: return "DSDP_ERR_NOT_FOUND";
+    case DSDP_ERR_TIMEOUT: return "DSDP_ERR_TIMEOUT";
+    case DSDP_ERR_CANCELLED: return "DSDP_ERR_CANCELLED";
+    case DSDP_ERR_DEVICE: return "DSDP_ERR_DEVICE";
+    case DSDP_ERR_INTERNAL: return "DSDP_ERR_INTERNAL";
+    default: return "DSDP_UNKNOWN_STATUS";
+  }
+}
+extern "C" const char* dsdp_last_error(void) { return dsdp::last_error(); }
+extern "C" const char* dsdp_version(void) { return "0.1.0"; }
+
+// ------------------------------------------------------------------ jobs
+namespace {
+
+// Frees a job's device resources (the caller adjusts ctx->in_use).
+void job_release_device(dsdp_ctx* ctx, Job* j) {
+  if (j->plan) {
+    dsdp_plan_destroy(ctx, j->plan);
+    j->plan = nullptr;
+  }
+  if (j->d_mem) {
+    ctx_free(ctx, j->d_mem, j->d_bytes, (void*)ctx->streams[j->stream]);
+    j->d_mem = nullptr;
+  }
+  if (j->ev_start) cudaEventDestroy(j->ev_start), j->ev_start = nullptr;
+  if (j->ev_done) cudaEventDestroy(j->ev_done), j->ev_done = nullptr;
+}
+
+void job_free_host(Job* j) {
+  if (j->h_res) cudaFreeHost(j->h_res), j->h_res = nullptr;
+}
+
+// Results region layout.
+void layout_results(Job* j) {
+  const dsdp_dock_params& p = j->params;
+  const int nx = 7 + j->T, k = p.top_k, C = p.n_chains;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += up256(bytes);
+    return at;
+  };
+  j->o_n = take(sizeof(int32_t));
+  j->o_chain = take(sizeof(int32_t) * k);
+  j->o_score = take(sizeof(double) * k);
+  j->o_inter = take(sizeof(double) * k);
+  j->o_intra = take(sizeof(double) * k);
+  j->o_conf = take(sizeof(double) * k * nx);
+  j->o_coords = take(sizeof(float) * k * j->n_atoms * 3);
+  j->o_cbe = take(sizeof(float) * C);
+  j->o_cbc = take(sizeof(float) * (size_t)C * nx);
+  j->o_evals = take(sizeof(uint32_t) * C);
+  j->o_trace = take(p.trace ? sizeof(float) * (size_t)C * (p.n_mc_steps + 1) * (nx + 4) : 0);
+  j->res_bytes = o;
+}
+
+// Estimated plan scratch of a job (rescoring arrays and tables).
+uint64_t plan_scratch_estimate(const Job* j) {
+  const uint64_t C = (uint64_t)j->params.n_chains;
+  return 4096 + 3 * 8 * C + 8 * C * j->n_atoms * 3 + 64 * C + 16 * C;
+}
+
+// Admit and launch one job (ctx->mu held).  Returns false if it could not start.
+bool job_launch(dsdp_ctx* ctx, Job* j) {
+  const dsdp_grid* g = j->grid;
+  j->stream = ctx->next_stream;
+  ctx->next_stream = (ctx->next_stream + 1) % (int)ctx->streams.size();
+  const cudaStream_t st = ctx->streams[j->stream];
+  layout_results(j);
+  j->res_off = up256(j->blob.size());
+  j->d_bytes = j->res_off + j->res_bytes;
+  j->d_mem = ctx_alloc(ctx, j->d_bytes, (void*)st);
+  auto fail = [&](dsdp_status s, const char* what) {
+    j->state = JobState::Failed;
+    j->err = s;
+    j->msg = what;
+    return false;
+  };
+  if (!j->d_mem) return fail(DSDP_ERR_OUT_OF_MEMORY, "job device allocation failed");
+  if (cudaMallocHost(&j->h_res, std::max(j->res_bytes, j->blob.size())) != cudaSuccess) {
+    cudaGetLastError();
+    ctx_free(ctx, j->d_mem, j->d_bytes, (void*)st);
+    j->d_mem = nullptr;
+    return fail(DSDP_ERR_OUT_OF_MEMORY, "pinned result buffer allocation failed");
+  }
+  // the blob goes up through the pinned result buffer; the results come back
+  // into it later on the same stream, after the upload has completed
+  uint8_t* dm = (uint8_t*)j->d_mem;
+  uint8_t* res = dm + j->res_off;
+  memcpy(j->h_res, j->blob.data(), j->blob.size());
+  cudaError_t e = cudaMemcpyAsync(dm, j->h_res, j->blob.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(check_cuda(e, "blob upload"), dsdp_last_error());
+  dsdp_job_device jd;
+  memset(&jd, 0, sizeof(jd));
+  jd.grid.d_maps = g->d_maps;
+  for (int a = 0; a < 3; ++a) {
+    jd.grid.n[a] = g->n[a];
+    jd.grid.origin[a] = g->origin[a];
+    jd.box_lo[a] = g->box.center[a] - g->box.size[a] / 2.0;
+    jd.box_size[a] = g->box.size[a];
+  }
+  jd.grid.spacing = g->box.spacing;
+  jd.grid.dtype = g->dtype;
+  jd.grid.mode = g->mode;
+  jd.receptor.n = g->n_rec;
+  jd.receptor.xyz = g->d_rec_xyz;
+  jd.receptor.xs_type = g->d_rec_type;
+  jd.h_blob = j->blob.data();
+  jd.d_blob = dm;
+  jd.params = j->params;
+  jd.d_chain_best_conf = (float*)(res + j->o_cbc);
+  jd.d_chain_best_e = (float*)(res + j->o_cbe);
+  jd.d_chain_evals = (uint32_t*)(res + j->o_evals);
+  jd.d_trace = j->params.trace ? (float*)(res + j->o_trace) : nullptr;
+  jd.d_out_n = (int32_t*)(res + j->o_n);
+  jd.d_out_chain = (int32_t*)(res + j->o_chain);
+  jd.d_out_score = (double*)(res + j->o_score);
+  jd.d_out_inter = (double*)(res + j->o_inter);
+  jd.d_out_intra = (double*)(res + j->o_intra);
+  jd.d_out_conf = (double*)(res + j->o_conf);
+  jd.d_out_coords = (float*)(res + j->o_coords);
+  dsdp_status s = dsdp_plan_create(ctx, 1, &jd, 0, 0, &j->plan);
+  if (s != DSDP_OK) {
+    ctx_free(ctx, j->d_mem, j->d_bytes, (void*)st);
+    j->d_mem = nullptr;
+    return fail(s, dsdp_last_error());
+  }
+  cudaEventCreate(&j->ev_start);
+  cudaEventCreate(&j->ev_done);
+  cudaEventRecord(j->ev_start, st);
+  s = dsdp_plan_launch(j->plan, (void*)st);
+  if (s == DSDP_OK) {
+    e = cudaMemcpyAsync(j->h_res, res, j->res_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, st);
+    if (e != cudaSuccess) s = check_cuda(e, "result download");
+  }
+  if (s != DSDP_OK) {
+    cudaStreamSynchronize(st);
+    fail(s, dsdp_last_error());
+    return false;
+  }
+  j->state = JobState::Running;
+  return true;
+}
+
+void progress_loop(dsdp_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  while (!ctx->stop) {
+    bool changed = false;
+    // retire finished jobs
+    for (auto& kv : ctx->jobs) {
+      Job* j = kv.second;
+      if (j->state != JobState::Running) continue;
+      const cudaError_t q = cudaEventQuery(j->ev_done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        j->state = JobState::Failed;
+        j->err = check_cuda(q, "job execution");
+        j->msg = dsdp_last_error();
+        ctx->stats.failed++;
+      } else {
+        j->state = JobState::Done;
+        cudaEventElapsedTime(&j->device_ms, j->ev_start, j->ev_done);
+        ctx->stats.completed++;
+      }
+      job_release_device(ctx, j);
+      ctx->in_use -= j->d_bytes + j->plan_bytes;
+      const_cast<dsdp_grid*>(j->grid)->users--;
+      ctx->running--;
+      changed = true;
+    }
+    // admit queued jobs in order while slots and memory allow
+    while (!ctx->queue.empty() && ctx->running < ctx->max_inflight) {
+      Job* j = ctx->jobs[ctx->queue.front()];
+      const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);
+      if (ctx->in_use + need > ctx->budget && ctx->running > 0) break;  // wait for memory
+      ctx->queue.pop_front();
+      if (job_launch(ctx, j)) {
+        j->plan_bytes = plan_scratch_estimate(j);
+        ctx->in_use += j->d_bytes + j->plan_bytes;
+        ctx->running++;
+      } else {
+        ctx->stats.failed++;
+        const_cast<dsdp_grid*>(j->grid)->users--;
+        job_release_device(ctx, j);
+      }
+      changed = true;
+    }
+    if (changed) ctx->cv_done.notify_all();
+    if (ctx->running > 0) ctx->cv_work.wait_for(lk, std::chrono::microseconds(100));
+    else ctx->cv_work.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+extern "C" dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** out) {
+  if (!out) return set_error(DSDP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  dsdp_create_params p{};
+  if (params) p = *params;
+  int n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess) return check_cuda(e, "cudaGetDeviceCount");
+  if (p.device < 0 || p.device >= n_dev) return set_error(DSDP_ERR_INVALID_ARG, "device %d of %d", p.device, n_dev);
+  if ((p.alloc == nullptr) != (p.free == nullptr))
+    return set_error(DSDP_ERR_INVALID_ARG, "alloc and free callbacks go together");
+  e = cudaSetDevice(p.device);
+  if (e != cudaSuccess) return check_cuda(e, "cudaSetDevice");
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p.device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p.device);
+  if (major * 10 + minor != 103)
+    return set_error(DSDP_ERR_DEVICE, "libdsdp is built for sm_103a (GB300); device %d is sm_%d%d", p.device, major,
+                     minor);
+  dsdp_ctx* ctx = new dsdp_ctx();
+  ctx->device = p.device;
+  cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, p.device);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  ctx->budget = p.mem_budget_bytes ? p.mem_budget_bytes : (uint64_t)(0.8 * (double)free_b);
+  ctx->max_inflight = p.max_inflight_jobs > 0 ? p.max_inflight_jobs : 16;
+  const int ns = p.n_streams > 0 ? p.n_streams : 4;
+  for (int i = 0; i < ns; ++i) {
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    ctx->streams.push_back(s);
+  }
+  cudaStreamCreateWithFlags(&ctx->sync_stream, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&ctx->alloc_stream, cudaStreamNonBlocking);
+  ctx->alloc = p.alloc;
+  ctx->free_fn = p.free;
+  ctx->alloc_user = p.alloc_user;
+  if (!ctx->alloc) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, p.device) == cudaSuccess) {
+      uint64_t thr = ctx->budget;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  ctx->stats.bytes_budget = ctx->budget;
+  ctx->progress = std::thread(progress_loop, ctx);
+  *out = ctx;
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_destroy(dsdp_ctx* ctx) {
+  if (!ctx) return DSDP_OK;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (uint64_t id : ctx->queue) ctx->jobs[id]->state = JobState::Cancelled;
+    ctx->queue.clear();
+    ctx->stop = true;
+  }
+  ctx->cv_work.notify_all();
+  if (ctx->progress.joinable()) ctx->progress.join();
+  cudaSetDevice(ctx->device);
+  for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+  for (auto& kv : ctx->jobs) {
+    Job* j = kv.second;
+    if (j->state == JobState::Running) job_release_device(ctx, j);
+    job_free_host(j);
+    delete j;
+  }
+  ctx->jobs.clear();
+  for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s), cudaStreamDestroy(s);
+  cudaStreamSynchronize(ctx->alloc_stream);
+  cudaStreamDestroy(ctx->alloc_stream);
+  cudaStreamDestroy(ctx->sync_stream);
+  delete ctx;
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_get_stats(dsdp_ctx* ctx, dsdp_stats* out) {
+  if (!ctx || !out) return set_error(DSDP_ERR_INVALID_ARG, "ctx/out NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *out = ctx->stats;
+  out->queued = (int32_t)ctx->queue.size();
+  out->running = ctx->running;
+  out->bytes_in_use = ctx->in_use;
+  out->bytes_budget = ctx->budget;
+  return DSDP_OK;
+}
+
+// ------------------------------------------------------------------ grids
+static dsdp_status check_receptor_host(const dsdp_receptor* r) {
+  if (!r || r->n < 1 || !r->xyz || !r->xs_type) return set_error(DSDP_ERR_INVALID_ARG, "receptor arrays invalid");
+  for (int i = 0; i < r->n; ++i) {
+    if (r->xs_type[i] > DSDP_XS_N_DA) return set_error(DSDP_ERR_INVALID_ARG, "receptor atom %d type %d", i, r->xs_type[i]);
+    for (int a = 0; a < 3; ++a)
+      if (!isfinite(r->xyz[3 * i + a])) return set_error(DSDP_ERR_INVALID_ARG, "receptor atom %d not finite", i);
+  }
+  return DSDP_OK;
+}
+
+static dsdp_status grid_alloc(dsdp_ctx* ctx, const dsdp_receptor* receptor, const dsdp_box* box,
+                              dsdp_map_dtype dtype, dsdp_grid_mode mode, dsdp_grid** out) {
+  dsdp_status s = validate_box(box);
+  if (s != DSDP_OK) return s;
+  if ((int)dtype < 0 || (int)dtype > 2 || (int)mode < 0 || (int)mode > 1)
+    return set_error(DSDP_ERR_INVALID_ARG, "bad map dtype/mode");
+  dsdp_grid* g = new dsdp_grid();
+  g->ctx = ctx;
+  g->box = *box;
+  grid_geometry(box, g->n, g->origin);
+  g->dtype = (int)dtype;
+  g->mode = (int)mode;
+  g->map_bytes = dsdp_grid_map_bytes(box, dtype, mode);
+  if (receptor) {
+    g->n_rec = receptor->n;
+    g->rec_bytes = up256((size_t)receptor->n * 12) + up256((size_t)receptor->n);
+  }
+  const uint64_t need = g->map_bytes + g->rec_bytes;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (need > ctx->budget) {
+      delete g;
+      return set_error(DSDP_ERR_OUT_OF_MEMORY, "grid of %llu bytes exceeds the budget", (unsigned long long)need);
+    }
+    ctx->in_use += need;
+  }
+  g->d_maps = ctx_alloc(ctx, g->map_bytes, nullptr);
+  if (receptor) {
+    uint8_t* r = (uint8_t*)ctx_alloc(ctx, g->rec_bytes, nullptr);
+    if (r) {
+      g->d_rec_xyz = (float*)r;
+      g->d_rec_type = r + up256((size_t)receptor->n * 12);
+    }
+  }
+  if (!g->d_maps || (receptor && !g->d_rec_xyz)) {
+    dsdp_grid_free(ctx, g);
+    return set_error(DSDP_ERR_OUT_OF_MEMORY, "grid device allocation failed");
+  }
+  if (receptor) {
+    cudaError_t e = cudaMemcpy(g->d_rec_xyz, receptor->xyz, (size_t)receptor->n * 12, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_rec_type, receptor->xs_type, receptor->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      dsdp_grid_free(ctx, g);
+      return check_cuda(e, "receptor upload");
+    }
+  }
+  *out = g;
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_grid_build(dsdp_ctx* ctx, const dsdp_receptor* receptor, const dsdp_box* box,
+                                       dsdp_map_dtype dtype, dsdp_grid_mode mode, dsdp_grid** out) {
+  if (!ctx || !out) return set_error(DSDP_ERR_INVALID_ARG, "ctx/out NULL");
+  *out = nullptr;
+  dsdp_status s = check_receptor_host(receptor);
+  if (s != DSDP_OK) return s;
+  cudaSetDevice(ctx->device);
+  dsdp_grid* g = nullptr;
+  s = grid_alloc(ctx, receptor, box, dtype, mode, &g);
+  if (s != DSDP_OK) return s;
+  dsdp_receptor dr{g->n_rec, g->d_rec_xyz, g->d_rec_type};
+  s = dsdp_grid_build_device(&dr, box, dtype, mode, g->d_maps, g->map_bytes, (void*)ctx->sync_stream);
+  if (s == DSDP_OK) s = check_cuda(cudaStreamSynchronize(ctx->sync_stream), "grid build");
+  if (s != DSDP_OK) {
+    dsdp_grid_free(ctx, g);
+    return s;
+  }
+  *out = g;
+  return DSDP_OK;
+}
+
+// FP32 host maps -> stored dtype (round to nearest even).
+static uint16_t f32_to_bf16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffff) ? 0x40 : 0));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+static float bf16_to_f32(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+static uint16_t f32_to_f16(float f) {
+  uint32_t x;
+  memcpy(&x, &f, 4);
+  const uint32_t sign = (x >> 16) & 0x8000u;
+  int32_t exp = (int32_t)((x >> 23) & 0xff) - 127 + 15;
+  uint32_t mant = x & 0x7fffffu;
+  if (((x >> 23) & 0xff) == 0xff) return (uint16_t)(sign | 0x7c00u | (mant ? 0x200u : 0u));
+  if (exp >= 31) return (uint16_t)(sign | 0x7c00u);
+  if (exp <= 0) {
+    if (exp < -10) return (uint16_t)sign;
+    mant |= 0x800000u;
+    const int shift = 14 - exp;
+    uint32_t half = mant >> shift;
+    const uint32_t rem = mant & ((1u << shift) - 1u), mid = 1u << (shift - 1);
+    if (rem > mid || (rem == mid && (half & 1u))) ++half;
+    return (uint16_t)(sign | half);
+  }
+  uint32_t h = sign | ((uint32_t)exp << 10) | (mant >> 13);
+  const uint32_t rem = mant & 0x1fffu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;
+  return (uint16_t)h;
+}
+static float f16_to_f32(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
+  const int exp = (h >> 10) & 0x1f;
+  const uint32_t mant = h & 0x3ffu;
+  float f;
+  if (exp == 0) {
+    f = ldexpf((float)mant, -24);
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u |= sign;
+    memcpy(&f, &u, 4);
+    return f;
+  }
+  uint32_t u = exp == 31 ? (sign | 0x7f800000u | (mant << 13)) : (sign | ((uint32_t)(exp - 15 + 127) << 23) | (mant << 13));
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+extern "C" dsdp_status dsdp_grid_from_maps(dsdp_ctx* ctx, const dsdp_receptor* receptor, const dsdp_box* box,
+                                           dsdp_map_dtype dtype, dsdp_grid_mode mode, const float* maps,
+                                           dsdp_grid** out) {
+  if (!ctx || !out || !maps) return set_error(DSDP_ERR_INVALID_ARG, "ctx/out/maps NULL");
+  *out = nullptr;
+  if (receptor) {
+    dsdp_status s = check_receptor_host(receptor);
+    if (s != DSDP_OK) return s;
+  }
+  cudaSetDevice(ctx->device);
+  dsdp_grid* g = nullptr;
+  dsdp_status s = grid_alloc(ctx, receptor, box, dtype, mode, &g);
+  if (s != DSDP_OK) return s;
+  const size_t count = (size_t)DSDP_NUM_MAP_TYPES * g->n[0] * g->n[1] * g->n[2] * (mode == DSDP_GRID_EQ4 ? 4 : 1);
+  cudaError_t e;
+  if (dtype == DSDP_MAP_F32) {
+    e = cudaMemcpy(g->d_maps, maps, count * 4, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<uint16_t> h(count);
+    for (size_t i = 0; i < count; ++i) h[i] = dtype == DSDP_MAP_BF16 ? f32_to_bf16(maps[i]) : f32_to_f16(maps[i]);
+    e = cudaMemcpy(g->d_maps, h.data(), count * 2, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    dsdp_grid_free(ctx, g);
+    return check_cuda(e, "maps upload");
+  }
+  *out = g;
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_grid_download(dsdp_ctx* ctx, const dsdp_grid* g, float* maps, size_t capacity_floats) {
+  if (!ctx || !g || !maps) return set_error(DSDP_ERR_INVALID_ARG, "ctx/grid/maps NULL");
+  const size_t count = (size_t)DSDP_NUM_MAP_TYPES * g->n[0] * g->n[1] * g->n[2] * (g->mode == DSDP_GRID_EQ4 ? 4 : 1);
+  if (capacity_floats < count) return set_error(DSDP_ERR_INVALID_ARG, "capacity %zu < %zu floats", capacity_floats, count);
+  cudaSetDevice(ctx->device);
+  cudaError_t e;
+  if (g->dtype == DSDP_MAP_F32) {
+    e = cudaMemcpy(maps, g->d_maps, count * 4, cudaMemcpyDeviceToHost);
+  } else {
+    std::vector<uint16_t> h(count);
+    e = cudaMemcpy(h.data(), g->d_maps, count * 2, cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < count; ++i) maps[i] = g->dtype == DSDP_MAP_BF16 ? bf16_to_f32(h[i]) : f16_to_f32(h[i]);
+  }
+  return check_cuda(e, "maps download");
+}
+
+extern "C" dsdp_status dsdp_grid_info(const dsdp_grid* g, int32_t n[3], double origin[3], double* spacing,
+                                      uint64_t* map_bytes) {
+  if (!g) return set_error(DSDP_ERR_INVALID_ARG, "grid NULL");
+  for (int a = 0; a < 3; ++a) {
+    if (n) n[a] = g->n[a];
+    if (origin) origin[a] = g->origin[a];
+  }
+  if (spacing) *spacing = g->box.spacing;
+  if (map_bytes) *map_bytes = g->map_bytes;
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_grid_free(dsdp_ctx* ctx, dsdp_grid* g) {
+  if (!g) return DSDP_OK;
+  if (!ctx) ctx = g->ctx;
+  if (g->users.load() > 0) return set_error(DSDP_ERR_INVALID_ARG, "grid still used by %d job(s)", g->users.load());
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->sync_stream);
+  ctx_free(ctx, g->d_maps, g->map_bytes, nullptr);
+  ctx_free(ctx, g->d_rec_xyz, g->rec_bytes, nullptr);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->in_use -= g->map_bytes + g->rec_bytes;
+  }
+  delete g;
+  return DSDP_OK;
+}
+
+static void grid_view_of(const dsdp_grid* g, dsdp_grid_view* v) {
+  memset(v, 0, sizeof(*v));
+  v->d_maps = g->d_maps;
+  for (int a = 0; a < 3; ++a) {
+    v->n[a] = g->n[a];
+    v->origin[a] = g->origin[a];
+  }
+  v->spacing = g->box.spacing;
+  v->dtype = g->dtype;
+  v->mode = g->mode;
+}
+
+// ------------------------------------------------------------------ scoring
+extern "C" dsdp_status dsdp_score_eval(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_ligand* ligand,
+                                       const double* conf, int32_t n_conf, double* energy, double* grad,
+                                       uint32_t flags) {
+  if (!ctx || !grid || !conf || n_conf < 0) return set_error(DSDP_ERR_INVALID_ARG, "score_eval arguments");
+  if (n_conf == 0) return DSDP_OK;
+  uint64_t bytes = 0;
+  dsdp_status s = dsdp_ligand_pack(ligand, nullptr, 0, &bytes);
+  if (s != DSDP_OK) return s;
+  std::vector<uint8_t> blob(bytes);
+  s = dsdp_ligand_pack(ligand, blob.data(), bytes, &bytes);
+  if (s != DSDP_OK) return s;
+  int32_t N, T, P, B;
+  dsdp_ligand_blob_info(blob.data(), &N, &T, &P, &B);
+  const size_t nx = 7 + T, nd = 6 + T;
+  std::vector<float> cf((size_t)n_conf * nx);
+  for (size_t i = 0; i < cf.size(); ++i) cf[i] = (float)conf[i];
+  cudaSetDevice(ctx->device);
+  const size_t o_conf = up256(bytes), o_e = o_conf + up256(cf.size() * 4), o_g = o_e + up256((size_t)n_conf * 4);
+  const size_t total = o_g + up256((size_t)n_conf * nd * 4);
+  uint8_t* d = (uint8_t*)ctx_alloc(ctx, total, nullptr);
+  if (!d) return set_error(DSDP_ERR_OUT_OF_MEMORY, "score_eval buffers");
+  cudaError_t e = cudaMemcpyAsync(d, blob.data(), bytes, cudaMemcpyHostToDevice, ctx->sync_stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d + o_conf, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice, ctx->sync_stream);
+  dsdp_grid_view v;
+  grid_view_of(grid, &v);
+  if (e == cudaSuccess) {
+    s = dsdp_score_eval_device(&v, blob.data(), d, (const float*)(d + o_conf), n_conf, (float*)(d + o_e),
+                               grad ? (float*)(d + o_g) : nullptr, flags, (void*)ctx->sync_stream);
+  } else {
+    s = check_cuda(e, "score_eval upload");
+  }
+  std::vector<float> he((size_t)n_conf), hg(grad ? (size_t)n_conf * nd : 0);
+  if (s == DSDP_OK) {
+    e = cudaMemcpyAsync(he.data(), d + o_e, he.size() * 4, cudaMemcpyDeviceToHost, ctx->sync_stream);
+    if (e == cudaSuccess && grad)
+      e = cudaMemcpyAsync(hg.data(), d + o_g, hg.size() * 4, cudaMemcpyDeviceToHost, ctx->sync_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->sync_stream);
+    if (e != cudaSuccess) s = check_cuda(e, "score_eval");
+  } else {
+    cudaStreamSynchronize(ctx->sync_stream);
+  }
+  ctx_free(ctx, d, total, nullptr);
+  if (s != DSDP_OK) return s;
+  if (energy)
+    for (int i = 0; i < n_conf; ++i) energy[i] = he[i];
+  if (grad)
+    for (size_t i = 0; i < hg.size(); ++i) grad[i] = hg[i];
+  return DSDP_OK;
+}
+
+// ------------------------------------------------------------------ docking
+extern "C" dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_ligand* ligand,
+                                        const dsdp_dock_params* params, uint64_t* job_id) {
+  if (!ctx || !grid || !job_id) return set_error(DSDP_ERR_INVALID_ARG, "ctx/grid/job_id NULL");
+  if (!grid->d_rec_xyz) return set_error(DSDP_ERR_INVALID_ARG, "grid has no receptor atoms (needed to rescore)");
+  Job* j = new Job();
+  dsdp_status s = normalize_params(params, &j->params);
+  if (s != DSDP_OK) {
+    delete j;
+    return s;
+  }
+  uint64_t bytes = 0;
+  s = dsdp_ligand_pack(ligand, nullptr, 0, &bytes);
+  if (s == DSDP_OK) {
+    j->blob.resize(bytes);
+    s = dsdp_ligand_pack(ligand, j->blob.data(), bytes, &bytes);
+  }
+  if (s != DSDP_OK) {
+    delete j;
+    return s;
+  }
+  int32_t P, B;
+  dsdp_ligand_blob_info(j->blob.data(), &j->n_atoms, &j->T, &P, &B);
+  j->grid = grid;
+  layout_results(j);
+  const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (need > ctx->budget) {
+      delete j;
+      return set_error(DSDP_ERR_OUT_OF_MEMORY, "job needs %llu bytes, budget %llu", (unsigned long long)need,
+                       (unsigned long long)ctx->budget);
+    }
+    j->id = ctx->next_id++;
+    const_cast<dsdp_grid*>(grid)->users++;
+    ctx->jobs[j->id] = j;
+    ctx->queue.push_back(j->id);
+    ctx->stats.submitted++;
+    *job_id = j->id;
+  }
+  ctx->cv_work.notify_all();
+  return DSDP_OK;
+}
+
+static void copy_results(const Job* j, dsdp_dock_result* out) {
+  const uint8_t* r = (const uint8_t*)j->h_res;
+  const int nx = 7 + j->T, k = j->params.top_k, C = j->params.n_chains;
+  int n_out = *(const int32_t*)(r + j->o_n);
+  if (n_out < 0 || n_out > k) n_out = 0;
+  const int m = std::min(n_out, std::max(out->capacity, 0));
+  out->n_out = m;
+  out->n_atoms = j->n_atoms;
+  out->n_torsions = j->T;
+  if (out->score) memcpy(out->score, r + j->o_score, sizeof(double) * m);
+  if (out->inter) memcpy(out->inter, r + j->o_inter, sizeof(double) * m);
+  if (out->intra) memcpy(out->intra, r + j->o_intra, sizeof(double) * m);
+  if (out->conf) memcpy(out->conf, r + j->o_conf, sizeof(double) * m * nx);
+  if (out->coords) memcpy(out->coords, r + j->o_coords, sizeof(float) * m * j->n_atoms * 3);
+  if (out->chain) memcpy(out->chain, r + j->o_chain, sizeof(int32_t) * m);
+  if (out->chain_best_e) memcpy(out->chain_best_e, r + j->o_cbe, sizeof(float) * C);
+  if (out->chain_best_conf) memcpy(out->chain_best_conf, r + j->o_cbc, sizeof(float) * (size_t)C * nx);
+  if (out->trace && j->params.trace)
+    memcpy(out->trace, r + j->o_trace, sizeof(float) * (size_t)C * (j->params.n_mc_steps + 1) * (nx + 4));
+  const uint32_t* ev = (const uint32_t*)(r + j->o_evals);
+  uint64_t total = 0;
+  for (int c = 0; c < C; ++c) total += ev[c];
+  out->n_evals = total;
+}
+
+extern "C" dsdp_status dsdp_dock_poll(dsdp_ctx* ctx, uint64_t job_id, dsdp_dock_result* out, int32_t wait_ms) {
+  if (!ctx) return set_error(DSDP_ERR_INVALID_ARG, "ctx NULL");
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto it = ctx->jobs.find(job_id);
+  if (it == ctx->jobs.end()) return set_error(DSDP_ERR_NOT_FOUND, "job %llu not found", (unsigned long long)job_id);
+  Job* j = it->second;
+  auto finished = [&] { return j->state != JobState::Queued && j->state != JobState::Running; };
+  if (!finished() && wait_ms != 0) {
+    if (wait_ms < 0) ctx->cv_done.wait(lk, finished);
+    else ctx->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), finished);
+  }
+  if (!finished()) return DSDP_PENDING;
+  dsdp_status s = DSDP_OK;
+  if (j->state == JobState::Done) {
+    if (out) {
+      copy_results(j, out);
+      out->device_ms = j->device_ms;
+    }
+  } else if (j->state == JobState::Cancelled) {
+    s = set_error(DSDP_ERR_CANCELLED, "job %llu was cancelled", (unsigned long long)job_id);
+  } else {
+    s = set_error(j->err, "job %llu failed: %s", (unsigned long long)job_id, j->msg.c_str());
+  }
+  ctx->jobs.erase(it);
+  lk.unlock();
+  job_free_host(j);
+  delete j;
+  return s;
+}
+
+extern "C" dsdp_status dsdp_dock_cancel(dsdp_ctx* ctx, uint64_t job_id) {
+  if (!ctx) return set_error(DSDP_ERR_INVALID_ARG, "ctx NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->jobs.find(job_id);
+  if (it == ctx->jobs.end()) return set_error(DSDP_ERR_NOT_FOUND, "job %llu not found", (unsigned long long)job_id);
+  Job* j = it->second;
+  if (j->state == JobState::Queued) {
+    ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), job_id), ctx->queue.end());
+    j->state = JobState::Cancelled;
+    const_cast<dsdp_grid*>(j->grid)->users--;
+    ctx->stats.cancelled++;
+    ctx->cv_done.notify_all();
+    return DSDP_OK;
+  }
+  if (j->state == JobState::Running) return DSDP_PENDING;
+  return DSDP_OK;
+}

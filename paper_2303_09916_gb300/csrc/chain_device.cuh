@@ -1,0 +1,547 @@
+// Warp-per-chain score + gradient, local optimisers and Monte Carlo chain.
+//
+// One warp owns one conformation.  Lanes hold atoms (APL atoms per lane, in
+// the blob's depth-first order), rigid bodies (lane b = body b) and the
+// components of 6 + T dimensional vectors (lane j = component j: 0..2
+// position, 3..5 rotation vector, 6 + k torsion k).  The ligand topology sits
+// in shared memory; grid maps are read from L2 through the read-only path.
+#pragma once
+#include "device_common.cuh"
+
+namespace dsdp {
+
+// Pointers into a staged (shared-memory) blob.
+struct LigView {
+  const BlobHeader* h;
+  const float4* atom;
+  const int32_t* atom_user;
+  const BodyRec* body;
+  const uint32_t* pairs;
+  const uint16_t* csr_start;
+  const uint32_t* csr;
+  const int32_t* torsion_body;
+  int n_atoms, T, n_bodies, n_pairs, rounds;
+};
+
+__device__ __forceinline__ LigView view_blob(const uint8_t* b) {
+  LigView v;
+  v.h = reinterpret_cast<const BlobHeader*>(b);
+  v.atom = reinterpret_cast<const float4*>(b + v.h->off_atom);
+  v.atom_user = reinterpret_cast<const int32_t*>(b + v.h->off_atom_user);
+  v.body = reinterpret_cast<const BodyRec*>(b + v.h->off_body);
+  v.pairs = reinterpret_cast<const uint32_t*>(b + v.h->off_pairs);
+  v.csr_start = reinterpret_cast<const uint16_t*>(b + v.h->off_csr_start);
+  v.csr = reinterpret_cast<const uint32_t*>(b + v.h->off_csr);
+  v.torsion_body = reinterpret_cast<const int32_t*>(b + v.h->off_torsion_body);
+  v.n_atoms = v.h->n_atoms;
+  v.T = v.h->n_torsions;
+  v.n_bodies = v.h->n_bodies;
+  v.n_pairs = v.h->n_pairs;
+  v.rounds = v.h->rounds;
+  return v;
+}
+
+// Per-lane registers of one ligand.
+template <int APL>
+struct LaneLig {
+  float3 loc[APL];
+  int type[APL];
+  int body[APL];
+  bool valid[APL];
+  // body lane
+  float3 boff, baxis;
+  int bparent, btors, ar0, ar1;
+  // vector lane 6 + k: body of torsion k
+  int tbody;
+};
+
+template <int APL>
+__device__ __forceinline__ void load_lane_lig(const LigView& L, LaneLig<APL>& R) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    const int i = lane * APL + s;
+    R.valid[s] = i < L.n_atoms;
+    const float4 a = R.valid[s] ? L.atom[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    R.loc[s] = make_float3(a.x, a.y, a.z);
+    const int packed = __float_as_int(a.w);
+    R.type[s] = packed & 0xff;
+    R.body[s] = R.valid[s] ? (packed >> 8) & 0xff : 0;
+  }
+  if (lane < L.n_bodies) {
+    const BodyRec& b = L.body[lane];
+    R.boff = make_float3(b.off[0], b.off[1], b.off[2]);
+    R.baxis = make_float3(b.axis[0], b.axis[1], b.axis[2]);
+    R.bparent = b.parent;
+    R.btors = b.torsion;
+    R.ar0 = b.atom_begin;
+    R.ar1 = b.atom_end;
+  } else {
+    R.boff = R.baxis = make_float3(0.f, 0.f, 0.f);
+    R.bparent = -1;
+    R.btors = -1;
+    R.ar0 = R.ar1 = 0;
+  }
+  R.tbody = (lane >= 6 && lane < 6 + L.T) ? L.torsion_body[lane - 6] : 0;
+}
+
+// Conformation held by a warp: p and q replicated in every lane, torsion k in lane 6 + k.
+struct Conf {
+  float3 p;
+  Quat q;
+  float th;
+};
+
+// Per-warp shared scratch.
+struct WarpScratch {
+  float4* coords;  // [kMaxAtoms]
+  float* pair_s;   // [n_pairs]
+};
+
+// Score and gradient of one conformation (all lanes return the same E;
+// lane j < 6 + T returns gradient component j, other lanes 0).
+template <int APL, int FMT>
+__device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, const LaneLig<APL>& R,
+                                           const WarpScratch& W, const Conf& c, float& grad, uint32_t flags) {
+  const int lane = threadIdx.x & 31;
+  const int nb = L.n_bodies;
+  // ---- body frames: local transforms composed by pointer jumping
+  const float tb = __shfl_sync(kFull, c.th, (lane > 0 && lane < nb) ? 6 + R.btors : 0);
+  Quat Q;
+  float3 O;
+  int ptr;
+  if (lane == 0) {
+    Q = c.q;
+    O = c.p;
+    ptr = -1;
+  } else if (lane < nb) {
+    float s, co;
+    sincosf(0.5f * tb, &s, &co);
+    Q = Quat{co, s * R.baxis.x, s * R.baxis.y, s * R.baxis.z};
+    O = R.boff;
+    ptr = R.bparent;
+  } else {
+    Q = Quat{1.f, 0.f, 0.f, 0.f};
+    O = make_float3(0.f, 0.f, 0.f);
+    ptr = -1;
+  }
+  for (int r = 0; r < L.rounds; ++r) {
+    const int src = ptr >= 0 ? ptr : lane;
+    const Quat Qp = shflq(Q, src);
+    const float3 Op = shfl3(O, src);
+    const int pp = __shfl_sync(kFull, ptr, src);
+    if (ptr >= 0) {
+      O = Op + qrot(Qp, O);
+      Q = qmul(Qp, Q);
+      ptr = pp;
+    }
+  }
+  // ---- atom positions
+  float3 pos[APL];
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    const Quat Qb = shflq(Q, R.body[s]);
+    const float3 Ob = shfl3(O, R.body[s]);
+    pos[s] = Ob + qrot(Qb, R.loc[s]);
+  }
+  // ---- inter: grid maps
+  float e_lane = 0.f;
+  float3 g[APL];
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    g[s] = make_float3(0.f, 0.f, 0.f);
+    if ((flags & DSDP_TERM_INTER) && R.valid[s]) e_lane += sample_map<FMT>(M, R.type[s], pos[s], g[s]);
+  }
+  // ---- intra: pairs once, forces gathered per atom
+  if (flags & DSDP_TERM_INTRA) {
+#pragma unroll
+    for (int s = 0; s < APL; ++s)
+      if (R.valid[s]) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
+    __syncwarp();
+    for (int p = lane; p < L.n_pairs; p += 32) {
+      const uint32_t pr = L.pairs[p];
+      const int i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
+      const float4 a = W.coords[i], b = W.coords[j];
+      const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      float sp = 0.f;
+      if (r2 < kCutoff * kCutoff) {
+        const float r = sqrtf(r2);
+        const int ti = tp >> 3, tj = tp & 7;
+        float e, de;
+        vina_pair(r - (c_xs_radius[ti] + c_xs_radius[tj]), pair_bits(ti, tj), e, de);
+        e_lane += e;
+        sp = r > 0.f ? de / r : 0.f;
+      }
+      W.pair_s[p] = sp;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < APL; ++s) {
+      if (!R.valid[s]) continue;
+      const int i = lane * APL + s;
+      const int k0 = L.csr_start[i], k1 = L.csr_start[i + 1];
+      for (int k = k0; k < k1; ++k) {
+        const uint32_t e = L.csr[k];
+        const float sp = W.pair_s[e & 0xffff];
+        const float4 b = W.coords[e >> 16];
+        g[s].x += sp * (pos[s].x - b.x);
+        g[s].y += sp * (pos[s].y - b.y);
+        g[s].z += sp * (pos[s].z - b.z);
+      }
+    }
+    __syncwarp();
+  }
+  const float E = warp_sum(e_lane);
+  // ---- back-propagation: prefix sums over atoms (depth-first order) of
+  //      (g_i, (r_i - p) x g_i); a subtree is a contiguous atom range.
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float acc[APL][6];
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    const float3 t = cross3(pos[s] - c.p, g[s]);
+    if (R.valid[s]) {
+      v[0] += g[s].x;
+      v[1] += g[s].y;
+      v[2] += g[s].z;
+      v[3] += t.x;
+      v[4] += t.y;
+      v[5] += t.z;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[s][k] = v[k];
+  }
+  float inc[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) inc[k] = v[k];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float t = __shfl_up_sync(kFull, inc[k], o);
+      if (lane >= o) inc[k] += t;
+    }
+  }
+  float pre[APL][6];  // inclusive prefix at each of this lane's atoms
+#pragma unroll
+  for (int s = 0; s < APL; ++s)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pre[s][k] = inc[k] - v[k] + acc[s][k];
+  float tot[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) tot[k] = __shfl_sync(kFull, inc[k], 31);
+  // torsion gradient on body lanes
+  const bool is_child = lane > 0 && lane < nb;
+  const int hi = is_child ? R.ar1 - 1 : 0, lo = is_child ? R.ar0 - 1 : 0;
+  float shi[6], slo[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    shi[k] = 0.f;
+    slo[k] = 0.f;
+  }
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float a = __shfl_sync(kFull, pre[s][k], hi / APL);
+      const float b = __shfl_sync(kFull, pre[s][k], lo / APL);
+      if (hi % APL == s) shi[k] = a;
+      if (lo % APL == s) slo[k] = b;
+    }
+  }
+  float tor = 0.f;
+  if (is_child) {
+    const float3 G = make_float3(shi[0] - slo[0], shi[1] - slo[1], shi[2] - slo[2]);
+    const float3 C = make_float3(shi[3] - slo[3], shi[4] - slo[4], shi[5] - slo[5]);
+    const float3 axis = qrot(Q, R.baxis);
+    tor = dot3(axis, C - cross3(O - c.p, G));
+  }
+  const float tv = __shfl_sync(kFull, tor, R.tbody);
+  float gl = 0.f;
+  if (lane < 6) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (lane == k) gl = tot[k];
+  } else if (lane < 6 + L.T) {
+    gl = tv;
+  }
+  grad = gl;
+  return E;
+}
+
+// Coordinates of this lane's atoms for a conformation (same kinematics as eval_conf).
+template <int APL>
+__device__ __forceinline__ void conf_coords(const LigView& L, const LaneLig<APL>& R, const Conf& c, float3* pos) {
+  const int lane = threadIdx.x & 31;
+  const int nb = L.n_bodies;
+  const float tb = __shfl_sync(kFull, c.th, (lane > 0 && lane < nb) ? 6 + R.btors : 0);
+  Quat Q;
+  float3 O;
+  int ptr;
+  if (lane == 0) {
+    Q = c.q;
+    O = c.p;
+    ptr = -1;
+  } else if (lane < nb) {
+    float s, co;
+    sincosf(0.5f * tb, &s, &co);
+    Q = Quat{co, s * R.baxis.x, s * R.baxis.y, s * R.baxis.z};
+    O = R.boff;
+    ptr = R.bparent;
+  } else {
+    Q = Quat{1.f, 0.f, 0.f, 0.f};
+    O = make_float3(0.f, 0.f, 0.f);
+    ptr = -1;
+  }
+  for (int r = 0; r < L.rounds; ++r) {
+    const int src = ptr >= 0 ? ptr : lane;
+    const Quat Qp = shflq(Q, src);
+    const float3 Op = shfl3(O, src);
+    const int pp = __shfl_sync(kFull, ptr, src);
+    if (ptr >= 0) {
+      O = Op + qrot(Qp, O);
+      Q = qmul(Qp, Q);
+      ptr = pp;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    const Quat Qb = shflq(Q, R.body[s]);
+    const float3 Ob = shfl3(O, R.body[s]);
+    pos[s] = Ob + qrot(Qb, R.loc[s]);
+  }
+}
+
+// c (+) s for a step held in lane layout.
+__device__ __forceinline__ Conf apply_step(const Conf& c, float s, int T) {
+  const int lane = threadIdx.x & 31;
+  Conf o;
+  o.p = make_float3(c.p.x + __shfl_sync(kFull, s, 0), c.p.y + __shfl_sync(kFull, s, 1),
+                    c.p.z + __shfl_sync(kFull, s, 2));
+  const Quat dq = quat_from_rotvec(__shfl_sync(kFull, s, 3), __shfl_sync(kFull, s, 4), __shfl_sync(kFull, s, 5));
+  o.q = qnormalize(qmul(dq, c.q));
+  o.th = (lane >= 6 && lane < 6 + T) ? wrap_angle(c.th + s) : c.th;
+  return o;
+}
+
+struct OptOut {
+  float e;
+  uint32_t evals;
+};
+
+// BFGS with Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1,
+// inverse-Hessian update Eq. 6.17).  Lane j keeps row j of H.
+template <int APL, int FMT>
+__device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, const LaneLig<APL>& R,
+                                            const WarpScratch& W, Conf& x, int max_iters) {
+  const int lane = threadIdx.x & 31;
+  const int D = 6 + L.T;
+  float g;
+  float e = eval_conf<APL, FMT>(M, L, R, W, x, g, DSDP_TERM_ALL);
+  uint32_t evals = 1;
+  float H[kMaxDim];
+#pragma unroll
+  for (int k = 0; k < kMaxDim; ++k) H[k] = (k == lane) ? 1.f : 0.f;
+  for (int it = 0; it < max_iters; ++it) {
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k) d -= H[k] * __shfl_sync(kFull, g, k);
+    if (lane >= D) d = 0.f;
+    const float gd = warp_sum(g * d);
+    float alpha = 1.f, et = 0.f, gt = 0.f;
+    Conf xt;
+    bool ok = false;
+    for (int trial = 0; trial < kMaxTrials; ++trial) {
+      xt = apply_step(x, alpha * d, L.T);
+      et = eval_conf<APL, FMT>(M, L, R, W, xt, gt, DSDP_TERM_ALL);
+      ++evals;
+      if (et <= e + kArmijoC1 * alpha * gd) {
+        ok = true;
+        break;
+      }
+      alpha *= kShrink;
+    }
+    if (!ok) break;
+    const float s = alpha * d, y = gt - g;
+    const float sy = warp_sum(s * y);
+    x = xt;
+    g = gt;
+    e = et;
+    if (sy > kMinCurvature) {
+      float hy = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxDim; ++k) hy += H[k] * __shfl_sync(kFull, y, k);
+      if (lane >= D) hy = 0.f;
+      const float yhy = warp_sum(y * hy);
+      const float rho = 1.f / sy;
+      const float coef = rho * rho * yhy + rho;
+#pragma unroll
+      for (int k = 0; k < kMaxDim; ++k) {
+        const float sk = __shfl_sync(kFull, s, k), hk = __shfl_sync(kFull, hy, k);
+        H[k] += coef * s * sk - rho * (s * hk + hy * sk);
+      }
+    }
+  }
+  return OptOut{e, evals};
+}
+
+// Barzilai-Borwein (the paper's second modification, Sec. 2 / ref. 37): BB1
+// step s.s / s.y without line search, clamped; returns the best iterate.
+template <int APL, int FMT>
+__device__ __forceinline__ OptOut bb_warp(const MapView& M, const LigView& L, const LaneLig<APL>& R,
+                                          const WarpScratch& W, Conf& x, int max_iters) {
+  float g;
+  float e = eval_conf<APL, FMT>(M, L, R, W, x, g, DSDP_TERM_ALL);
+  uint32_t evals = 1;
+  Conf best = x;
+  float ebest = e;
+  float alpha = kBBAlpha0;
+  for (int it = 0; it < max_iters; ++it) {
+    const float s = -alpha * g;
+    x = apply_step(x, s, L.T);
+    float gn;
+    e = eval_conf<APL, FMT>(M, L, R, W, x, gn, DSDP_TERM_ALL);
+    ++evals;
+    const float sy = warp_sum(s * (gn - g));
+    const float ss = warp_sum(s * s);
+    alpha = sy > 0.f ? fminf(fmaxf(ss / sy, kBBAlphaMin), kBBAlphaMax) : kBBAlphaMax;
+    g = gn;
+    if (e < ebest) {
+      ebest = e;
+      best = x;
+    }
+  }
+  x = best;
+  return OptOut{ebest, evals};
+}
+
+template <int APL, int FMT>
+__device__ __forceinline__ OptOut local_opt(const MapView& M, const LigView& L, const LaneLig<APL>& R,
+                                            const WarpScratch& W, Conf& x, int optimizer, int iters) {
+  return optimizer == DSDP_OPT_BB ? bb_warp<APL, FMT>(M, L, R, W, x, iters)
+                                  : bfgs_warp<APL, FMT>(M, L, R, W, x, iters);
+}
+
+// Write conf (7 + T floats) from lane layout: lanes 0..2 p, 3..6 q, 7 + k theta_k.
+__device__ __forceinline__ void store_conf(float* out, const Conf& c, int T) {
+  const int lane = threadIdx.x & 31;
+  const float th = __shfl_sync(kFull, c.th, lane >= 7 ? lane - 1 : 0);
+  if (lane < 7 + T) {
+    float v;
+    if (lane == 0) v = c.p.x;
+    else if (lane == 1) v = c.p.y;
+    else if (lane == 2) v = c.p.z;
+    else if (lane == 3) v = c.q.w;
+    else if (lane == 4) v = c.q.x;
+    else if (lane == 5) v = c.q.y;
+    else if (lane == 6) v = c.q.z;
+    else v = th;
+    out[lane] = v;
+  }
+}
+
+__device__ __forceinline__ Conf load_conf(const float* in, int T) {
+  const int lane = threadIdx.x & 31;
+  Conf c;
+  c.p = make_float3(in[0], in[1], in[2]);
+  c.q = Quat{in[3], in[4], in[5], in[6]};
+  c.th = (lane >= 6 && lane < 6 + T) ? in[lane + 1] : 0.f;
+  return c;
+}
+
+// One Monte Carlo chain (Sec. 2: one of many short independent copies; Vina's
+// mutation and Metropolis rules).
+template <int APL, int FMT>
+__device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& W, int chain) {
+  const int lane = threadIdx.x & 31;
+  const MapView M = make_map_view(J);
+  LaneLig<APL> R;
+  load_lane_lig<APL>(L, R);
+  const int T = L.T, nx = 7 + T;
+  const ChainStream rs{J.seed_lo, J.seed_hi, (uint32_t)chain};
+  // initial conformation: uniform words n = 0.. of step 0 (word n % 4 of block n / 4)
+  const uint4 b0 = rs.block(0, 0), b1 = rs.block(0, 1);
+  Conf cur;
+  cur.p = make_float3(J.box_lo[0] + J.box_size[0] * ChainStream::to_uniform(b0.x),
+                      J.box_lo[1] + J.box_size[1] * ChainStream::to_uniform(b0.y),
+                      J.box_lo[2] + J.box_size[2] * ChainStream::to_uniform(b0.z));
+  {
+    const float u1 = ChainStream::to_uniform(b0.w), u2 = ChainStream::to_uniform(b1.x),
+                u3 = ChainStream::to_uniform(b1.y);
+    float s2, c2, s3, c3;
+    sincosf(kTwoPiF * u2, &s2, &c2);
+    sincosf(kTwoPiF * u3, &s3, &c3);
+    const float a = sqrtf(1.f - u1), b = sqrtf(u1);
+    cur.q = Quat{b * c3, a * s2, a * c2, b * s3};
+  }
+  {
+    const int n = 6 + (lane - 6);  // word index of torsion lane - 6
+    float th = 0.f;
+    if (lane >= 6 && lane < 6 + T) {
+      const uint4 bk = rs.block(0, (uint32_t)(n >> 2));
+      th = kPiF - kTwoPiF * ChainStream::to_uniform(pick(bk, n & 3));
+    }
+    cur.th = th;
+  }
+  OptOut o = local_opt<APL, FMT>(M, L, R, W, cur, J.optimizer, J.n_opt_iters);
+  float e_cur = o.e;
+  uint32_t evals = o.evals;
+  Conf best = cur;
+  float e_best = e_cur;
+  const size_t trace_stride = (size_t)nx + 4;
+  float* trace = J.trace ? J.trace + (size_t)chain * (J.n_steps + 1) * trace_stride : nullptr;
+  if (trace) {
+    store_conf(trace, cur, T);
+    if (lane == 0) {
+      trace[nx + 0] = e_cur;
+      trace[nx + 1] = e_cur;
+      trace[nx + 2] = -1.f;
+      trace[nx + 3] = 1.f;
+    }
+  }
+  const float inv_gyr = 1.f / L.h->gyration_radius;
+  for (int step = 1; step <= J.n_steps; ++step) {
+    const uint4 w0 = rs.block((uint32_t)step, 0);
+    const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
+    Conf cand = cur;
+    if (mode == 0) {
+      const float3 b = unit_ball(rs, (uint32_t)step);
+      cand.p = cand.p + kMutationAmplitude * b;
+    } else if (mode == 1) {
+      const float3 b = unit_ball(rs, (uint32_t)step);
+      const float k = kMutationAmplitude * inv_gyr;
+      cand.q = qnormalize(qmul(quat_from_rotvec(k * b.x, k * b.y, k * b.z), cand.q));
+    } else if (lane == 6 + (mode - 2)) {
+      cand.th = kPiF - kTwoPiF * ChainStream::to_uniform(w0.z);
+    }
+    o = local_opt<APL, FMT>(M, L, R, W, cand, J.optimizer, J.n_opt_iters);
+    evals += o.evals;
+    const float u = ChainStream::to_uniform(w0.y);
+    const bool accept = (o.e < e_cur) || (u < expf(-(o.e - e_cur) / J.temperature));
+    if (accept) {
+      cur = cand;
+      e_cur = o.e;
+      if (o.e < e_best) {
+        best = cand;
+        e_best = o.e;
+      }
+    }
+    if (trace) {
+      float* t = trace + (size_t)step * trace_stride;
+      store_conf(t, cur, T);
+      if (lane == 0) {
+        t[nx + 0] = o.e;
+        t[nx + 1] = e_cur;
+        t[nx + 2] = (float)mode;
+        t[nx + 3] = accept ? 1.f : 0.f;
+      }
+    }
+  }
+  store_conf(J.chain_best_conf + (size_t)chain * nx, best, T);
+  if (lane == 0) {
+    J.chain_best_e[chain] = e_best;
+    J.chain_evals[chain] = evals;
+  }
+}
+
+}  // namespace dsdp

@@ -1,0 +1,312 @@
+// Device helpers shared by the kernels of libdsdp (sm_103a).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dsdp_internal.h"
+
+namespace dsdp {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+// Per-type tables (Vina XS types 0..8): radius and bits (1 hydrophobic,
+// 2 donor, 4 acceptor).
+static __constant__ float c_xs_radius[9] = {1.9f, 1.9f, 1.8f, 1.8f, 1.8f, 1.7f, 1.7f, 2.0f, 1.8f};
+static __constant__ int c_xs_bits[9] = {1, 0, 0, 2, 4, 4, 6, 0, 6};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds; each round multiplies words 0 and 2 by the two Philox
+// constants, swaps in the high halves xor-ed with the key and the other words,
+// and bumps the key by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t pick(uint4 v, int w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+// Stream of one chain: word w of block b at MC step s is word w of
+// Philox(counter (chain, s, b, 0), key (seed_lo, seed_hi)).
+struct ChainStream {
+  uint32_t k0, k1, chain;
+  __device__ __forceinline__ uint4 block(uint32_t step, uint32_t b) const {
+    return philox4x32_10(make_uint4(chain, step, b, 0u), k0, k1);
+  }
+  // top 24 bits * 2^-24: exact in FP32
+  __device__ __forceinline__ static float to_uniform(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+};
+
+// Uniform point in the unit ball: attempt a (0..15) uses block 1 + a; the
+// coordinates are (word >> 8) - 2^23, accepted when the integer sum of squares
+// is <= 2^46; the point is v / 2^23.  All lanes compute the same point.
+__device__ __forceinline__ float3 unit_ball(const ChainStream& s, uint32_t step) {
+  for (int a = 0; a < 16; ++a) {
+    const uint4 v = s.block(step, 1u + a);
+    const long long x = (long long)(v.x >> 8) - (1ll << 23);
+    const long long y = (long long)(v.y >> 8) - (1ll << 23);
+    const long long z = (long long)(v.z >> 8) - (1ll << 23);
+    if (x * x + y * y + z * z <= (1ll << 46))
+      return make_float3((float)x * (1.0f / 8388608.0f), (float)y * (1.0f / 8388608.0f),
+                         (float)z * (1.0f / 8388608.0f));
+  }
+  return make_float3(0.f, 0.f, 0.f);
+}
+
+// ------------------------------------------------------------------ small math
+struct Quat {
+  float w, x, y, z;
+};
+
+__device__ __forceinline__ Quat qmul(const Quat& a, const Quat& b) {
+  Quat r;
+  r.w = a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z;
+  r.x = a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y;
+  r.y = a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x;
+  r.z = a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w;
+  return r;
+}
+
+// R(q) v for a unit quaternion: v + w t + u x t with t = 2 u x v.
+__device__ __forceinline__ float3 qrot(const Quat& q, const float3& v) {
+  const float tx = 2.f * (q.y * v.z - q.z * v.y);
+  const float ty = 2.f * (q.z * v.x - q.x * v.z);
+  const float tz = 2.f * (q.x * v.y - q.y * v.x);
+  return make_float3(v.x + q.w * tx + (q.y * tz - q.z * ty), v.y + q.w * ty + (q.z * tx - q.x * tz),
+                     v.z + q.w * tz + (q.x * ty - q.y * tx));
+}
+
+__device__ __forceinline__ Quat qnormalize(const Quat& q) {
+  const float inv = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  return Quat{q.w * inv, q.x * inv, q.y * inv, q.z * inv};
+}
+
+// Unit quaternion of a rotation vector.
+__device__ __forceinline__ Quat quat_from_rotvec(float wx, float wy, float wz) {
+  const float angle = sqrtf(wx * wx + wy * wy + wz * wz);
+  if (angle == 0.f) return Quat{1.f, 0.f, 0.f, 0.f};
+  float s, c;
+  sincosf(0.5f * angle, &s, &c);
+  const float k = s / angle;
+  return Quat{c, wx * k, wy * k, wz * k};
+}
+
+// Wrap to (-pi, pi].
+__device__ __forceinline__ float wrap_angle(float t) { return t - kTwoPiF * ceilf((t - kPiF) / kTwoPiF); }
+
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float3 shfl3(float3 v, int src) {
+  return make_float3(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src));
+}
+__device__ __forceinline__ Quat shflq(const Quat& q, int src) {
+  return Quat{__shfl_sync(kFull, q.w, src), __shfl_sync(kFull, q.x, src), __shfl_sync(kFull, q.y, src),
+              __shfl_sync(kFull, q.z, src)};
+}
+
+// ------------------------------------------------------------------ pair score
+// Vina pair score of surface distance d (the scoring function DSDP keeps,
+// Sec. 2): weighted gauss1, gauss2, repulsion, hydrophobic and H-bond terms.
+// bits: 1 = hydrophobic pair, 2 = donor/acceptor pair.  Returns e and de/dd.
+__device__ __forceinline__ void vina_pair(float d, int bits, float& e, float& de) {
+  const float a = 2.f * d;  // d / 0.5
+  const float g1 = __expf(-a * a);
+  const float b = 0.5f * (d - 3.f);  // (d - 3) / 2
+  const float g2 = __expf(-b * b);
+  e = kWGauss1 * g1 + kWGauss2 * g2;
+  de = kWGauss1 * g1 * (-8.f * d) + kWGauss2 * g2 * (-b);
+  if (d < 0.f) {
+    e += kWRepulsion * d * d;
+    de += 2.f * kWRepulsion * d;
+  }
+  if (bits & 1) {
+    if (d < 0.5f) {
+      e += kWHydrophobic;
+    } else if (d < 1.5f) {
+      e += kWHydrophobic * (1.5f - d);
+      de -= kWHydrophobic;
+    }
+  }
+  if (bits & 2) {
+    if (d < -0.7f) {
+      e += kWHBond;
+    } else if (d < 0.f) {
+      e += kWHBond * (-d * (1.0f / 0.7f));
+      de -= kWHBond * (1.0f / 0.7f);
+    }
+  }
+}
+
+__device__ __forceinline__ int pair_bits(int ti, int tj) {
+  const int a = c_xs_bits[ti], b = c_xs_bits[tj];
+  int bits = (a & b & 1);
+  if (((a & 2) && (b & 4)) || ((a & 4) && (b & 2))) bits |= 2;
+  return bits;
+}
+
+// FP64 version for the rescoring (same terms; exp in double).
+__device__ __forceinline__ double vina_pair_f64(double d, int bits) {
+  const double a = 2.0 * d;
+  const double b = 0.5 * (d - 3.0);
+  double e = (double)kWGauss1 * exp(-a * a) + (double)kWGauss2 * exp(-b * b);
+  if (d < 0.0) e += (double)kWRepulsion * d * d;
+  if (bits & 1) {
+    if (d < 0.5) e += (double)kWHydrophobic;
+    else if (d < 1.5) e += (double)kWHydrophobic * (1.5 - d);
+  }
+  if (bits & 2) {
+    if (d < -0.7) e += (double)kWHBond;
+    else if (d < 0.0) e += (double)kWHBond * (-d / 0.7);
+  }
+  return e;
+}
+
+// ------------------------------------------------------------------ map formats
+// FMT encodes (dtype, mode): 0 F32 EQ4, 1 BF16 EQ4, 2 F16 EQ4, 3 F32 EQ3,
+// 4 BF16 EQ3, 5 F16 EQ3.
+__host__ __device__ constexpr int map_fmt(int dtype, int mode) { return mode * 3 + dtype; }
+__host__ __device__ constexpr int fmt_channels(int fmt) { return fmt < 3 ? 4 : 1; }
+__host__ __device__ constexpr int fmt_elem_bytes(int fmt) { return (fmt % 3 == 0) ? 4 : 2; }
+
+template <int FMT>
+__device__ __forceinline__ float4 load_node(const void* maps, size_t idx) {
+  if (FMT == 0) {
+    return __ldg(reinterpret_cast<const float4*>(maps) + idx);
+  } else if (FMT == 1 || FMT == 2) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(maps) + idx);
+    if (FMT == 1) {
+      const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+      const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+      const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+      return make_float4(fa.x, fa.y, fb.x, fb.y);
+    } else {
+      const __half2 a = *reinterpret_cast<const __half2*>(&raw.x);
+      const __half2 b = *reinterpret_cast<const __half2*>(&raw.y);
+      const float2 fa = __half22float2(a), fb = __half22float2(b);
+      return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+  } else if (FMT == 3) {
+    return make_float4(__ldg(reinterpret_cast<const float*>(maps) + idx), 0.f, 0.f, 0.f);
+  } else {
+    const unsigned short raw = __ldg(reinterpret_cast<const unsigned short*>(maps) + idx);
+    float v;
+    if (FMT == 4) v = __bfloat162float(__ushort_as_bfloat16(raw));
+    else v = __half2float(__ushort_as_half(raw));
+    return make_float4(v, 0.f, 0.f, 0.f);
+  }
+}
+
+struct MapView {
+  const void* maps;
+  int nx, ny, nz;
+  float ox, oy, oz;
+  float h, inv_h;
+};
+
+// Trilinear score (Eq. 2) and gradient (Eq. 4 from the gradient maps, or
+// Eq. 3 as the derivative of the interpolant) at r for map type t, with the
+// out-of-grid wall: evaluated at the clamped point plus kWallSlope per
+// Angstrom of excess along each axis; along such an axis the gradient is the
+// wall slope.
+template <int FMT>
+__device__ __forceinline__ float sample_map(const MapView& M, int t, float3 r, float3& g) {
+  const float ux = (r.x - M.ox) * M.inv_h, uy = (r.y - M.oy) * M.inv_h, uz = (r.z - M.oz) * M.inv_h;
+  const float cx = fminf(fmaxf(ux, 0.f), (float)(M.nx - 1));
+  const float cy = fminf(fmaxf(uy, 0.f), (float)(M.ny - 1));
+  const float cz = fminf(fmaxf(uz, 0.f), (float)(M.nz - 1));
+  const int ix = min((int)cx, M.nx - 2), iy = min((int)cy, M.ny - 2), iz = min((int)cz, M.nz - 2);
+  const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
+  const size_t sxy = (size_t)M.nx * M.ny;
+  const size_t base = (size_t)t * sxy * M.nz + (size_t)iz * sxy + (size_t)iy * M.nx + ix;
+  const float4 v000 = load_node<FMT>(M.maps, base);
+  const float4 v100 = load_node<FMT>(M.maps, base + 1);
+  const float4 v010 = load_node<FMT>(M.maps, base + M.nx);
+  const float4 v110 = load_node<FMT>(M.maps, base + M.nx + 1);
+  const float4 v001 = load_node<FMT>(M.maps, base + sxy);
+  const float4 v101 = load_node<FMT>(M.maps, base + sxy + 1);
+  const float4 v011 = load_node<FMT>(M.maps, base + sxy + M.nx);
+  const float4 v111 = load_node<FMT>(M.maps, base + sxy + M.nx + 1);
+  const float gx0 = 1.f - fx, gy0 = 1.f - fy, gz0 = 1.f - fz;
+  const float w000 = gx0 * gy0 * gz0, w100 = fx * gy0 * gz0, w010 = gx0 * fy * gz0, w110 = fx * fy * gz0;
+  const float w001 = gx0 * gy0 * fz, w101 = fx * gy0 * fz, w011 = gx0 * fy * fz, w111 = fx * fy * fz;
+  float e = w000 * v000.x + w100 * v100.x + w010 * v010.x + w110 * v110.x + w001 * v001.x + w101 * v101.x +
+            w011 * v011.x + w111 * v111.x;
+  if (fmt_channels(FMT) == 4) {
+    g.x = w000 * v000.y + w100 * v100.y + w010 * v010.y + w110 * v110.y + w001 * v001.y + w101 * v101.y +
+          w011 * v011.y + w111 * v111.y;
+    g.y = w000 * v000.z + w100 * v100.z + w010 * v010.z + w110 * v110.z + w001 * v001.z + w101 * v101.z +
+          w011 * v011.z + w111 * v111.z;
+    g.z = w000 * v000.w + w100 * v100.w + w010 * v010.w + w110 * v110.w + w001 * v001.w + w101 * v101.w +
+          w011 * v011.w + w111 * v111.w;
+  } else {
+    // d/dx of the trilinear interpolant: difference of the x = 1 and x = 0 faces / h
+    const float f0 = gy0 * gz0 * v000.x + fy * gz0 * v010.x + gy0 * fz * v001.x + fy * fz * v011.x;
+    const float f1 = gy0 * gz0 * v100.x + fy * gz0 * v110.x + gy0 * fz * v101.x + fy * fz * v111.x;
+    const float e0 = gx0 * gz0 * v000.x + fx * gz0 * v100.x + gx0 * fz * v001.x + fx * fz * v101.x;
+    const float e1 = gx0 * gz0 * v010.x + fx * gz0 * v110.x + gx0 * fz * v011.x + fx * fz * v111.x;
+    const float d0 = gx0 * gy0 * v000.x + fx * gy0 * v100.x + gx0 * fy * v010.x + fx * fy * v110.x;
+    const float d1 = gx0 * gy0 * v001.x + fx * gy0 * v101.x + gx0 * fy * v011.x + fx * fy * v111.x;
+    g.x = (f1 - f0) * M.inv_h;
+    g.y = (e1 - e0) * M.inv_h;
+    g.z = (d1 - d0) * M.inv_h;
+  }
+  const float ex = (ux - cx) * M.h, ey = (uy - cy) * M.h, ez = (uz - cz) * M.h;
+  if (ex != 0.f) {
+    e += kWallSlope * fabsf(ex);
+    g.x = ex > 0.f ? kWallSlope : -kWallSlope;
+  }
+  if (ey != 0.f) {
+    e += kWallSlope * fabsf(ey);
+    g.y = ey > 0.f ? kWallSlope : -kWallSlope;
+  }
+  if (ez != 0.f) {
+    e += kWallSlope * fabsf(ez);
+    g.z = ez > 0.f ? kWallSlope : -kWallSlope;
+  }
+  return e;
+}
+
+__host__ __device__ inline MapView make_map_view(const DevJob& J) {
+  MapView M;
+  M.maps = J.maps;
+  M.nx = J.n[0];
+  M.ny = J.n[1];
+  M.nz = J.n[2];
+  M.ox = J.origin[0];
+  M.oy = J.origin[1];
+  M.oz = J.origin[2];
+  M.h = J.spacing;
+  M.inv_h = J.inv_spacing;
+  return M;
+}
+
+}  // namespace dsdp

@@ -1,0 +1,136 @@
+// Chain and scoring kernels, instantiated once per map format by the
+// dock_fmt*.cu translation units (compiled in parallel).
+#pragma once
+#include "chain_device.cuh"
+#include "launch.h"
+
+namespace dsdp {
+
+// Bytes of per-warp shared scratch for a ligand with n_pairs pairs.
+__host__ __device__ inline int warp_scratch_bytes(int n_pairs) {
+  return 16 * kMaxAtoms + ((4 * n_pairs + 15) & ~15);
+}
+
+// Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
+// The job's ligand blob is staged into shared memory once per tile.
+// persistent != 0: CTAs pull tiles from *tile_counter until none are left.
+template <int APL, int FMT>
+__global__ void __launch_bounds__(256) dock_chains_kernel(const DevJob* __restrict__ jobs,
+                                                          const Tile* __restrict__ tiles, int n_tiles,
+                                                          int* tile_counter, int persistent, int blob_smem,
+                                                          int warp_smem) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int s_tile;
+  __shared__ int s_job;
+  const int warp = threadIdx.x >> 5;
+  WarpScratch W;
+  W.coords = reinterpret_cast<float4*>(smem + blob_smem + warp * warp_smem);
+  W.pair_s = reinterpret_cast<float*>(smem + blob_smem + warp * warp_smem + 16 * kMaxAtoms);
+  if (threadIdx.x == 0) s_job = -1;
+  __syncthreads();
+  int t = blockIdx.x;
+  for (;;) {
+    if (persistent) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
+      __syncthreads();
+      t = s_tile;
+    }
+    if (t >= n_tiles) break;
+    const Tile tile = tiles[t];
+    const DevJob& J = jobs[tile.job];
+    if (s_job != tile.job) {  // uniform: s_job only changes between barriers
+      __syncthreads();
+      const int words = reinterpret_cast<const BlobHeader*>(J.blob)->bytes / 16;
+      for (int i = threadIdx.x; i < words; i += blockDim.x)
+        reinterpret_cast<int4*>(smem)[i] = __ldg(reinterpret_cast<const int4*>(J.blob) + i);
+      __syncthreads();
+      if (threadIdx.x == 0) s_job = tile.job;
+      __syncthreads();
+    }
+    const LigView L = view_blob(smem);
+    if (warp < tile.count) run_chain<APL, FMT>(J, L, W, tile.chain0 + warp);
+    if (!persistent) break;
+  }
+}
+
+// Score + gradient of a batch of conformations: one warp per conformation.
+template <int APL, int FMT>
+__global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_t* __restrict__ blob,
+                                                         const float* __restrict__ conf, int n_conf,
+                                                         float* __restrict__ energy, float* __restrict__ grad,
+                                                         uint32_t flags, int blob_smem, int warp_smem) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int words = reinterpret_cast<const BlobHeader*>(blob)->bytes / 16;
+  for (int i = threadIdx.x; i < words; i += blockDim.x)
+    reinterpret_cast<int4*>(smem)[i] = __ldg(reinterpret_cast<const int4*>(blob) + i);
+  __syncthreads();
+  const LigView L = view_blob(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpScratch W;
+  W.coords = reinterpret_cast<float4*>(smem + blob_smem + warp * warp_smem);
+  W.pair_s = reinterpret_cast<float*>(smem + blob_smem + warp * warp_smem + 16 * kMaxAtoms);
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= n_conf) return;
+  LaneLig<APL> R;
+  load_lane_lig<APL>(L, R);
+  const int T = L.T;
+  Conf x = load_conf(conf + (size_t)c * (7 + T), T);
+  x.q = qnormalize(x.q);
+  float g;
+  const float e = eval_conf<APL, FMT>(M, L, R, W, x, g, flags);
+  if (lane == 0 && energy) energy[c] = e;
+  if (grad && lane < 6 + T) grad[(size_t)c * (6 + T) + lane] = g;
+}
+
+template <int FMT>
+cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
+  const dim3 block(32 * a.warps_per_cta);
+  const size_t smem = (size_t)a.blob_smem + (size_t)a.warps_per_cta * a.warp_smem;
+  const DevJob* jobs = reinterpret_cast<const DevJob*>(a.jobs);
+  const Tile* tiles = reinterpret_cast<const Tile*>(a.tiles);
+  if (a.apl == 1) {
+    auto k = dock_chains_kernel<1, FMT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<a.grid, block, smem, st>>>(jobs, tiles, a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.warp_smem);
+  } else {
+    auto k = dock_chains_kernel<2, FMT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<a.grid, block, smem, st>>>(jobs, tiles, a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.warp_smem);
+  }
+  return cudaGetLastError();
+}
+
+template <int FMT>
+cudaError_t launch_score_impl(const ScoreLaunch& a, cudaStream_t st) {
+  const int wpc = 4;
+  const dim3 block(32 * wpc), grid((a.n_conf + wpc - 1) / wpc);
+  const size_t smem = (size_t)a.blob_smem + (size_t)wpc * a.warp_smem;
+  const MapView M = a.map;
+  if (a.apl == 1) {
+    auto k = score_eval_kernel<1, FMT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(M, a.blob, a.conf, a.n_conf, a.energy, a.grad, a.flags, a.blob_smem, a.warp_smem);
+  } else {
+    auto k = score_eval_kernel<2, FMT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(M, a.blob, a.conf, a.n_conf, a.energy, a.grad, a.flags, a.blob_smem, a.warp_smem);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dsdp
+
+#define DSDP_INSTANTIATE_FMT(F)                                                                   \
+  namespace dsdp {                                                                                \
+  cudaError_t launch_chains_fmt##F(const ChainLaunch& a, cudaStream_t st) {                       \
+    return launch_chains_impl<F>(a, st);                                                          \
+  }                                                                                               \
+  cudaError_t launch_score_fmt##F(const ScoreLaunch& a, cudaStream_t st) {                        \
+    return launch_score_impl<F>(a, st);                                                           \
+  }                                                                                               \
+  }

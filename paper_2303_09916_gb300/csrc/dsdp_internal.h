@@ -1,0 +1,139 @@
+// Internal layouts shared by the host code and the kernels of libdsdp.
+#pragma once
+#include <stdint.h>
+
+#include "../../include/dsdp.h"
+
+namespace dsdp {
+
+constexpr uint32_t kBlobMagic = 0x50445344u;  // "DSDP"
+constexpr int kMaxAtoms = DSDP_MAX_LIGAND_ATOMS;
+constexpr int kMaxBodies = DSDP_MAX_TORSIONS + 1;
+constexpr int kMaxDim = 6 + DSDP_MAX_TORSIONS;  // gradient / step dimension
+constexpr int kMaxPairs = kMaxAtoms * (kMaxAtoms - 1) / 2;
+
+// Packed ligand (dsdp_ligand_pack).  Internal atom order: rigid bodies in
+// depth-first pre-order from the root (children by torsion index), atoms of a
+// body in ascending input index.  Every subtree is then one contiguous atom
+// range, which the kernels use for the torsion gradients.
+struct BlobHeader {
+  uint32_t magic;
+  uint32_t bytes;          // whole blob, multiple of 16
+  int32_t n_atoms;
+  int32_t n_torsions;
+  int32_t n_bodies;
+  int32_t n_pairs;
+  int32_t rounds;          // pointer-jumping rounds: ceil(log2(max depth + 1))
+  float gyration_radius;   // of the reference pose about the root origin atom
+  float root_ref[3];       // input coordinates of the root origin atom
+  int32_t root_user_atom;
+  uint32_t off_atom;       // float4[n_atoms]: local xyz (reference frame, relative to the body origin);
+                           //   w = int bits: map type | body << 8
+  uint32_t off_atom_user;  // int32[n_atoms]: input index of internal atom i
+  uint32_t off_body;       // BodyRec[n_bodies]
+  uint32_t off_pairs;      // uint32[n_pairs]: i | j << 8 | (type_i * 8 + type_j) << 16 (internal indices)
+  uint32_t off_csr_start;  // uint16[n_atoms + 1]
+  uint32_t off_csr;        // uint32[2 n_pairs]: pair index | partner << 16
+  uint32_t off_torsion_body;  // int32[n_torsions]: body driven by torsion k
+  uint32_t off_atom64;     // double[n_atoms][3]: local xyz in FP64 (rescoring)
+  uint32_t off_body64;     // double[n_bodies][6]: origin offset and unit axis in FP64 (rescoring)
+  int32_t pad[3];
+};
+static_assert(sizeof(BlobHeader) % 16 == 0, "blob header alignment");
+
+struct BodyRec {
+  float off[3];       // origin minus parent origin, reference frame
+  int32_t parent;     // -1 for the root
+  float axis[3];      // unit torsion axis (parent-side atom -> child-side atom), reference frame
+  int32_t torsion;    // torsion index, -1 for the root
+  int32_t atom_begin; // subtree atoms [atom_begin, atom_end)
+  int32_t atom_end;
+  int32_t depth;
+  int32_t pad;
+};
+static_assert(sizeof(BodyRec) == 48, "body record size");
+
+// One job as the kernels see it.
+struct DevJob {
+  const uint8_t* blob;
+  const void* maps;
+  int32_t n[3];
+  float origin[3];
+  float spacing;
+  float inv_spacing;
+  int32_t dtype;
+  int32_t mode;
+  int32_t n_chains;
+  int32_t n_steps;
+  int32_t n_opt_iters;
+  int32_t optimizer;
+  float temperature;
+  uint32_t seed_lo, seed_hi;
+  float box_lo[3];
+  float box_size[3];
+  float* chain_best_conf;
+  float* chain_best_e;
+  uint32_t* chain_evals;
+  float* trace;
+  // rescoring
+  int32_t n_rec;
+  const float* rec_xyz;
+  const uint8_t* rec_type;
+  double* chain_score;   // scratch [n_chains]
+  double* chain_inter;   // scratch [n_chains]
+  double* chain_intra;   // scratch [n_chains]
+  double* chain_coords;  // scratch [n_chains][n_atoms][3] (internal atom order)
+  int32_t top_k;
+  float rmsd_dedup;
+  int32_t* out_n;
+  int32_t* out_chain;
+  double* out_score;
+  double* out_inter;
+  double* out_intra;
+  double* out_conf;
+  float* out_coords;
+};
+
+struct Tile {
+  int32_t job;
+  int32_t chain0;
+  int32_t count;
+  int32_t pad;
+};
+
+// Vina constants of the kernels (the scoring function DSDP keeps, Sec. 2).
+constexpr float kWGauss1 = -0.0356f;
+constexpr float kWGauss2 = -0.00516f;
+constexpr float kWRepulsion = 0.840f;
+constexpr float kWHydrophobic = -0.0351f;
+constexpr float kWHBond = -0.587f;
+constexpr double kWRot = 0.0585;
+constexpr float kCutoff = 8.0f;
+constexpr float kWallSlope = 10.0f;
+
+// Optimiser constants (BFGS: Armijo backtracking; BB: BB1 step with clamps).
+constexpr float kArmijoC1 = 1e-4f;
+constexpr float kShrink = 0.5f;
+constexpr int kMaxTrials = 10;
+constexpr float kMinCurvature = 1e-10f;
+constexpr float kBBAlpha0 = 1e-3f;
+constexpr float kBBAlphaMin = 1e-4f;
+constexpr float kBBAlphaMax = 0.1f;
+constexpr float kMutationAmplitude = 2.0f;
+
+}  // namespace dsdp
+
+// Host-side helpers implemented in the library's .cpp / .cu files.
+namespace dsdp {
+dsdp_status set_error(dsdp_status s, const char* fmt, ...);
+const char* last_error();
+dsdp_status check_cuda(int err, const char* what);
+void grid_geometry(const dsdp_box* box, int n[3], double origin[3]);
+dsdp_status validate_box(const dsdp_box* box);
+// dock parameters with the documented defaults filled in; INVALID_ARG if out of range
+dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out);
+// context allocator (ctx may be NULL: plain cudaMalloc / cudaFree)
+void* ctx_alloc(dsdp_ctx* ctx, size_t bytes, void* stream);
+void ctx_free(dsdp_ctx* ctx, void* p, size_t bytes, void* stream);
+int ctx_sm_count(dsdp_ctx* ctx);
+}  // namespace dsdp

@@ -1,0 +1,330 @@
+// Device-resident entry points of the C ABI: scoring a batch of
+// conformations, and docking plans (chain kernels, FP64 rescoring, top-k)
+// that can be enqueued repeatedly or captured into CUDA graphs.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "launch.h"
+
+struct dsdp_plan {
+  dsdp_ctx* ctx = nullptr;
+  int n_jobs = 0;
+  uint32_t flags = 0;
+  int warps_per_cta = 2;
+  int max_chains = 0;
+  // one device arena holding job table, tiles, counters and scratch
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  struct Group {
+    int fmt, apl, first_tile, n_tiles, blob_smem, warp_smem;
+  };
+  std::vector<Group> groups;
+  void* d_jobs = nullptr;
+  void* d_tiles = nullptr;
+  void* d_rtiles = nullptr;
+  int* d_counters = nullptr;
+  int n_rtiles = 0;
+  int sms = 148;
+};
+
+namespace dsdp {
+
+int warp_scratch_bytes_host(int n_pairs) { return 16 * kMaxAtoms + ((4 * n_pairs + 15) & ~15); }
+
+dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) {
+  if (!in) return set_error(DSDP_ERR_INVALID_ARG, "dock params NULL");
+  *out = *in;
+  if (out->n_chains == 0) out->n_chains = 384;
+  if (out->n_mc_steps == 0) out->n_mc_steps = 40;
+  if (out->n_opt_iters == 0) out->n_opt_iters = 100;
+  if (out->temperature == 0.0) out->temperature = 1.2;
+  if (out->top_k == 0) out->top_k = 9;
+  if (out->rmsd_dedup == 0.0) out->rmsd_dedup = 1.0;
+  if (out->n_chains < 1 || out->n_chains > DSDP_MAX_CHAINS)
+    return set_error(DSDP_ERR_INVALID_ARG, "n_chains %d outside 1..%d", out->n_chains, DSDP_MAX_CHAINS);
+  if (out->n_mc_steps < 0 || out->n_mc_steps > 100000) return set_error(DSDP_ERR_INVALID_ARG, "n_mc_steps out of range");
+  if (out->n_opt_iters < 0 || out->n_opt_iters > 100000)
+    return set_error(DSDP_ERR_INVALID_ARG, "n_opt_iters out of range");
+  if (out->optimizer != DSDP_OPT_BFGS && out->optimizer != DSDP_OPT_BB)
+    return set_error(DSDP_ERR_INVALID_ARG, "unknown optimizer %d", out->optimizer);
+  if (!(out->temperature > 0.0)) return set_error(DSDP_ERR_INVALID_ARG, "temperature must be positive");
+  if (out->top_k < 1 || out->top_k > DSDP_MAX_TOP_K)
+    return set_error(DSDP_ERR_INVALID_ARG, "top_k %d outside 1..%d", out->top_k, DSDP_MAX_TOP_K);
+  if (!(out->rmsd_dedup >= 0.0)) return set_error(DSDP_ERR_INVALID_ARG, "rmsd_dedup must be >= 0");
+  return DSDP_OK;
+}
+
+static cudaError_t launch_chains_dispatch(int fmt, const ChainLaunch& a, cudaStream_t st) {
+  switch (fmt) {
+    case 0: return launch_chains_fmt0(a, st);
+    case 1: return launch_chains_fmt1(a, st);
+    case 2: return launch_chains_fmt2(a, st);
+    case 3: return launch_chains_fmt3(a, st);
+    case 4: return launch_chains_fmt4(a, st);
+    default: return launch_chains_fmt5(a, st);
+  }
+}
+
+static cudaError_t launch_score_dispatch(int fmt, const ScoreLaunch& a, cudaStream_t st) {
+  switch (fmt) {
+    case 0: return launch_score_fmt0(a, st);
+    case 1: return launch_score_fmt1(a, st);
+    case 2: return launch_score_fmt2(a, st);
+    case 3: return launch_score_fmt3(a, st);
+    case 4: return launch_score_fmt4(a, st);
+    default: return launch_score_fmt5(a, st);
+  }
+}
+
+static dsdp_status check_view(const dsdp_grid_view* g) {
+  if (!g || !g->d_maps) return set_error(DSDP_ERR_INVALID_ARG, "grid view or maps NULL");
+  if (g->dtype < 0 || g->dtype > 2 || g->mode < 0 || g->mode > 1)
+    return set_error(DSDP_ERR_INVALID_ARG, "grid view dtype/mode invalid");
+  for (int a = 0; a < 3; ++a)
+    if (g->n[a] < 2) return set_error(DSDP_ERR_INVALID_ARG, "grid needs >= 2 vertices per axis");
+  if (!(g->spacing > 0.0)) return set_error(DSDP_ERR_INVALID_ARG, "grid spacing must be positive");
+  return DSDP_OK;
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace dsdp
+
+using namespace dsdp;
+
+extern "C" dsdp_status dsdp_score_eval_device(const dsdp_grid_view* grid, const void* h_blob, const void* d_blob,
+                                              const float* d_conf, int32_t n_conf, float* d_energy, float* d_grad,
+                                              uint32_t flags, void* stream) {
+  dsdp_status s = check_view(grid);
+  if (s != DSDP_OK) return s;
+  int32_t n_atoms = 0, T = 0, P = 0, B = 0;
+  s = dsdp_ligand_blob_info(h_blob, &n_atoms, &T, &P, &B);
+  if (s != DSDP_OK) return s;
+  if (!d_blob || !d_conf || n_conf < 0) return set_error(DSDP_ERR_INVALID_ARG, "score_eval_device arguments");
+  if (n_conf == 0) return DSDP_OK;
+  if ((flags & DSDP_TERM_ALL) == 0 || (flags & ~(uint32_t)DSDP_TERM_ALL))
+    return set_error(DSDP_ERR_INVALID_ARG, "flags must select DSDP_TERM_INTER and/or DSDP_TERM_INTRA");
+  ScoreLaunch a;
+  a.map = map_view_of(grid);
+  a.blob = (const uint8_t*)d_blob;
+  a.conf = d_conf;
+  a.n_conf = n_conf;
+  a.energy = d_energy;
+  a.grad = d_grad;
+  a.flags = flags;
+  a.apl = n_atoms <= 32 ? 1 : 2;
+  a.blob_smem = (int)((const BlobHeader*)h_blob)->bytes;
+  a.warp_smem = warp_scratch_bytes_host(P);
+  return check_cuda(launch_score_dispatch(map_fmt(grid->dtype, grid->mode), a, (cudaStream_t)stream),
+                    "score_eval_kernel launch");
+}
+
+extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
+                                        int32_t warps_per_cta, dsdp_plan** out) {
+  if (!out) return set_error(DSDP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_jobs < 1 || !jobs) return set_error(DSDP_ERR_INVALID_ARG, "plan needs >= 1 job");
+  if (warps_per_cta < 0 || warps_per_cta > 8) return set_error(DSDP_ERR_INVALID_ARG, "warps_per_cta outside 0..8");
+  std::vector<DevJob> dj(n_jobs);
+  std::vector<int> fmt(n_jobs), apl(n_jobs), blob_bytes(n_jobs), pairs(n_jobs), atoms(n_jobs), tors(n_jobs);
+  size_t scratch = 0;
+  int max_chains = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const dsdp_job_device& J = jobs[j];
+    dsdp_status s = check_view(&J.grid);
+    if (s != DSDP_OK) return s;
+    s = dsdp_ligand_blob_info(J.h_blob, &atoms[j], &tors[j], &pairs[j], nullptr);
+    if (s != DSDP_OK) return s;
+    if (!J.d_blob) return set_error(DSDP_ERR_INVALID_ARG, "job %d: d_blob NULL", j);
+    dsdp_dock_params p;
+    s = normalize_params(&J.params, &p);
+    if (s != DSDP_OK) return s;
+    if (!(flags & DSDP_PLAN_NO_RESCORE) && (J.receptor.n < 1 || !J.receptor.xyz || !J.receptor.xs_type))
+      return set_error(DSDP_ERR_INVALID_ARG, "job %d: rescoring needs the receptor's device arrays", j);
+    for (int a = 0; a < 3; ++a)
+      if (!(J.box_size[a] >= 0.0) || !isfinite(J.box_lo[a]))
+        return set_error(DSDP_ERR_INVALID_ARG, "job %d: search box invalid", j);
+    if (p.trace && !J.d_trace) return set_error(DSDP_ERR_INVALID_ARG, "job %d: trace requested without d_trace", j);
+    fmt[j] = map_fmt(J.grid.dtype, J.grid.mode);
+    apl[j] = atoms[j] <= 32 ? 1 : 2;
+    blob_bytes[j] = (int)((const BlobHeader*)J.h_blob)->bytes;
+    max_chains = std::max(max_chains, p.n_chains);
+    const int nx = 7 + tors[j];
+    if (!J.d_chain_best_conf) scratch += up256(sizeof(float) * (size_t)p.n_chains * nx);
+    if (!J.d_chain_best_e) scratch += up256(sizeof(float) * (size_t)p.n_chains);
+    if (!J.d_chain_evals) scratch += up256(sizeof(uint32_t) * (size_t)p.n_chains);
+    scratch += 3 * up256(sizeof(double) * (size_t)p.n_chains);
+    scratch += up256(sizeof(double) * (size_t)p.n_chains * atoms[j] * 3);
+    DevJob& d = dj[j];
+    memset(&d, 0, sizeof(d));
+    d.blob = (const uint8_t*)J.d_blob;
+    d.maps = J.grid.d_maps;
+    for (int a = 0; a < 3; ++a) {
+      d.n[a] = J.grid.n[a];
+      d.origin[a] = (float)J.grid.origin[a];
+      d.box_lo[a] = (float)J.box_lo[a];
+      d.box_size[a] = (float)J.box_size[a];
+    }
+    d.spacing = (float)J.grid.spacing;
+    d.inv_spacing = (float)(1.0 / J.grid.spacing);
+    d.dtype = J.grid.dtype;
+    d.mode = J.grid.mode;
+    d.n_chains = p.n_chains;
+    d.n_steps = p.n_mc_steps;
+    d.n_opt_iters = p.n_opt_iters;
+    d.optimizer = p.optimizer;
+    d.temperature = (float)p.temperature;
+    d.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
+    d.seed_hi = (uint32_t)(p.seed >> 32);
+    d.chain_best_conf = J.d_chain_best_conf;
+    d.chain_best_e = J.d_chain_best_e;
+    d.chain_evals = J.d_chain_evals;
+    d.trace = p.trace ? J.d_trace : nullptr;
+    d.n_rec = J.receptor.n;
+    d.rec_xyz = J.receptor.xyz;
+    d.rec_type = J.receptor.xs_type;
+    d.top_k = p.top_k;
+    d.rmsd_dedup = (float)p.rmsd_dedup;
+    d.out_n = J.d_out_n;
+    d.out_chain = J.d_out_chain;
+    d.out_score = J.d_out_score;
+    d.out_inter = J.d_out_inter;
+    d.out_intra = J.d_out_intra;
+    d.out_conf = J.d_out_conf;
+    d.out_coords = J.d_out_coords;
+  }
+  dsdp_plan* P = new dsdp_plan();
+  P->ctx = ctx;
+  P->n_jobs = n_jobs;
+  P->flags = flags;
+  P->max_chains = max_chains;
+  P->sms = ctx_sm_count(ctx);
+  int W = warps_per_cta;
+  if (W == 0) {
+    size_t total = 0;
+    for (int j = 0; j < n_jobs; ++j) total += dj[j].n_chains;
+    W = total <= (size_t)P->sms * 2 ? 1 : (total <= (size_t)P->sms * 8 ? 2 : 4);
+  }
+  P->warps_per_cta = W;
+  // chain tiles grouped by map format (one launch per format present)
+  std::vector<Tile> tiles;
+  for (int f = 0; f < 6; ++f) {
+    dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0};
+    for (int j = 0; j < n_jobs; ++j) {
+      if (fmt[j] != f) continue;
+      g.apl = std::max(g.apl, apl[j]);
+      g.blob_smem = std::max(g.blob_smem, blob_bytes[j]);
+      g.warp_smem = std::max(g.warp_smem, warp_scratch_bytes_host(pairs[j]));
+      for (int c = 0; c < dj[j].n_chains; c += W) tiles.push_back(Tile{j, c, std::min(W, dj[j].n_chains - c), 0});
+    }
+    g.n_tiles = (int)tiles.size() - g.first_tile;
+    if (g.n_tiles > 0) P->groups.push_back(g);
+  }
+  std::vector<Tile> rtiles;
+  const int rw = rescore_tile_chains();
+  for (int j = 0; j < n_jobs; ++j)
+    for (int c = 0; c < dj[j].n_chains; c += rw) rtiles.push_back(Tile{j, c, std::min(rw, dj[j].n_chains - c), 0});
+  P->n_rtiles = (int)rtiles.size();
+  const size_t b_jobs = up256(sizeof(DevJob) * n_jobs), b_tiles = up256(sizeof(Tile) * tiles.size()),
+               b_rtiles = up256(sizeof(Tile) * rtiles.size()), b_cnt = up256(sizeof(int) * 8);
+  P->arena_bytes = b_jobs + b_tiles + b_rtiles + b_cnt + scratch;
+  P->arena = ctx_alloc(ctx, P->arena_bytes, nullptr);
+  if (!P->arena) {
+    delete P;
+    return set_error(DSDP_ERR_OUT_OF_MEMORY, "plan arena of %zu bytes", (size_t)(b_jobs + b_tiles + b_rtiles + scratch));
+  }
+  uint8_t* a = (uint8_t*)P->arena;
+  P->d_jobs = a;
+  P->d_tiles = a + b_jobs;
+  P->d_rtiles = a + b_jobs + b_tiles;
+  P->d_counters = (int*)(a + b_jobs + b_tiles + b_rtiles);
+  uint8_t* sc = a + b_jobs + b_tiles + b_rtiles + b_cnt;
+  for (int j = 0; j < n_jobs; ++j) {
+    DevJob& d = dj[j];
+    const int nx = 7 + tors[j];
+    auto take = [&](size_t bytes) {
+      uint8_t* p = sc;
+      sc += up256(bytes);
+      return p;
+    };
+    if (!d.chain_best_conf) d.chain_best_conf = (float*)take(sizeof(float) * (size_t)d.n_chains * nx);
+    if (!d.chain_best_e) d.chain_best_e = (float*)take(sizeof(float) * (size_t)d.n_chains);
+    if (!d.chain_evals) d.chain_evals = (uint32_t*)take(sizeof(uint32_t) * (size_t)d.n_chains);
+    d.chain_score = (double*)take(sizeof(double) * (size_t)d.n_chains);
+    d.chain_inter = (double*)take(sizeof(double) * (size_t)d.n_chains);
+    d.chain_intra = (double*)take(sizeof(double) * (size_t)d.n_chains);
+    d.chain_coords = (double*)take(sizeof(double) * (size_t)d.n_chains * atoms[j] * 3);
+  }
+  cudaError_t e = cudaMemcpy(P->d_jobs, dj.data(), sizeof(DevJob) * n_jobs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpy(P->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !rtiles.empty())
+    e = cudaMemcpy(P->d_rtiles, rtiles.data(), sizeof(Tile) * rtiles.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ctx_free(ctx, P->arena, P->arena_bytes, nullptr);
+    delete P;
+    return check_cuda(e, "plan upload");
+  }
+  *out = P;
+  return DSDP_OK;
+}
+
+extern "C" int32_t dsdp_plan_kernel_count(const dsdp_plan* P) {
+  if (!P) return 0;
+  int n = (int)P->groups.size();
+  if (!(P->flags & DSDP_PLAN_NO_RESCORE)) n += 2;
+  return n;
+}
+
+extern "C" dsdp_status dsdp_plan_launch_stage(dsdp_plan* P, uint32_t stages, void* stream) {
+  if (!P) return set_error(DSDP_ERR_INVALID_ARG, "plan is NULL");
+  if (stages == 0 || (stages & ~(uint32_t)DSDP_STAGE_ALL)) return set_error(DSDP_ERR_INVALID_ARG, "bad stages");
+  const cudaStream_t st = (cudaStream_t)stream;
+  const bool persistent = (P->flags & DSDP_PLAN_PERSISTENT) != 0;
+  if ((stages & DSDP_STAGE_CHAINS) && persistent) {
+    cudaError_t e = cudaMemsetAsync(P->d_counters, 0, sizeof(int) * 8, st);
+    if (e != cudaSuccess) return check_cuda(e, "plan counter reset");
+  }
+  for (size_t gi = 0; (stages & DSDP_STAGE_CHAINS) && gi < P->groups.size(); ++gi) {
+    const dsdp_plan::Group& g = P->groups[gi];
+    ChainLaunch a;
+    a.jobs = P->d_jobs;
+    a.tiles = (const Tile*)P->d_tiles + g.first_tile;
+    a.n_tiles = g.n_tiles;
+    a.tile_counter = P->d_counters + gi;
+    a.persistent = persistent ? 1 : 0;
+    a.warps_per_cta = P->warps_per_cta;
+    a.apl = g.apl;
+    a.blob_smem = (g.blob_smem + 15) & ~15;
+    a.warp_smem = g.warp_smem;
+    if (persistent) {
+      int per_sm = 0;
+      per_sm = std::max(1, 8 / P->warps_per_cta);
+      a.grid = std::min(g.n_tiles, P->sms * per_sm);
+    } else {
+      a.grid = g.n_tiles;
+    }
+    cudaError_t e = launch_chains_dispatch(g.fmt, a, st);
+    if (e != cudaSuccess) return check_cuda(e, "dock_chains_kernel launch");
+  }
+  if ((stages & DSDP_STAGE_RESCORE) && !(P->flags & DSDP_PLAN_NO_RESCORE)) {
+    cudaError_t e = launch_rescore(P->d_jobs, P->d_rtiles, P->n_rtiles, st);
+    if (e != cudaSuccess) return check_cuda(e, "rescore_kernel launch");
+    e = launch_topk(P->d_jobs, P->n_jobs, P->max_chains, st);
+    if (e != cudaSuccess) return check_cuda(e, "topk_kernel launch");
+  }
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_plan_launch(dsdp_plan* P, void* stream) {
+  return dsdp_plan_launch_stage(P, DSDP_STAGE_ALL, stream);
+}
+
+extern "C" dsdp_status dsdp_plan_destroy(dsdp_ctx* ctx, dsdp_plan* P) {
+  if (!P) return DSDP_OK;
+  if (P->arena) ctx_free(ctx ? ctx : P->ctx, P->arena, P->arena_bytes, nullptr);
+  delete P;
+  return DSDP_OK;
+}

@@ -1,0 +1,354 @@
+// Ligand preparation on the host (the paper prepares the copies on the CPU,
+// Sec. 2 / Fig. 4): rigid bodies, torsion tree, internal atom order, intra
+// pair list, packed into one position-independent blob the kernels read.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dsdp_internal.h"
+
+namespace dsdp {
+
+static thread_local char g_last_error[512] = "";
+
+dsdp_status set_error(dsdp_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+const char* last_error() { return g_last_error; }
+
+namespace {
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct Prepared {
+  int n = 0, T = 0, B = 0, P = 0, rounds = 0, root_atom = 0;
+  float gyr = 1.0f;
+  std::vector<int> user_of;         // internal -> input index
+  std::vector<float> local;         // [n][3]
+  std::vector<double> local64;      // [n][3]
+  std::vector<double> body64;       // [B][6]: offset, axis
+  std::vector<int> type, body;      // per internal atom
+  std::vector<BodyRec> bodies;      // DFS pre-order
+  std::vector<uint32_t> pairs;
+  std::vector<uint16_t> csr_start;
+  std::vector<uint32_t> csr;
+  std::vector<int> torsion_body;
+  float root_ref[3];
+};
+
+dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
+  if (!L) return set_error(DSDP_ERR_INVALID_ARG, "ligand is NULL");
+  const int n = L->n_atoms;
+  if (n < 1 || n > kMaxAtoms) return set_error(DSDP_ERR_INVALID_ARG, "ligand n_atoms %d outside 1..%d", n, kMaxAtoms);
+  if (!L->xyz || !L->xs_type) return set_error(DSDP_ERR_INVALID_ARG, "ligand xyz/xs_type NULL");
+  if (L->n_bonds < 0 || (L->n_bonds > 0 && (!L->bonds || !L->rotatable)))
+    return set_error(DSDP_ERR_INVALID_ARG, "ligand bonds/rotatable NULL");
+  for (int i = 0; i < n; ++i) {
+    if (L->xs_type[i] >= DSDP_NUM_MAP_TYPES)
+      return set_error(DSDP_ERR_INVALID_ARG, "ligand atom %d has type %d; ligands use map types 0..7", i,
+                       (int)L->xs_type[i]);
+    for (int a = 0; a < 3; ++a)
+      if (!isfinite(L->xyz[3 * i + a])) return set_error(DSDP_ERR_INVALID_ARG, "ligand atom %d not finite", i);
+  }
+  std::vector<std::vector<int>> adj(n), rigid(n);
+  std::vector<int> rot_bonds;
+  for (int b = 0; b < L->n_bonds; ++b) {
+    const int i = L->bonds[2 * b], j = L->bonds[2 * b + 1];
+    if (i < 0 || j < 0 || i >= n || j >= n || i == j)
+      return set_error(DSDP_ERR_INVALID_ARG, "bond %d (%d, %d) invalid", b, i, j);
+    adj[i].push_back(j);
+    adj[j].push_back(i);
+    if (L->rotatable[b]) rot_bonds.push_back(b);
+    else {
+      rigid[i].push_back(j);
+      rigid[j].push_back(i);
+    }
+  }
+  const int T = (int)rot_bonds.size();
+  if (T > DSDP_MAX_TORSIONS) return set_error(DSDP_ERR_INVALID_ARG, "%d rotatable bonds > %d", T, DSDP_MAX_TORSIONS);
+  // bodies numbered by their lowest atom
+  std::vector<int> comp(n, -1);
+  int B = 0;
+  for (int s = 0; s < n; ++s) {
+    if (comp[s] >= 0) continue;
+    std::vector<int> st{s};
+    comp[s] = B;
+    while (!st.empty()) {
+      const int a = st.back();
+      st.pop_back();
+      for (int c : rigid[a])
+        if (comp[c] < 0) comp[c] = B, st.push_back(c);
+    }
+    ++B;
+  }
+  if (B != T + 1)
+    return set_error(DSDP_ERR_INVALID_ARG,
+                     "ligand must be one molecule whose rotatable bonds each split it (bodies %d, torsions %d)", B, T);
+  for (int k = 0; k < T; ++k) {
+    const int b = rot_bonds[k];
+    if (comp[L->bonds[2 * b]] == comp[L->bonds[2 * b + 1]])
+      return set_error(DSDP_ERR_INVALID_ARG, "rotatable bond %d lies in a ring", b);
+  }
+  std::vector<int> count(B, 0);
+  for (int i = 0; i < n; ++i) ++count[comp[i]];
+  int root = 0;
+  for (int b = 1; b < B; ++b)
+    if (count[b] > count[root]) root = b;
+  // body tree by BFS from the root
+  std::vector<int> parent(B, -2), origin(B, -1), near_atom(B, -1), tors(B, -1), depth(B, 0);
+  std::vector<std::vector<int>> children(B);
+  parent[root] = -1;
+  for (int i = 0; i < n; ++i)
+    if (comp[i] == root) {
+      origin[root] = i;
+      break;
+    }
+  std::vector<int> queue{root};
+  for (size_t qi = 0; qi < queue.size(); ++qi) {
+    const int b = queue[qi];
+    for (int k = 0; k < T; ++k) {
+      const int i = L->bonds[2 * rot_bonds[k]], j = L->bonds[2 * rot_bonds[k] + 1];
+      int nr = -1, fr = -1;
+      if (comp[i] == b) nr = i, fr = j;
+      else if (comp[j] == b) nr = j, fr = i;
+      if (nr < 0) continue;
+      const int c = comp[fr];
+      if (parent[c] != -2) continue;
+      parent[c] = b;
+      origin[c] = fr;
+      near_atom[c] = nr;
+      tors[c] = k;
+      depth[c] = depth[b] + 1;
+      children[b].push_back(c);
+      queue.push_back(c);
+    }
+  }
+  if ((int)queue.size() != B) return set_error(DSDP_ERR_INVALID_ARG, "ligand is not connected");
+  for (auto& ch : children) std::sort(ch.begin(), ch.end(), [&](int a, int b) { return tors[a] < tors[b]; });
+  // DFS pre-order of bodies
+  std::vector<int> dfs;
+  std::vector<int> st{root};
+  while (!st.empty()) {
+    const int b = st.back();
+    st.pop_back();
+    dfs.push_back(b);
+    for (int c = (int)children[b].size() - 1; c >= 0; --c) st.push_back(children[b][c]);
+  }
+  std::vector<int> new_body(B);
+  for (int i = 0; i < B; ++i) new_body[dfs[i]] = i;
+  // internal atom order
+  out.user_of.clear();
+  std::vector<int> body_first(B), internal_of(n);
+  for (int bi = 0; bi < B; ++bi) {
+    body_first[bi] = (int)out.user_of.size();
+    for (int i = 0; i < n; ++i)
+      if (comp[i] == dfs[bi]) {
+        internal_of[i] = (int)out.user_of.size();
+        out.user_of.push_back(i);
+      }
+  }
+  // subtree end = begin of the next body in pre-order that is not a descendant
+  std::vector<int> subtree_end(B, n);
+  for (int bi = 0; bi < B; ++bi) {
+    for (int bj = bi + 1; bj < B; ++bj) {
+      // bj is a descendant of bi iff bi is on bj's ancestor chain
+      int a = dfs[bj];
+      bool desc = false;
+      while (a >= 0) {
+        if (a == dfs[bi]) {
+          desc = true;
+          break;
+        }
+        a = parent[a];
+      }
+      if (!desc) {
+        subtree_end[bi] = body_first[bj];
+        break;
+      }
+    }
+  }
+  auto ref = [&](int i, int a) { return (double)L->xyz[3 * i + a]; };
+  out.bodies.assign(B, BodyRec{});
+  out.body64.assign(6 * (size_t)B, 0.0);
+  int max_depth = 0;
+  for (int bi = 0; bi < B; ++bi) {
+    const int b = dfs[bi];
+    BodyRec& r = out.bodies[bi];
+    r.parent = parent[b] < 0 ? -1 : new_body[parent[b]];
+    r.torsion = tors[b];
+    r.atom_begin = body_first[bi];
+    r.atom_end = subtree_end[bi];
+    r.depth = depth[b];
+    max_depth = std::max(max_depth, depth[b]);
+    if (parent[b] >= 0) {
+      double ax[3], len = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        r.off[a] = (float)(ref(origin[b], a) - ref(origin[parent[b]], a));
+        ax[a] = ref(origin[b], a) - ref(near_atom[b], a);
+        len += ax[a] * ax[a];
+      }
+      len = sqrt(len);
+      if (!(len > 1e-6)) return set_error(DSDP_ERR_INVALID_ARG, "rotatable bond %d has zero length", rot_bonds[tors[b]]);
+      for (int a = 0; a < 3; ++a) {
+        r.axis[a] = (float)(ax[a] / len);
+        out.body64[6 * bi + a] = ref(origin[b], a) - ref(origin[parent[b]], a);
+        out.body64[6 * bi + 3 + a] = ax[a] / len;
+      }
+    }
+  }
+  out.rounds = 0;
+  while ((1 << out.rounds) < max_depth + 1) ++out.rounds;
+  out.torsion_body.assign(T, 0);
+  for (int bi = 0; bi < B; ++bi)
+    if (out.bodies[bi].torsion >= 0) out.torsion_body[out.bodies[bi].torsion] = bi;
+  // atoms
+  out.local.assign(3 * n, 0.0f);
+  out.local64.assign(3 * n, 0.0);
+  out.type.assign(n, 0);
+  out.body.assign(n, 0);
+  for (int ii = 0; ii < n; ++ii) {
+    const int i = out.user_of[ii];
+    const int b = comp[i];
+    out.type[ii] = L->xs_type[i];
+    out.body[ii] = new_body[b];
+    for (int a = 0; a < 3; ++a) {
+      out.local64[3 * ii + a] = ref(i, a) - ref(origin[b], a);
+      out.local[3 * ii + a] = (float)out.local64[3 * ii + a];
+    }
+  }
+  // pairs: different bodies and more than three bonds apart (internal indices)
+  std::vector<int> dist(n);
+  out.pairs.clear();
+  std::vector<std::vector<int>> topo(n, std::vector<int>(n, 1 << 20));
+  for (int i = 0; i < n; ++i) {
+    std::fill(dist.begin(), dist.end(), -1);
+    std::vector<int> q{i};
+    dist[i] = 0;
+    for (size_t qi = 0; qi < q.size(); ++qi)
+      for (int c : adj[q[qi]])
+        if (dist[c] < 0) dist[c] = dist[q[qi]] + 1, q.push_back(c);
+    for (int j = 0; j < n; ++j) topo[i][j] = dist[j] < 0 ? (1 << 20) : dist[j];
+  }
+  for (int ii = 0; ii < n; ++ii)
+    for (int jj = ii + 1; jj < n; ++jj) {
+      const int i = out.user_of[ii], j = out.user_of[jj];
+      if (comp[i] != comp[j] && topo[i][j] > 3)
+        out.pairs.push_back((uint32_t)ii | ((uint32_t)jj << 8) |
+                            ((uint32_t)(out.type[ii] * DSDP_NUM_MAP_TYPES + out.type[jj]) << 16));
+    }
+  const int P = (int)out.pairs.size();
+  out.csr_start.assign(n + 1, 0);
+  out.csr.clear();
+  for (int a = 0; a < n; ++a) {
+    out.csr_start[a] = (uint16_t)out.csr.size();
+    for (int p = 0; p < P; ++p) {
+      const int i = out.pairs[p] & 0xff, j = (out.pairs[p] >> 8) & 0xff;
+      if (i == a) out.csr.push_back((uint32_t)p | ((uint32_t)j << 16));
+      else if (j == a) out.csr.push_back((uint32_t)p | ((uint32_t)i << 16));
+    }
+  }
+  out.csr_start[n] = (uint16_t)out.csr.size();
+  double s2 = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double d = ref(i, a) - ref(origin[root], a);
+      s2 += d * d;
+    }
+  out.gyr = (float)sqrt(s2 / n);
+  if (!(out.gyr > 1e-3f)) out.gyr = 1.0f;
+  out.n = n;
+  out.T = T;
+  out.B = B;
+  out.P = P;
+  out.root_atom = origin[root];
+  for (int a = 0; a < 3; ++a) out.root_ref[a] = L->xyz[3 * origin[root] + a];
+  return DSDP_OK;
+}
+
+}  // namespace
+}  // namespace dsdp
+
+using namespace dsdp;
+
+extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, uint64_t capacity,
+                                        uint64_t* blob_bytes) {
+  Prepared p;
+  const dsdp_status s = prepare(ligand, p);
+  if (s != DSDP_OK) return s;
+  BlobHeader h;
+  memset(&h, 0, sizeof(h));
+  size_t off = sizeof(BlobHeader);
+  h.off_atom = (uint32_t)off;
+  off = align16(off + 16 * (size_t)p.n);
+  h.off_atom_user = (uint32_t)off;
+  off = align16(off + 4 * (size_t)p.n);
+  h.off_body = (uint32_t)off;
+  off = align16(off + sizeof(BodyRec) * (size_t)p.B);
+  h.off_pairs = (uint32_t)off;
+  off = align16(off + 4 * (size_t)p.P);
+  h.off_csr_start = (uint32_t)off;
+  off = align16(off + 2 * (size_t)(p.n + 1));
+  h.off_csr = (uint32_t)off;
+  off = align16(off + 4 * (size_t)p.csr.size());
+  h.off_torsion_body = (uint32_t)off;
+  off = align16(off + 4 * (size_t)p.T);
+  h.off_atom64 = (uint32_t)off;
+  off = align16(off + 8 * 3 * (size_t)p.n);
+  h.off_body64 = (uint32_t)off;
+  off = align16(off + 8 * 6 * (size_t)p.B);
+  h.magic = kBlobMagic;
+  h.bytes = (uint32_t)off;
+  h.n_atoms = p.n;
+  h.n_torsions = p.T;
+  h.n_bodies = p.B;
+  h.n_pairs = p.P;
+  h.rounds = p.rounds;
+  h.gyration_radius = p.gyr;
+  for (int a = 0; a < 3; ++a) h.root_ref[a] = p.root_ref[a];
+  h.root_user_atom = p.root_atom;
+  if (blob_bytes) *blob_bytes = off;
+  if (!blob) return DSDP_OK;
+  if (capacity < off) return set_error(DSDP_ERR_INVALID_ARG, "blob capacity %llu < %llu bytes",
+                                       (unsigned long long)capacity, (unsigned long long)off);
+  uint8_t* b = (uint8_t*)blob;
+  memset(b, 0, off);
+  memcpy(b, &h, sizeof(h));
+  float* atoms = (float*)(b + h.off_atom);
+  for (int i = 0; i < p.n; ++i) {
+    atoms[4 * i + 0] = p.local[3 * i + 0];
+    atoms[4 * i + 1] = p.local[3 * i + 1];
+    atoms[4 * i + 2] = p.local[3 * i + 2];
+    const int32_t packed = p.type[i] | (p.body[i] << 8);
+    memcpy(&atoms[4 * i + 3], &packed, 4);
+  }
+  memcpy(b + h.off_atom_user, p.user_of.data(), 4 * (size_t)p.n);
+  memcpy(b + h.off_body, p.bodies.data(), sizeof(BodyRec) * (size_t)p.B);
+  if (p.P) memcpy(b + h.off_pairs, p.pairs.data(), 4 * (size_t)p.P);
+  memcpy(b + h.off_csr_start, p.csr_start.data(), 2 * (size_t)(p.n + 1));
+  if (!p.csr.empty()) memcpy(b + h.off_csr, p.csr.data(), 4 * p.csr.size());
+  if (p.T) memcpy(b + h.off_torsion_body, p.torsion_body.data(), 4 * (size_t)p.T);
+  memcpy(b + h.off_atom64, p.local64.data(), 8 * 3 * (size_t)p.n);
+  memcpy(b + h.off_body64, p.body64.data(), 8 * 6 * (size_t)p.B);
+  return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_ligand_blob_info(const void* blob, int32_t* n_atoms, int32_t* n_torsions,
+                                             int32_t* n_pairs, int32_t* n_bodies) {
+  if (!blob) return set_error(DSDP_ERR_INVALID_ARG, "blob is NULL");
+  const BlobHeader* h = (const BlobHeader*)blob;
+  if (h->magic != kBlobMagic) return set_error(DSDP_ERR_INVALID_ARG, "not a packed ligand blob");
+  if (n_atoms) *n_atoms = h->n_atoms;
+  if (n_torsions) *n_torsions = h->n_torsions;
+  if (n_pairs) *n_pairs = h->n_pairs;
+  if (n_bodies) *n_bodies = h->n_bodies;
+  return DSDP_OK;
+}

@@ -1,0 +1,282 @@
+// Postprocess of a docking job (Fig. 4: the sampled poses are ranked after the
+// copies finish), on the device and in FP64: every chain's best pose is
+// rebuilt with FP64 kinematics and scored gridless (exact pair sums against
+// the receptor atoms, plus intra); poses are sorted by the torsion-normalised
+// inter score, near-duplicates (heavy-atom RMSD below a cut) are dropped and
+// the best top_k are written out.
+#include "launch.h"
+#include "chain_device.cuh"
+
+namespace dsdp {
+namespace {
+
+constexpr int kRescoreWarps = 8;
+constexpr int kRecTile = 1024;
+
+struct DQuat {
+  double w, x, y, z;
+};
+__device__ __forceinline__ DQuat dqmul(const DQuat& a, const DQuat& b) {
+  return DQuat{a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+               a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x, a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ double3 dqrot(const DQuat& q, double3 v) {
+  const double tx = 2.0 * (q.y * v.z - q.z * v.y), ty = 2.0 * (q.z * v.x - q.x * v.z),
+               tz = 2.0 * (q.x * v.y - q.y * v.x);
+  return make_double3(v.x + q.w * tx + (q.y * tz - q.z * ty), v.y + q.w * ty + (q.z * tx - q.x * tz),
+                      v.z + q.w * tz + (q.x * ty - q.y * tx));
+}
+__device__ __forceinline__ double shd(double v, int src) { return __shfl_sync(kFull, v, src); }
+
+// One warp per chain: FP64 pose, exact inter (receptor staged through shared
+// memory in tiles, FP32 pre-filter then FP64 distance) and intra.
+__global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJob* __restrict__ jobs,
+                                                                     const Tile* __restrict__ tiles) {
+  __shared__ float4 s_rec[kRecTile];
+  __shared__ double s_xyz[kRescoreWarps][kMaxAtoms * 3];
+  const Tile tile = tiles[blockIdx.x];
+  const DevJob& J = jobs[tile.job];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool has_chain = warp < tile.count;
+  const int chain = tile.chain0 + warp;
+  const LigView L = view_blob(J.blob);  // read through the cache; small
+  const double* atom64 = reinterpret_cast<const double*>(J.blob + L.h->off_atom64);
+  const double* body64 = reinterpret_cast<const double*>(J.blob + L.h->off_body64);
+  const int T = L.T, N = L.n_atoms, nb = L.n_bodies;
+  double3 pos[2];
+  int type[2];
+  bool valid[2];
+  if (has_chain) {
+    const float* cf = J.chain_best_conf + (size_t)chain * (7 + T);
+    DQuat q{(double)cf[3], (double)cf[4], (double)cf[5], (double)cf[6]};
+    const double qn = sqrt(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+    q = DQuat{q.w / qn, q.x / qn, q.y / qn, q.z / qn};
+    const double3 p = make_double3(cf[0], cf[1], cf[2]);
+    DQuat Q{1.0, 0.0, 0.0, 0.0};
+    double3 O = make_double3(0.0, 0.0, 0.0);
+    int ptr = -1;
+    if (lane == 0) {
+      Q = q;
+      O = p;
+    } else if (lane < nb) {
+      const BodyRec& b = L.body[lane];
+      const double* g = body64 + 6 * lane;
+      const double th = (double)cf[7 + b.torsion];
+      const double s = sin(0.5 * th), c = cos(0.5 * th);
+      Q = DQuat{c, s * g[3], s * g[4], s * g[5]};
+      O = make_double3(g[0], g[1], g[2]);
+      ptr = b.parent;
+    }
+    for (int r = 0; r < L.rounds; ++r) {
+      const int src = ptr >= 0 ? ptr : lane;
+      const DQuat Qp{shd(Q.w, src), shd(Q.x, src), shd(Q.y, src), shd(Q.z, src)};
+      const double3 Op = make_double3(shd(O.x, src), shd(O.y, src), shd(O.z, src));
+      const int pp = __shfl_sync(kFull, ptr, src);
+      if (ptr >= 0) {
+        const double3 ro = dqrot(Qp, O);
+        O = make_double3(Op.x + ro.x, Op.y + ro.y, Op.z + ro.z);
+        Q = dqmul(Qp, Q);
+        ptr = pp;
+      }
+    }
+    for (int s = 0; s < 2; ++s) {
+      const int i = lane + 32 * s;
+      valid[s] = i < N;
+      const float4 a = valid[s] ? L.atom[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int packed = __float_as_int(a.w);
+      type[s] = packed & 0xff;
+      const int b = valid[s] ? (packed >> 8) & 0xff : 0;
+      const DQuat Qb{shd(Q.w, b), shd(Q.x, b), shd(Q.y, b), shd(Q.z, b)};
+      const double3 Ob = make_double3(shd(O.x, b), shd(O.y, b), shd(O.z, b));
+      const double3 r = valid[s] ? dqrot(Qb, make_double3(atom64[3 * i], atom64[3 * i + 1], atom64[3 * i + 2]))
+                                 : make_double3(0.0, 0.0, 0.0);
+      pos[s] = make_double3(Ob.x + r.x, Ob.y + r.y, Ob.z + r.z);
+      if (valid[s]) {
+        s_xyz[warp][3 * i + 0] = pos[s].x;
+        s_xyz[warp][3 * i + 1] = pos[s].y;
+        s_xyz[warp][3 * i + 2] = pos[s].z;
+        double* out = J.chain_coords + ((size_t)chain * N + i) * 3;
+        out[0] = pos[s].x;
+        out[1] = pos[s].y;
+        out[2] = pos[s].z;
+      }
+    }
+  } else {
+    valid[0] = valid[1] = false;
+    type[0] = type[1] = 0;
+    pos[0] = pos[1] = make_double3(0.0, 0.0, 0.0);
+  }
+  const float pfx[2] = {(float)pos[0].x, (float)pos[1].x}, pfy[2] = {(float)pos[0].y, (float)pos[1].y},
+              pfz[2] = {(float)pos[0].z, (float)pos[1].z};
+  const float pre2 = (kCutoff + 0.05f) * (kCutoff + 0.05f);
+  double e_inter = 0.0;
+  for (int r0 = 0; r0 < J.n_rec; r0 += kRecTile) {
+    const int cnt = min(kRecTile, J.n_rec - r0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const int j = r0 + k;
+      s_rec[k] = make_float4(J.rec_xyz[3 * j], J.rec_xyz[3 * j + 1], J.rec_xyz[3 * j + 2],
+                             __int_as_float((int)J.rec_type[j]));
+    }
+    __syncthreads();
+    if (!has_chain) continue;
+    for (int k = 0; k < cnt; ++k) {
+      const float4 a = s_rec[k];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (!valid[s]) continue;
+        const float fx = pfx[s] - a.x, fy = pfy[s] - a.y, fz = pfz[s] - a.z;
+        if (fx * fx + fy * fy + fz * fz >= pre2) continue;
+        const double dx = pos[s].x - (double)a.x, dy = pos[s].y - (double)a.y, dz = pos[s].z - (double)a.z;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(r < (double)kCutoff)) continue;
+        const int tj = min(__float_as_int(a.w), 8);
+        const double rs = (double)c_xs_radius[type[s]] + (double)c_xs_radius[tj];
+        e_inter += vina_pair_f64(r - rs, pair_bits(type[s], tj));
+      }
+    }
+  }
+  if (!has_chain) return;
+  __syncwarp();
+  double e_intra = 0.0;
+  for (int p = lane; p < L.n_pairs; p += 32) {
+    const uint32_t pr = L.pairs[p];
+    const int i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
+    const double dx = s_xyz[warp][3 * i] - s_xyz[warp][3 * j], dy = s_xyz[warp][3 * i + 1] - s_xyz[warp][3 * j + 1],
+                 dz = s_xyz[warp][3 * i + 2] - s_xyz[warp][3 * j + 2];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (!(r < (double)kCutoff)) continue;
+    const int ti = tp >> 3, tj = tp & 7;
+    e_intra += vina_pair_f64(r - ((double)c_xs_radius[ti] + (double)c_xs_radius[tj]), pair_bits(ti, tj));
+  }
+  e_inter = warp_sum_d(e_inter);
+  e_intra = warp_sum_d(e_intra);
+  if (lane == 0) {
+    J.chain_inter[chain] = e_inter;
+    J.chain_intra[chain] = e_intra;
+    J.chain_score[chain] = e_inter / (1.0 + kWRot * (double)T);
+  }
+}
+
+// One CTA per job: bitonic sort of (score, chain), greedy RMSD de-duplication,
+// top-k output in the caller's atom order.
+__global__ void __launch_bounds__(512) topk_kernel(const DevJob* __restrict__ jobs, int np2) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  double* key = reinterpret_cast<double*>(smem);
+  int* idx = reinterpret_cast<int*>(smem + sizeof(double) * np2);
+  __shared__ int s_kept[DSDP_MAX_TOP_K];
+  __shared__ int s_nkept;
+  __shared__ int s_dup;
+  const DevJob& J = jobs[blockIdx.x];
+  const int n = J.n_chains;
+  const LigView L = view_blob(J.blob);
+  const int N = L.n_atoms, T = L.T;
+  int size = 1;
+  while (size < n) size <<= 1;
+  for (int i = threadIdx.x; i < size; i += blockDim.x) {
+    double k = 1.0 / 0.0;
+    if (i < n) {
+      k = J.chain_score[i];
+      if (k != k) k = 1.0 / 0.0;  // NaN ranks last
+    }
+    key[i] = k;
+    idx[i] = i < n ? i : 0x7fffffff;
+  }
+  __syncthreads();
+  for (int k = 2; k <= size; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const bool gt = key[i] > key[ixj] || (key[i] == key[ixj] && idx[i] > idx[ixj]);
+          if (gt == up) {
+            const double tk = key[i];
+            key[i] = key[ixj];
+            key[ixj] = tk;
+            const int ti = idx[i];
+            idx[i] = idx[ixj];
+            idx[ixj] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) s_nkept = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const double cut2n = (double)J.rmsd_dedup * (double)J.rmsd_dedup * (double)N;
+  for (int pos = 0; pos < n; ++pos) {
+    const int kept = s_nkept;
+    if (kept >= J.top_k) break;
+    const int c = idx[pos];
+    if (threadIdx.x == 0) s_dup = 0;
+    __syncthreads();
+    for (int q = warp; q < kept; q += nwarps) {
+      const double* a = J.chain_coords + (size_t)c * N * 3;
+      const double* b = J.chain_coords + (size_t)s_kept[q] * N * 3;
+      double sum = 0.0;
+      for (int i = lane; i < N; i += 32) {
+        const double dx = a[3 * i] - b[3 * i], dy = a[3 * i + 1] - b[3 * i + 1], dz = a[3 * i + 2] - b[3 * i + 2];
+        sum += dx * dx + dy * dy + dz * dz;
+      }
+      sum = warp_sum_d(sum);
+      if (lane == 0 && sum < cut2n) s_dup = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !s_dup) {
+      s_kept[kept] = c;
+      s_nkept = kept + 1;
+    }
+    __syncthreads();
+  }
+  const int kept = s_nkept;
+  if (threadIdx.x == 0 && J.out_n) J.out_n[0] = kept;
+  for (int q = threadIdx.x; q < kept; q += blockDim.x) {
+    const int c = s_kept[q];
+    if (J.out_chain) J.out_chain[q] = c;
+    if (J.out_score) J.out_score[q] = J.chain_score[c];
+    if (J.out_inter) J.out_inter[q] = J.chain_inter[c];
+    if (J.out_intra) J.out_intra[q] = J.chain_intra[c];
+  }
+  if (J.out_conf)
+    for (int e = threadIdx.x; e < kept * (7 + T); e += blockDim.x) {
+      const int q = e / (7 + T), k = e % (7 + T);
+      J.out_conf[e] = (double)J.chain_best_conf[(size_t)s_kept[q] * (7 + T) + k];
+    }
+  if (J.out_coords)
+    for (int e = threadIdx.x; e < kept * N; e += blockDim.x) {
+      const int q = e / N, i = e % N;
+      const int u = L.atom_user[i];
+      const double* src = J.chain_coords + ((size_t)s_kept[q] * N + i) * 3;
+      float* dst = J.out_coords + ((size_t)q * N + u) * 3;
+      dst[0] = (float)src[0];
+      dst[1] = (float)src[1];
+      dst[2] = (float)src[2];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rescore(const void* jobs, const void* tiles, int n_tiles, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  rescore_kernel<<<n_tiles, 32 * kRescoreWarps, 0, st>>>(reinterpret_cast<const DevJob*>(jobs),
+                                                         reinterpret_cast<const Tile*>(tiles));
+  return cudaGetLastError();
+}
+
+int rescore_tile_chains() { return kRescoreWarps; }
+
+cudaError_t launch_topk(const void* jobs, int n_jobs, int max_chains, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  int np2 = 1;
+  while (np2 < max_chains) np2 <<= 1;
+  const size_t smem = (size_t)np2 * (sizeof(double) + sizeof(int));
+  cudaError_t e = cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  topk_kernel<<<n_jobs, 512, smem, st>>>(reinterpret_cast<const DevJob*>(jobs), np2);
+  return cudaGetLastError();
+}
+
+}  // namespace dsdp

@@ -1,0 +1,129 @@
+"""The C ABI library without a GPU: it loads, exports every declared symbol,
+and its host-side ligand preparation and validation behave (CPU only)."""
+import re
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09916_gb300 import synth
+
+dsdp = pytest.importorskip("paper_2303_09916_gb300.dsdp", reason="libdsdp.so not built")
+
+HEADER = __import__("os").path.join(__import__("os").path.dirname(__file__), "..", "include", "dsdp.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dsdp_[a-z0-9_]+)\s*\(", text)) - {"dsdp_alloc_fn", "dsdp_free_fn"})
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(dsdp._lib, n), n
+    assert sorted(dsdp.EXPORTED) == names
+
+
+def test_status_strings_and_version():
+    assert dsdp.dsdp_status_string(0) == "DSDP_OK"
+    assert dsdp.dsdp_status_string(-5) == "DSDP_ERR_CANCELLED"
+    assert re.match(r"\d+\.\d+\.\d+", dsdp.dsdp_version())
+
+
+def _parse_blob(blob):
+    hdr = struct.unpack_from("<2I5if3fi9I", blob, 0)
+    keys = ["magic", "bytes", "n_atoms", "T", "n_bodies", "n_pairs", "rounds", "gyr", "rx", "ry", "rz", "root_atom",
+            "off_atom", "off_user", "off_body", "off_pairs", "off_csr_start", "off_csr", "off_tb", "off_a64", "off_b64"]
+    h = dict(zip(keys, hdr))
+    n, P = h["n_atoms"], h["n_pairs"]
+    user = np.frombuffer(blob, dtype=np.int32, count=n, offset=h["off_user"])
+    atom = np.frombuffer(blob, dtype=np.float32, count=4 * n, offset=h["off_atom"]).reshape(n, 4)
+    body = atom[:, 3].copy().view(np.int32) >> 8
+    pairs = np.frombuffer(blob, dtype=np.uint32, count=P, offset=h["off_pairs"])
+    csr_start = np.frombuffer(blob, dtype=np.uint16, count=n + 1, offset=h["off_csr_start"])
+    csr = np.frombuffer(blob, dtype=np.uint32, count=2 * P, offset=h["off_csr"])
+    brec = np.frombuffer(blob, dtype=np.int32, count=12 * h["n_bodies"], offset=h["off_body"]).reshape(-1, 12)
+    return h, user, body, pairs, csr_start, csr, brec
+
+
+@pytest.mark.parametrize("n,t,seed", [(8, 2, 0), (20, 4, 1), (30, 8, 2), (45, 12, 3), (60, 15, 4), (10, 0, 5)])
+def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
+    lig = synth.ligand(n, t, seed)
+    blob = dsdp.dsdp_ligand_pack(lig)
+    h, user, body, pairs, csr_start, csr, brec = _parse_blob(bytes(blob))
+    ol = oracle.Ligand(lig.xyz.astype(np.float64), lig.xs_type, lig.bonds, lig.rotatable)
+    assert h["magic"] == 0x50445344 and h["bytes"] == len(blob) and h["bytes"] % 16 == 0
+    assert (h["n_atoms"], h["T"], h["n_bodies"], h["n_pairs"]) == (ol.n_atoms, ol.T, ol.n_bodies, ol.n_pairs)
+    assert h["root_atom"] == ol.root_atom
+    assert h["gyr"] == pytest.approx(ol.gyration_radius, rel=1e-6)
+    assert sorted(user.tolist()) == list(range(n))
+    # same pair set (mapped back to input indices)
+    got = {tuple(sorted((int(user[p & 0xFF]), int(user[(p >> 8) & 0xFF])))) for p in pairs}
+    assert got == {tuple(p) for p in ol.pairs()}
+    # every atom's pair index lists each of its pairs once
+    for a in range(n):
+        entries = csr[csr_start[a]:csr_start[a + 1]]
+        mine = {int(e & 0xFFFF) for e in entries}
+        expect = {k for k, p in enumerate(pairs) if (p & 0xFF) == a or ((p >> 8) & 0xFF) == a}
+        assert mine == expect
+    # bodies: depth-first order, subtree atom ranges contiguous and nested
+    parent = brec[:, 3]
+    begin, end = brec[:, 8], brec[:, 9]
+    assert parent[0] == -1 and all(parent[b] < b for b in range(1, h["n_bodies"]))
+    for b in range(h["n_bodies"]):
+        sub = {b}
+        for c in range(b + 1, h["n_bodies"]):
+            if parent[c] in sub:
+                sub.add(c)
+        atoms = [i for i in range(n) if body[i] in sub]
+        assert atoms == list(range(begin[b], end[b]))
+    assert (1 << h["rounds"]) >= int(brec[:, 10].max()) + 1
+
+
+@pytest.mark.parametrize("bad", ["n_da_type", "ring_rotatable", "too_many_atoms", "disconnected", "bad_bond"])
+def test_ligand_pack_rejects_invalid_input(bad):
+    lig = synth.ligand(12, 3, 0)
+    if bad == "n_da_type":
+        lig.xs_type = lig.xs_type.copy()
+        lig.xs_type[0] = 8
+    elif bad == "ring_rotatable":
+        lig.bonds = np.vstack([lig.bonds, [[0, 11]]]).astype(np.int32)
+        lig.rotatable = np.append(lig.rotatable, 1).astype(np.uint8)
+    elif bad == "too_many_atoms":
+        lig = synth.ligand(12, 3, 0)
+        lig.xyz = np.zeros((70, 3), np.float32)
+        lig.xs_type = np.zeros(70, np.uint8)
+    elif bad == "disconnected":
+        lig.bonds = lig.bonds[:-1]
+        lig.rotatable = lig.rotatable[:-1]
+    elif bad == "bad_bond":
+        lig.bonds = lig.bonds.copy()
+        lig.bonds[0, 1] = 99
+    with pytest.raises(dsdp.DSDPError) as ei:
+        dsdp.dsdp_ligand_pack(lig)
+    assert ei.value.status == dsdp.DSDP_ERR_INVALID_ARG
+    assert dsdp.dsdp_last_error()
+
+
+def test_grid_map_bytes():
+    box = dsdp.make_box([0, 0, 0], [30, 30, 30], 0.375)
+    assert dsdp.dsdp_grid_map_bytes(box, dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ4) == 8 * 80 ** 3 * 16
+    assert dsdp.dsdp_grid_map_bytes(box, dsdp.DSDP_MAP_BF16, dsdp.DSDP_GRID_EQ4) == 8 * 80 ** 3 * 8
+    assert dsdp.dsdp_grid_map_bytes(box, dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ3) == 8 * 80 ** 3 * 4
+    box20 = dsdp.make_box([0, 0, 0], [20, 20, 20], 0.375)
+    assert dsdp.dsdp_grid_map_bytes(box20) == 8 * 54 ** 3 * 16
+    assert dsdp.dsdp_grid_map_bytes(dsdp.make_box([0, 0, 0], [0.1, 1, 1], 0.375)) == 0
+
+
+def test_create_without_a_gpu_fails_cleanly():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(dsdp.DSDPError) as ei:
+        dsdp.dsdp_create(0)
+    assert ei.value.status == dsdp.DSDP_ERR_DEVICE

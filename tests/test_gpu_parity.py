@@ -1,0 +1,314 @@
+"""GPU path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 device arithmetic against FP64):
+  energy   |dE| <= 1e-4 * max(sum_i |e_i|, 1)   (e_i: per-atom and per-pair terms)
+  gradient ||dg||_inf <= 1e-4 * max(||g||_inf, 1e-2)
+Where FP32 and FP64 may take different branches (a pair within 2e-4 A of the
+cutoff or of a slope kink, an atom on a cell face in Eq. 3 mode) the input is
+skipped and counted, never silently compared with a looser bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09916_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_09916_gb300 import dsdp  # noqa: E402
+
+from gpu_util import E_REL, G_REL, Complex, vertex_ambiguity  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = dsdp.dsdp_create(0)
+    yield c
+    dsdp.dsdp_destroy(c)
+
+
+def _box(cx):
+    return dsdp.make_box(cx.center, cx.size, cx.spacing)
+
+
+# ---------------------------------------------------------------- grid maps
+@pytest.fixture(scope="module")
+def ragged():
+    # 7.1 A at 0.375 A -> 19 vertices per axis: bricks of 8 x 8 x 4 leave ragged tails on every axis
+    return Complex(2000, 7.1, 10, 2, seed=11)
+
+
+def test_grid_build_f32_matches_oracle(ctx, ragged):
+    cx = ragged
+    grid = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ4)
+    try:
+        info = dsdp.dsdp_grid_info(grid)
+        og = cx.oracle_grid()
+        assert info["n"] == list(og.n) == [19, 19, 19]
+        assert np.allclose(info["origin"], og.origin, atol=1e-12)
+        maps = dsdp.dsdp_grid_download(ctx, grid).astype(np.float64)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    ref = og.maps
+    amb = vertex_ambiguity(cx.rec_xyz64, cx.rec.xs_type, og.origin, og.n, og.h)
+    ok = ~amb
+    assert amb.mean() < 0.01, amb.mean()
+    e_err = np.abs(maps[..., 0] - ref[..., 0])
+    assert np.all(e_err[ok] <= E_REL * np.maximum(np.abs(ref[..., 0][ok]), 1.0)), e_err[ok].max()
+    gmax = np.abs(ref[..., 1:]).max(-1)
+    g_err = np.abs(maps[..., 1:] - ref[..., 1:]).max(-1)
+    assert np.all(g_err[ok] <= G_REL * np.maximum(gmax[ok], 1e-2)), (g_err[ok] / np.maximum(gmax[ok], 1e-2)).max()
+
+
+@pytest.mark.parametrize("dtype", [dsdp.DSDP_MAP_BF16, dsdp.DSDP_MAP_F16])
+def test_grid_build_16bit_is_the_rounded_fp32_map(ctx, ragged, dtype):
+    cx = ragged
+    g32 = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ4)
+    g16 = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dtype, dsdp.DSDP_GRID_EQ4)
+    try:
+        m32 = dsdp.dsdp_grid_download(ctx, g32)
+        m16 = dsdp.dsdp_grid_download(ctx, g16)
+    finally:
+        dsdp.dsdp_grid_free(ctx, g32)
+        dsdp.dsdp_grid_free(ctx, g16)
+    t = torch.from_numpy(m32)
+    rounded = (t.to(torch.bfloat16) if dtype == dsdp.DSDP_MAP_BF16 else t.to(torch.float16)).float().numpy()
+    assert np.array_equal(m16, rounded)
+
+
+def test_grid_eq3_score_channel_equals_eq4(ctx, ragged):
+    cx = ragged
+    g4 = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ4)
+    g3 = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ3)
+    try:
+        m4 = dsdp.dsdp_grid_download(ctx, g4, dsdp.DSDP_GRID_EQ4)
+        m3 = dsdp.dsdp_grid_download(ctx, g3, dsdp.DSDP_GRID_EQ3)
+    finally:
+        dsdp.dsdp_grid_free(ctx, g4)
+        dsdp.dsdp_grid_free(ctx, g3)
+    assert np.array_equal(m3[..., 0], m4[..., 0])
+
+
+# ---------------------------------------------------------------- scoring
+@pytest.fixture(scope="module")
+def scoring_complex():
+    return Complex(2000, 16.0, 24, 6, seed=3)
+
+
+def _compare_scores(cx, grid_o, mode, confs, e, g, flags=3):
+    skipped = 0
+    worst_e = worst_g = 0.0
+    for i, c in enumerate(confs):
+        if cx.conf_is_ambiguous(grid_o, mode, c):
+            skipped += 1
+            continue
+        terms, gref = cx.olig.score_grid(grid_o, mode, c, flags)
+        eref = (terms[0] if flags & 1 else 0.0) + (terms[1] if flags & 2 else 0.0)
+        scale = max(cx.abs_terms(grid_o, mode, c), 1.0)
+        de = abs(e[i] - eref)
+        dg = np.abs(g[i] - gref).max()
+        gs = max(np.abs(gref).max(), 1e-2)
+        worst_e = max(worst_e, de / scale)
+        worst_g = max(worst_g, dg / gs)
+        assert de <= E_REL * scale, (i, e[i], eref, scale)
+        assert dg <= G_REL * gs, (i, g[i], gref)
+    assert skipped <= len(confs) // 4, skipped
+    return worst_e, worst_g
+
+
+@pytest.mark.parametrize("mode", [dsdp.DSDP_GRID_EQ4, dsdp.DSDP_GRID_EQ3])
+def test_score_eval_on_oracle_maps(ctx, scoring_complex, mode):
+    """(i) the scoring kernel alone, on the oracle's maps rounded to FP32."""
+    cx = scoring_complex
+    og = cx.oracle_grid()
+    maps = og.maps if mode == dsdp.DSDP_GRID_EQ4 else og.maps[..., :1]
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, mode,
+                                    maps.astype(np.float32))
+    try:
+        confs = cx.random_confs(96, seed=1 + mode)
+        for flags in (dsdp.DSDP_TERM_ALL, dsdp.DSDP_TERM_INTER, dsdp.DSDP_TERM_INTRA):
+            e, g = dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs, flags)
+            _compare_scores(cx, og, mode, confs, e, g, flags)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+
+
+def test_score_eval_end_to_end_on_gpu_maps(ctx, scoring_complex):
+    """(ii) GPU-built maps and the scoring kernel together."""
+    cx = scoring_complex
+    og = cx.oracle_grid()
+    grid = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ4)
+    try:
+        confs = cx.random_confs(64, seed=7)
+        e, g = dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs)
+        _compare_scores(cx, og, 0, confs, e, g)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+
+
+@pytest.mark.parametrize("n_atoms,T,seed", [(60, 15, 21), (33, 0, 22), (1, 0, 23), (2, 0, 24), (32, 9, 25)])
+def test_score_eval_ligand_shapes(ctx, n_atoms, T, seed):
+    """Edge shapes: two atoms per lane (> 32 atoms), rigid ligands, a single atom."""
+    if n_atoms == 1:
+        cx = Complex(800, 12.0, 2, 0, seed=seed)
+        lig = synth.Ligand(cx.lig.xyz[:1].copy(), cx.lig.xs_type[:1].copy(), np.zeros((0, 2), np.int32),
+                           np.zeros(0, np.uint8), 0)
+        cx.lig = lig
+        cx.olig = oracle.Ligand(lig.xyz.astype(np.float64), lig.xs_type, lig.bonds, lig.rotatable)
+    else:
+        cx = Complex(800, 12.0, n_atoms, T, seed=seed)
+    og = cx.oracle_grid()
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
+                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    try:
+        confs = cx.random_confs(40, seed=seed)
+        e, g = dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs)
+        _compare_scores(cx, og, 0, confs, e, g)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+
+
+# ---------------------------------------------------------------- chains
+@pytest.fixture(scope="module")
+def chain_complex():
+    return Complex(1500, 14.0, 16, 4, seed=5)
+
+
+def _run_job(ctx, grid, lig, T, **kw):
+    params = dsdp.make_params(**kw)
+    jid = dsdp.dsdp_dock_submit(ctx, grid, lig, params)
+    return dsdp.dsdp_dock_poll(ctx, jid, dsdp.result_buffers(lig.n_atoms, T, params), wait_ms=-1)
+
+
+@pytest.mark.parametrize("optimizer", [dsdp.DSDP_OPT_BFGS, dsdp.DSDP_OPT_BB])
+def test_chains_step_for_step(ctx, chain_complex, optimizer):
+    """Identical Philox streams: short chains agree with the oracle step by step.
+    A Metropolis or best-iterate decision may flip only at a near tie; the chain
+    is compared up to such a flip and the flip is reported."""
+    cx = chain_complex
+    og = cx.oracle_grid()
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
+                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    S, iters, nc = 5, 20, 16
+    try:
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=7,
+                       optimizer=optimizer, trace=1, top_k=4)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    nx = 7 + cx.T
+    tr = res["trace"]
+    dp = oracle.dock_params_array(S, optimizer, 1.2, cx.box_lo(), cx.size)
+    agree = 0
+    flips = []
+    for c in range(nc):
+        ref = oracle.run_chain(cx.olig, og, 0, dp, 7, c, opt=dict(max_iters=iters))
+        full = True
+        for s in range(S + 1):
+            g_e_cur = tr[c, s, nx + 1]
+            r_e_cur = ref["trace_rec"][s, 3]
+            if s > 0:
+                assert int(tr[c, s, nx + 2]) == int(ref["trace_rec"][s, 0]), "mutation mode must match exactly"
+            scale = max(cx.abs_terms(og, 0, ref["trace_conf"][s]), 1.0)
+            if abs(g_e_cur - r_e_cur) > E_REL * scale or int(tr[c, s, nx + 3]) != int(ref["trace_rec"][s, 1]):
+                flips.append((c, s, float(g_e_cur), float(r_e_cur)))
+                full = False
+                break
+        agree += full
+    print(f"optimizer {optimizer}: {agree}/{nc} chains agree on all {S} steps; diverged at {flips}")
+    assert agree >= nc * 3 // 4, flips
+
+
+def test_replay_one_step_transitions(ctx, chain_complex):
+    """Long chains (40 steps x 100 BFGS iterations): re-seed the oracle with the GPU
+    state at each step start and replay one step.  The mutation must match
+    exactly, the Metropolis decision must follow from the GPU's own energies, an
+    accepted pose's energy must equal the oracle's score of that pose, and the
+    candidate energies must agree for the large majority of steps (a flipped
+    line-search decision can lead the two optimisers to different local minima)."""
+    cx = chain_complex
+    og = cx.oracle_grid()
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
+                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    S, iters, nc = 40, 100, 8
+    try:
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=11, trace=1,
+                       top_k=4)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    nx = 7 + cx.T
+    tr = res["trace"].astype(np.float64)
+    dp = oracle.dock_params_array(S, 0, 1.2, cx.box_lo(), cx.size)
+    n_steps = n_match = 0
+    for c in range(nc):
+        for s in range(1, S + 1):
+            cur, e_cur = tr[c, s - 1, :nx], tr[c, s - 1, nx + 1]
+            new, e_new, rec = oracle.mc_step(cx.olig, og, 0, dp, 11, c, s, cur, e_cur, opt=dict(max_iters=iters))
+            g_cand, g_cur, g_mode, g_acc = tr[c, s, nx:nx + 4]
+            assert int(g_mode) == int(rec[0])
+            # Metropolis from the GPU's energies and the Philox uniform of this step
+            w = oracle.philox([c, s, 0, 0], [11, 0])
+            u = (int(w[1]) >> 8) / 2.0 ** 24
+            p_acc = 1.0 if g_cand < e_cur else math.exp(-(g_cand - e_cur) / 1.2)
+            if abs(u - p_acc) > 1e-5 and g_cand != e_cur:
+                assert bool(g_acc) == (u < p_acc), (c, s)
+            if g_acc:
+                terms, _ = cx.olig.score_grid(og, 0, tr[c, s, :nx])
+                scale = max(cx.abs_terms(og, 0, tr[c, s, :nx]), 1.0)
+                assert abs(terms.sum() - g_cand) <= E_REL * scale, (c, s, terms.sum(), g_cand)
+            scale = max(cx.abs_terms(og, 0, cur), 1.0)
+            n_steps += 1
+            n_match += abs(rec[2] - g_cand) <= E_REL * scale
+    print(f"replay: candidate energies agree on {n_match}/{n_steps} steps")
+    assert n_match >= 0.8 * n_steps
+
+
+def test_rescore_topk_matches_oracle(ctx):
+    cx = Complex(2000, 16.0, 20, 4, seed=9)
+    grid = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx))
+    try:
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=64, n_mc_steps=5, n_opt_iters=30, seed=3, top_k=9)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    confs = res["chain_best_conf"].astype(np.float64)
+    scores, idx, terms = oracle.rescore_topk(cx.olig, cx.rec_xyz64, cx.rec.xs_type, confs, k=9, rmsd_cut=1.0)
+    assert list(res["chain"]) == list(idx)
+    assert np.allclose(res["score"], terms[:, 0], rtol=1e-10, atol=1e-12)
+    assert np.allclose(res["inter"], terms[:, 1], rtol=1e-10, atol=1e-12)
+    assert np.allclose(res["intra"], terms[:, 2], rtol=1e-10, atol=1e-12)
+    assert np.array_equal(res["conf"], confs[idx])
+    for q, c in enumerate(idx):
+        assert np.allclose(res["coords"][q], cx.olig.coords(confs[c]), atol=2e-5)
+
+
+def test_determinism_and_batch_independence(ctx):
+    """A job's results depend on (seed, chain) only: bitwise equal when rerun and
+    when run together with other jobs on other grids."""
+    a = Complex(1500, 14.0, 18, 5, seed=31)
+    b = Complex(2500, 18.0, 40, 10, seed=32)
+    ga = dsdp.dsdp_grid_build(ctx, a.rec.xyz, a.rec.xs_type, _box(a))
+    gb = dsdp.dsdp_grid_build(ctx, b.rec.xyz, b.rec.xs_type, _box(b), dsdp.DSDP_MAP_BF16)
+    try:
+        kw = dict(n_chains=48, n_mc_steps=6, n_opt_iters=25, seed=5, top_k=6)
+        r1 = _run_job(ctx, ga, a.lig, a.T, **kw)
+        r2 = _run_job(ctx, ga, a.lig, a.T, **kw)
+        # in the mix: other jobs submitted before and after, all in flight together
+        pa = dsdp.make_params(**kw)
+        pb = dsdp.make_params(n_chains=96, n_mc_steps=6, n_opt_iters=25, seed=9, top_k=6)
+        j0 = dsdp.dsdp_dock_submit(ctx, gb, b.lig, pb)
+        j1 = dsdp.dsdp_dock_submit(ctx, ga, a.lig, pa)
+        j2 = dsdp.dsdp_dock_submit(ctx, gb, b.lig, pb)
+        r3 = dsdp.dsdp_dock_poll(ctx, j1, dsdp.result_buffers(a.lig.n_atoms, a.T, pa), wait_ms=-1)
+        for j in (j0, j2):
+            dsdp.dsdp_dock_poll(ctx, j, dsdp.result_buffers(b.lig.n_atoms, b.T, pb), wait_ms=-1)
+    finally:
+        dsdp.dsdp_grid_free(ctx, ga)
+        dsdp.dsdp_grid_free(ctx, gb)
+    for r in (r2, r3):
+        assert np.array_equal(r["chain_best_e"], r1["chain_best_e"])
+        assert np.array_equal(r["chain_best_conf"], r1["chain_best_conf"])
+        assert np.array_equal(r["score"], r1["score"]) and list(r["chain"]) == list(r1["chain"])
