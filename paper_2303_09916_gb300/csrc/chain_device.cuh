@@ -20,6 +20,7 @@ struct LigView {
   const uint16_t* csr_start;
   const uint32_t* csr;
   const int32_t* torsion_body;
+  const float2* pair_tab;
   int n_atoms, T, n_bodies, n_pairs, rounds;
 };
 
@@ -33,6 +34,7 @@ __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
   v.csr_start = reinterpret_cast<const uint16_t*>(b + v.h->off_csr_start);
   v.csr = reinterpret_cast<const uint32_t*>(b + v.h->off_csr);
   v.torsion_body = reinterpret_cast<const int32_t*>(b + v.h->off_torsion_body);
+  v.pair_tab = reinterpret_cast<const float2*>(b + v.h->off_pair_tab);
   v.n_atoms = v.h->n_atoms;
   v.T = v.h->n_torsions;
   v.n_bodies = v.h->n_bodies;
@@ -41,47 +43,19 @@ __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
   return v;
 }
 
-// Per-lane registers of one ligand.
+// Per-lane ligand data: atom slots lane * APL + s and, on lane b < n_bodies,
+// body b's record; re-read from the staged blob (shared memory) where used.
 template <int APL>
 struct LaneLig {
-  float3 loc[APL];
-  int type[APL];
-  int body[APL];
-  bool valid[APL];
-  // body lane
-  float3 boff, baxis;
-  int bparent, btors, ar0, ar1;
-  // vector lane 6 + k: body of torsion k
-  int tbody;
+  int n_atoms, nb, T, tbody;
 };
 
 template <int APL>
 __device__ __forceinline__ void load_lane_lig(const LigView& L, LaneLig<APL>& R) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < APL; ++s) {
-    const int i = lane * APL + s;
-    R.valid[s] = i < L.n_atoms;
-    const float4 a = R.valid[s] ? L.atom[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    R.loc[s] = make_float3(a.x, a.y, a.z);
-    const int packed = __float_as_int(a.w);
-    R.type[s] = packed & 0xff;
-    R.body[s] = R.valid[s] ? (packed >> 8) & 0xff : 0;
-  }
-  if (lane < L.n_bodies) {
-    const BodyRec& b = L.body[lane];
-    R.boff = make_float3(b.off[0], b.off[1], b.off[2]);
-    R.baxis = make_float3(b.axis[0], b.axis[1], b.axis[2]);
-    R.bparent = b.parent;
-    R.btors = b.torsion;
-    R.ar0 = b.atom_begin;
-    R.ar1 = b.atom_end;
-  } else {
-    R.boff = R.baxis = make_float3(0.f, 0.f, 0.f);
-    R.bparent = -1;
-    R.btors = -1;
-    R.ar0 = R.ar1 = 0;
-  }
+  R.n_atoms = L.n_atoms;
+  R.nb = L.n_bodies;
+  R.T = L.T;
   R.tbody = (lane >= 6 && lane < 6 + L.T) ? L.torsion_body[lane - 6] : 0;
 }
 
@@ -92,38 +66,67 @@ struct Conf {
   float th;
 };
 
-// Per-warp shared scratch.
+// Per-warp shared scratch (layout in warp_scratch_bytes).
 struct WarpScratch {
-  float4* coords;  // [kMaxAtoms]
-  float* pair_s;   // [n_pairs]
+  float4* coords;  // [kMaxAtoms] atom positions
+  float* pre;      // [kMaxAtoms][6] inclusive prefix sums of (g, (r - p) x g)
+  float* H;        // [kMaxDim][kMaxDim] BFGS inverse Hessian, row j owned by lane j
+  float* cur;      // [7 + kMaxDim] current conformation
+  float* best;     // [7 + kMaxDim] best conformation
+  float* pair_s;   // [n_pairs] dE/dr / r of each intra pair
 };
 
-// Score and gradient of one conformation (all lanes return the same E;
-// lane j < 6 + T returns gradient component j, other lanes 0).
-template <int APL, int FMT>
-__device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, const LaneLig<APL>& R,
-                                           const WarpScratch& W, const Conf& c, float& grad, uint32_t flags) {
+constexpr int kConfFloats = 7 + kMaxDim;
+__host__ __device__ constexpr int warp_scratch_fixed_bytes() {
+  return 16 * kMaxAtoms + 24 * kMaxAtoms + ((4 * kMaxDim * kMaxDim + 15) & ~15) + 2 * ((4 * kConfFloats + 15) & ~15);
+}
+__host__ __device__ inline int warp_scratch_bytes(int n_pairs) {
+  return warp_scratch_fixed_bytes() + ((4 * n_pairs + 15) & ~15);
+}
+__device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base) {
+  WarpScratch W;
+  W.coords = reinterpret_cast<float4*>(base);
+  base += 16 * kMaxAtoms;
+  W.pre = reinterpret_cast<float*>(base);
+  base += 24 * kMaxAtoms;
+  W.H = reinterpret_cast<float*>(base);
+  base += (4 * kMaxDim * kMaxDim + 15) & ~15;
+  W.cur = reinterpret_cast<float*>(base);
+  base += (4 * kConfFloats + 15) & ~15;
+  W.best = reinterpret_cast<float*>(base);
+  base += (4 * kConfFloats + 15) & ~15;
+  W.pair_s = reinterpret_cast<float*>(base);
+  return W;
+}
+
+// Body frames for a conformation: lane b < n_bodies returns body b's world
+// rotation Q and origin O, composed from the local transforms by pointer
+// jumping (ceil(log2(depth + 1)) rounds of shuffles).
+__device__ __forceinline__ void body_frames(const LigView& L, const Conf& c, Quat& Q, float3& O) {
   const int lane = threadIdx.x & 31;
   const int nb = L.n_bodies;
-  // ---- body frames: local transforms composed by pointer jumping
-  const float tb = __shfl_sync(kFull, c.th, (lane > 0 && lane < nb) ? 6 + R.btors : 0);
-  Quat Q;
-  float3 O;
-  int ptr;
+  const bool child = lane > 0 && lane < nb;
+  float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+  if (child) {
+    const float4* rec = reinterpret_cast<const float4*>(L.body + lane);
+    b0 = rec[0];  // off xyz, parent
+    b1 = rec[1];  // axis xyz, torsion
+  }
+  const int tors = __float_as_int(b1.w);
+  const float tb = __shfl_sync(kFull, c.th, child ? 6 + tors : 0);
+  int ptr = -1;
   if (lane == 0) {
     Q = c.q;
     O = c.p;
-    ptr = -1;
-  } else if (lane < nb) {
+  } else if (child) {
     float s, co;
     sincosf(0.5f * tb, &s, &co);
-    Q = Quat{co, s * R.baxis.x, s * R.baxis.y, s * R.baxis.z};
-    O = R.boff;
-    ptr = R.bparent;
+    Q = Quat{co, s * b1.x, s * b1.y, s * b1.z};
+    O = make_float3(b0.x, b0.y, b0.z);
+    ptr = __float_as_int(b0.w);
   } else {
     Q = Quat{1.f, 0.f, 0.f, 0.f};
     O = make_float3(0.f, 0.f, 0.f);
-    ptr = -1;
   }
   for (int r = 0; r < L.rounds; ++r) {
     const int src = ptr >= 0 ? ptr : lane;
@@ -136,13 +139,31 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       ptr = pp;
     }
   }
+}
+
+// Score and gradient of one conformation (all lanes return the same E;
+// lane j < 6 + T returns gradient component j, other lanes 0).
+template <int APL, int FMT>
+__device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, const LaneLig<APL>& R,
+                                           const WarpScratch& W, const Conf& c, float& grad, uint32_t flags) {
+  const int lane = threadIdx.x & 31;
+  const int N = L.n_atoms, nb = L.n_bodies;
+  Quat Q;
+  float3 O;
+  body_frames(L, c, Q, O);
   // ---- atom positions
   float3 pos[APL];
+  int type[APL];
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
-    const Quat Qb = shflq(Q, R.body[s]);
-    const float3 Ob = shfl3(O, R.body[s]);
-    pos[s] = Ob + qrot(Qb, R.loc[s]);
+    const int i = lane * APL + s;
+    const float4 a = L.atom[i < N ? i : N - 1];
+    const int packed = __float_as_int(a.w);
+    type[s] = packed & 0xff;
+    const int b = i < N ? (packed >> 8) & 0xff : 0;
+    const Quat Qb = shflq(Q, b);
+    const float3 Ob = shfl3(O, b);
+    pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
   }
   // ---- inter: grid maps
   float e_lane = 0.f;
@@ -150,26 +171,26 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
     g[s] = make_float3(0.f, 0.f, 0.f);
-    if ((flags & DSDP_TERM_INTER) && R.valid[s]) e_lane += sample_map<FMT>(M, R.type[s], pos[s], g[s]);
+    if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) e_lane += sample_map<FMT>(M, type[s], pos[s], g[s]);
   }
   // ---- intra: pairs once, forces gathered per atom
   if (flags & DSDP_TERM_INTRA) {
 #pragma unroll
     for (int s = 0; s < APL; ++s)
-      if (R.valid[s]) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
+      if (lane * APL + s < N) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
     __syncwarp();
     for (int p = lane; p < L.n_pairs; p += 32) {
       const uint32_t pr = L.pairs[p];
-      const int i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
+      const int i = pr & 0xff, j = (pr >> 8) & 0xff;
+      const float2 tab = L.pair_tab[pr >> 16];
       const float4 a = W.coords[i], b = W.coords[j];
       const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
       float sp = 0.f;
       if (r2 < kCutoff * kCutoff) {
         const float r = sqrtf(r2);
-        const int ti = tp >> 3, tj = tp & 7;
         float e, de;
-        vina_pair(r - (c_xs_radius[ti] + c_xs_radius[tj]), pair_bits(ti, tj), e, de);
+        vina_pair(r - tab.x, __float_as_int(tab.y), e, de);
         e_lane += e;
         sp = r > 0.f ? de / r : 0.f;
       }
@@ -178,38 +199,38 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < APL; ++s) {
-      if (!R.valid[s]) continue;
       const int i = lane * APL + s;
+      if (i >= N) continue;
       const int k0 = L.csr_start[i], k1 = L.csr_start[i + 1];
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll 4
       for (int k = k0; k < k1; ++k) {
         const uint32_t e = L.csr[k];
         const float sp = W.pair_s[e & 0xffff];
         const float4 b = W.coords[e >> 16];
-        g[s].x += sp * (pos[s].x - b.x);
-        g[s].y += sp * (pos[s].y - b.y);
-        g[s].z += sp * (pos[s].z - b.z);
+        gx += sp * (pos[s].x - b.x);
+        gy += sp * (pos[s].y - b.y);
+        gz += sp * (pos[s].z - b.z);
       }
+      g[s].x += gx;
+      g[s].y += gy;
+      g[s].z += gz;
     }
-    __syncwarp();
   }
   const float E = warp_sum(e_lane);
-  // ---- back-propagation: prefix sums over atoms (depth-first order) of
-  //      (g_i, (r_i - p) x g_i); a subtree is a contiguous atom range.
+  // ---- back-propagation: inclusive prefix sums over atoms (depth-first
+  //      order) of (g_i, (r_i - p) x g_i); a subtree is a contiguous range.
   float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float acc[APL][6];
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
+    if (lane * APL + s >= N) continue;
     const float3 t = cross3(pos[s] - c.p, g[s]);
-    if (R.valid[s]) {
-      v[0] += g[s].x;
-      v[1] += g[s].y;
-      v[2] += g[s].z;
-      v[3] += t.x;
-      v[4] += t.y;
-      v[5] += t.z;
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc[s][k] = v[k];
+    v[0] += g[s].x;
+    v[1] += g[s].y;
+    v[2] += g[s].z;
+    v[3] += t.x;
+    v[4] += t.y;
+    v[5] += t.z;
   }
   float inc[6];
 #pragma unroll
@@ -222,93 +243,66 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       if (lane >= o) inc[k] += t;
     }
   }
-  float pre[APL][6];  // inclusive prefix at each of this lane's atoms
+  {
+    // this lane's atoms: exclusive prefix of the lane plus its own slots
+    float run[6];
 #pragma unroll
-  for (int s = 0; s < APL; ++s)
+    for (int k = 0; k < 6; ++k) run[k] = inc[k] - v[k];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) pre[s][k] = inc[k] - v[k] + acc[s][k];
-  float tot[6];
+    for (int s = 0; s < APL; ++s) {
+      const int i = lane * APL + s;
+      if (i >= N) continue;
+      const float3 t = cross3(pos[s] - c.p, g[s]);
+      run[0] += g[s].x;
+      run[1] += g[s].y;
+      run[2] += g[s].z;
+      run[3] += t.x;
+      run[4] += t.y;
+      run[5] += t.z;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) tot[k] = __shfl_sync(kFull, inc[k], 31);
-  // torsion gradient on body lanes
-  const bool is_child = lane > 0 && lane < nb;
-  const int hi = is_child ? R.ar1 - 1 : 0, lo = is_child ? R.ar0 - 1 : 0;
-  float shi[6], slo[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    shi[k] = 0.f;
-    slo[k] = 0.f;
-  }
-#pragma unroll
-  for (int s = 0; s < APL; ++s) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const float a = __shfl_sync(kFull, pre[s][k], hi / APL);
-      const float b = __shfl_sync(kFull, pre[s][k], lo / APL);
-      if (hi % APL == s) shi[k] = a;
-      if (lo % APL == s) slo[k] = b;
+      for (int k = 0; k < 6; ++k) W.pre[6 * i + k] = run[k];
     }
   }
+  __syncwarp();
   float tor = 0.f;
-  if (is_child) {
-    const float3 G = make_float3(shi[0] - slo[0], shi[1] - slo[1], shi[2] - slo[2]);
-    const float3 C = make_float3(shi[3] - slo[3], shi[4] - slo[4], shi[5] - slo[5]);
-    const float3 axis = qrot(Q, R.baxis);
+  if (lane > 0 && lane < nb) {
+    const float4* rec = reinterpret_cast<const float4*>(L.body + lane);
+    const float4 b1 = rec[1];
+    const int4 b2 = *reinterpret_cast<const int4*>(rec + 2);  // atom_begin, atom_end, depth, pad
+    const float* hi = W.pre + 6 * (b2.y - 1);
+    const float* lo = W.pre + 6 * (b2.x - 1);
+    const float3 G = make_float3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
+    const float3 C = make_float3(hi[3] - lo[3], hi[4] - lo[4], hi[5] - lo[5]);
+    const float3 axis = qrot(Q, make_float3(b1.x, b1.y, b1.z));
     tor = dot3(axis, C - cross3(O - c.p, G));
   }
   const float tv = __shfl_sync(kFull, tor, R.tbody);
   float gl = 0.f;
   if (lane < 6) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (lane == k) gl = tot[k];
+    gl = W.pre[6 * (N - 1) + lane];
   } else if (lane < 6 + L.T) {
     gl = tv;
   }
+  __syncwarp();  // W.pre / W.coords are rewritten by the next evaluation
   grad = gl;
   return E;
 }
 
 // Coordinates of this lane's atoms for a conformation (same kinematics as eval_conf).
 template <int APL>
-__device__ __forceinline__ void conf_coords(const LigView& L, const LaneLig<APL>& R, const Conf& c, float3* pos) {
+__device__ __forceinline__ void conf_coords(const LigView& L, const Conf& c, float3* pos) {
   const int lane = threadIdx.x & 31;
-  const int nb = L.n_bodies;
-  const float tb = __shfl_sync(kFull, c.th, (lane > 0 && lane < nb) ? 6 + R.btors : 0);
   Quat Q;
   float3 O;
-  int ptr;
-  if (lane == 0) {
-    Q = c.q;
-    O = c.p;
-    ptr = -1;
-  } else if (lane < nb) {
-    float s, co;
-    sincosf(0.5f * tb, &s, &co);
-    Q = Quat{co, s * R.baxis.x, s * R.baxis.y, s * R.baxis.z};
-    O = R.boff;
-    ptr = R.bparent;
-  } else {
-    Q = Quat{1.f, 0.f, 0.f, 0.f};
-    O = make_float3(0.f, 0.f, 0.f);
-    ptr = -1;
-  }
-  for (int r = 0; r < L.rounds; ++r) {
-    const int src = ptr >= 0 ? ptr : lane;
-    const Quat Qp = shflq(Q, src);
-    const float3 Op = shfl3(O, src);
-    const int pp = __shfl_sync(kFull, ptr, src);
-    if (ptr >= 0) {
-      O = Op + qrot(Qp, O);
-      Q = qmul(Qp, Q);
-      ptr = pp;
-    }
-  }
+  body_frames(L, c, Q, O);
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
-    const Quat Qb = shflq(Q, R.body[s]);
-    const float3 Ob = shfl3(O, R.body[s]);
-    pos[s] = Ob + qrot(Qb, R.loc[s]);
+    const int i = lane * APL + s;
+    const float4 a = L.atom[i < L.n_atoms ? i : L.n_atoms - 1];
+    const int b = i < L.n_atoms ? (__float_as_int(a.w) >> 8) & 0xff : 0;
+    const Quat Qb = shflq(Q, b);
+    const float3 Ob = shfl3(O, b);
+    pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
   }
 }
 
@@ -330,23 +324,26 @@ struct OptOut {
 };
 
 // BFGS with Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1,
-// inverse-Hessian update Eq. 6.17).  Lane j keeps row j of H.
+// inverse-Hessian update Eq. 6.17).  Row j of H lives in shared memory and is
+// owned by lane j; vectors are held one component per lane.
 template <int APL, int FMT>
 __device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, const LaneLig<APL>& R,
                                             const WarpScratch& W, Conf& x, int max_iters) {
   const int lane = threadIdx.x & 31;
   const int D = 6 + L.T;
+  float* Hrow = W.H + kMaxDim * (lane < kMaxDim ? lane : 0);
   float g;
   float e = eval_conf<APL, FMT>(M, L, R, W, x, g, DSDP_TERM_ALL);
   uint32_t evals = 1;
-  float H[kMaxDim];
-#pragma unroll
-  for (int k = 0; k < kMaxDim; ++k) H[k] = (k == lane) ? 1.f : 0.f;
+  if (lane < D)
+    for (int k = 0; k < D; ++k) Hrow[k] = (k == lane) ? 1.f : 0.f;
+  __syncwarp();
   for (int it = 0; it < max_iters; ++it) {
     float d = 0.f;
-#pragma unroll
-    for (int k = 0; k < kMaxDim; ++k) d -= H[k] * __shfl_sync(kFull, g, k);
-    if (lane >= D) d = 0.f;
+    for (int k = 0; k < D; ++k) {
+      const float gk = __shfl_sync(kFull, g, k);
+      if (lane < D) d -= Hrow[k] * gk;
+    }
     const float gd = warp_sum(g * d);
     float alpha = 1.f, et = 0.f, gt = 0.f;
     Conf xt;
@@ -369,17 +366,19 @@ __device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, 
     e = et;
     if (sy > kMinCurvature) {
       float hy = 0.f;
-#pragma unroll
-      for (int k = 0; k < kMaxDim; ++k) hy += H[k] * __shfl_sync(kFull, y, k);
-      if (lane >= D) hy = 0.f;
+      for (int k = 0; k < D; ++k) {
+        const float yk = __shfl_sync(kFull, y, k);
+        if (lane < D) hy += Hrow[k] * yk;
+      }
       const float yhy = warp_sum(y * hy);
       const float rho = 1.f / sy;
       const float coef = rho * rho * yhy + rho;
-#pragma unroll
-      for (int k = 0; k < kMaxDim; ++k) {
+      __syncwarp();
+      for (int k = 0; k < D; ++k) {
         const float sk = __shfl_sync(kFull, s, k), hk = __shfl_sync(kFull, hy, k);
-        H[k] += coef * s * sk - rho * (s * hk + hy * sk);
+        if (lane < D) Hrow[k] += coef * s * sk - rho * (s * hk + hy * sk);
       }
+      __syncwarp();
     }
   }
   return OptOut{e, evals};
@@ -440,6 +439,7 @@ __device__ __forceinline__ void store_conf(float* out, const Conf& c, int T) {
   }
 }
 
+// Make the conformation written by store_conf visible to the whole warp, then read it.
 __device__ __forceinline__ Conf load_conf(const float* in, int T) {
   const int lane = threadIdx.x & 31;
   Conf c;
@@ -450,7 +450,8 @@ __device__ __forceinline__ Conf load_conf(const float* in, int T) {
 }
 
 // One Monte Carlo chain (Sec. 2: one of many short independent copies; Vina's
-// mutation and Metropolis rules).
+// mutation and Metropolis rules).  The current and best conformations wait in
+// shared memory; only the candidate being optimised is held in registers.
 template <int APL, int FMT>
 __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& W, int chain) {
   const int lane = threadIdx.x & 31;
@@ -459,39 +460,36 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
   load_lane_lig<APL>(L, R);
   const int T = L.T, nx = 7 + T;
   const ChainStream rs{J.seed_lo, J.seed_hi, (uint32_t)chain};
-  // initial conformation: uniform words n = 0.. of step 0 (word n % 4 of block n / 4)
-  const uint4 b0 = rs.block(0, 0), b1 = rs.block(0, 1);
-  Conf cur;
-  cur.p = make_float3(J.box_lo[0] + J.box_size[0] * ChainStream::to_uniform(b0.x),
-                      J.box_lo[1] + J.box_size[1] * ChainStream::to_uniform(b0.y),
-                      J.box_lo[2] + J.box_size[2] * ChainStream::to_uniform(b0.z));
+  // initial conformation: uniform word n of step 0 is word n % 4 of block n / 4
+  Conf cand;
   {
+    const uint4 b0 = rs.block(0, 0), b1 = rs.block(0, 1);
+    cand.p = make_float3(J.box_lo[0] + J.box_size[0] * ChainStream::to_uniform(b0.x),
+                         J.box_lo[1] + J.box_size[1] * ChainStream::to_uniform(b0.y),
+                         J.box_lo[2] + J.box_size[2] * ChainStream::to_uniform(b0.z));
     const float u1 = ChainStream::to_uniform(b0.w), u2 = ChainStream::to_uniform(b1.x),
                 u3 = ChainStream::to_uniform(b1.y);
     float s2, c2, s3, c3;
     sincosf(kTwoPiF * u2, &s2, &c2);
     sincosf(kTwoPiF * u3, &s3, &c3);
     const float a = sqrtf(1.f - u1), b = sqrtf(u1);
-    cur.q = Quat{b * c3, a * s2, a * c2, b * s3};
-  }
-  {
-    const int n = 6 + (lane - 6);  // word index of torsion lane - 6
+    cand.q = Quat{b * c3, a * s2, a * c2, b * s3};
     float th = 0.f;
     if (lane >= 6 && lane < 6 + T) {
-      const uint4 bk = rs.block(0, (uint32_t)(n >> 2));
-      th = kPiF - kTwoPiF * ChainStream::to_uniform(pick(bk, n & 3));
+      const uint4 bk = rs.block(0, (uint32_t)(lane >> 2));
+      th = kPiF - kTwoPiF * ChainStream::to_uniform(pick(bk, lane & 3));
     }
-    cur.th = th;
+    cand.th = th;
   }
-  OptOut o = local_opt<APL, FMT>(M, L, R, W, cur, J.optimizer, J.n_opt_iters);
-  float e_cur = o.e;
+  OptOut o = local_opt<APL, FMT>(M, L, R, W, cand, J.optimizer, J.n_opt_iters);
+  float e_cur = o.e, e_best = o.e;
   uint32_t evals = o.evals;
-  Conf best = cur;
-  float e_best = e_cur;
+  store_conf(W.cur, cand, T);
+  store_conf(W.best, cand, T);
   const size_t trace_stride = (size_t)nx + 4;
   float* trace = J.trace ? J.trace + (size_t)chain * (J.n_steps + 1) * trace_stride : nullptr;
   if (trace) {
-    store_conf(trace, cur, T);
+    store_conf(trace, cand, T);
     if (lane == 0) {
       trace[nx + 0] = e_cur;
       trace[nx + 1] = e_cur;
@@ -499,11 +497,12 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
       trace[nx + 3] = 1.f;
     }
   }
+  __syncwarp();
   const float inv_gyr = 1.f / L.h->gyration_radius;
   for (int step = 1; step <= J.n_steps; ++step) {
     const uint4 w0 = rs.block((uint32_t)step, 0);
     const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
-    Conf cand = cur;
+    cand = load_conf(W.cur, T);
     if (mode == 0) {
       const float3 b = unit_ball(rs, (uint32_t)step);
       cand.p = cand.p + kMutationAmplitude * b;
@@ -519,16 +518,17 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
     const float u = ChainStream::to_uniform(w0.y);
     const bool accept = (o.e < e_cur) || (u < expf(-(o.e - e_cur) / J.temperature));
     if (accept) {
-      cur = cand;
       e_cur = o.e;
+      store_conf(W.cur, cand, T);
       if (o.e < e_best) {
-        best = cand;
         e_best = o.e;
+        store_conf(W.best, cand, T);
       }
     }
+    __syncwarp();
     if (trace) {
       float* t = trace + (size_t)step * trace_stride;
-      store_conf(t, cur, T);
+      if (lane < nx) t[lane] = W.cur[lane];
       if (lane == 0) {
         t[nx + 0] = o.e;
         t[nx + 1] = e_cur;
@@ -537,11 +537,12 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
       }
     }
   }
-  store_conf(J.chain_best_conf + (size_t)chain * nx, best, T);
+  if (lane < nx) J.chain_best_conf[(size_t)chain * nx + lane] = W.best[lane];
   if (lane == 0) {
     J.chain_best_e[chain] = e_best;
     J.chain_evals[chain] = evals;
   }
+  __syncwarp();
 }
 
 }  // namespace dsdp

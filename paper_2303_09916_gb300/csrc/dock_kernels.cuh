@@ -6,11 +6,6 @@
 
 namespace dsdp {
 
-// Bytes of per-warp shared scratch for a ligand with n_pairs pairs.
-__host__ __device__ inline int warp_scratch_bytes(int n_pairs) {
-  return 16 * kMaxAtoms + ((4 * n_pairs + 15) & ~15);
-}
-
 // Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
 // The job's ligand blob is staged into shared memory once per tile.
 // persistent != 0: CTAs pull tiles from *tile_counter until none are left.
@@ -23,9 +18,7 @@ __global__ void __launch_bounds__(256) dock_chains_kernel(const DevJob* __restri
   __shared__ int s_tile;
   __shared__ int s_job;
   const int warp = threadIdx.x >> 5;
-  WarpScratch W;
-  W.coords = reinterpret_cast<float4*>(smem + blob_smem + warp * warp_smem);
-  W.pair_s = reinterpret_cast<float*>(smem + blob_smem + warp * warp_smem + 16 * kMaxAtoms);
+  const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * warp_smem);
   if (threadIdx.x == 0) s_job = -1;
   __syncthreads();
   int t = blockIdx.x;
@@ -67,9 +60,7 @@ __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_
   __syncthreads();
   const LigView L = view_blob(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpScratch W;
-  W.coords = reinterpret_cast<float4*>(smem + blob_smem + warp * warp_smem);
-  W.pair_s = reinterpret_cast<float*>(smem + blob_smem + warp * warp_smem + 16 * kMaxAtoms);
+  const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * warp_smem);
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= n_conf) return;
   LaneLig<APL> R;

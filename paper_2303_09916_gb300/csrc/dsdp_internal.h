@@ -37,7 +37,8 @@ struct BlobHeader {
   uint32_t off_torsion_body;  // int32[n_torsions]: body driven by torsion k
   uint32_t off_atom64;     // double[n_atoms][3]: local xyz in FP64 (rescoring)
   uint32_t off_body64;     // double[n_bodies][6]: origin offset and unit axis in FP64 (rescoring)
-  int32_t pad[3];
+  uint32_t off_pair_tab;   // float2[64]: for type pair t_i * 8 + t_j: (R_i + R_j, bits 1 hydrophobic | 2 H-bond)
+  int32_t pad[2];
 };
 static_assert(sizeof(BlobHeader) % 16 == 0, "blob header alignment");
 

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "launch.h"
+#include "chain_device.cuh"
 
 struct dsdp_plan {
   dsdp_ctx* ctx = nullptr;
@@ -31,7 +32,7 @@ struct dsdp_plan {
 
 namespace dsdp {
 
-int warp_scratch_bytes_host(int n_pairs) { return 16 * kMaxAtoms + ((4 * n_pairs + 15) & ~15); }
+int warp_scratch_bytes_host(int n_pairs) { return warp_scratch_bytes(n_pairs); }
 
 dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) {
   if (!in) return set_error(DSDP_ERR_INVALID_ARG, "dock params NULL");

@@ -305,6 +305,8 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   off = align16(off + 8 * 3 * (size_t)p.n);
   h.off_body64 = (uint32_t)off;
   off = align16(off + 8 * 6 * (size_t)p.B);
+  h.off_pair_tab = (uint32_t)off;
+  off = align16(off + 8 * 64);
   h.magic = kBlobMagic;
   h.bytes = (uint32_t)off;
   h.n_atoms = p.n;
@@ -338,6 +340,19 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   if (p.T) memcpy(b + h.off_torsion_body, p.torsion_body.data(), 4 * (size_t)p.T);
   memcpy(b + h.off_atom64, p.local64.data(), 8 * 3 * (size_t)p.n);
   memcpy(b + h.off_body64, p.body64.data(), 8 * 6 * (size_t)p.B);
+  {
+    // Vina XS radii and bits (1 hydrophobic, 2 donor, 4 acceptor) of the 8 ligand map types
+    static const double radius[8] = {1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0};
+    static const int bits[8] = {1, 0, 0, 2, 4, 4, 6, 0};
+    float* tab = (float*)(b + h.off_pair_tab);
+    for (int ti = 0; ti < 8; ++ti)
+      for (int tj = 0; tj < 8; ++tj) {
+        int pb = (bits[ti] & bits[tj] & 1);
+        if (((bits[ti] & 2) && (bits[tj] & 4)) || ((bits[ti] & 4) && (bits[tj] & 2))) pb |= 2;
+        tab[2 * (ti * 8 + tj)] = (float)(radius[ti] + radius[tj]);
+        memcpy(&tab[2 * (ti * 8 + tj) + 1], &pb, 4);
+      }
+  }
   return DSDP_OK;
 }
 
