@@ -17,6 +17,7 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 // 2 donor, 4 acceptor).
 static __constant__ float c_xs_radius[9] = {1.9f, 1.9f, 1.8f, 1.8f, 1.8f, 1.7f, 1.7f, 2.0f, 1.8f};
 static __constant__ int c_xs_bits[9] = {1, 0, 0, 2, 4, 4, 6, 0, 6};
+static __constant__ double c_xs_radius_d[9] = {1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0, 1.8};
 
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
@@ -177,15 +178,15 @@ __device__ __forceinline__ int pair_bits(int ti, int tj) {
 __device__ __forceinline__ double vina_pair_f64(double d, int bits) {
   const double a = 2.0 * d;
   const double b = 0.5 * (d - 3.0);
-  double e = (double)kWGauss1 * exp(-a * a) + (double)kWGauss2 * exp(-b * b);
-  if (d < 0.0) e += (double)kWRepulsion * d * d;
+  double e = kWGauss1D * exp(-a * a) + kWGauss2D * exp(-b * b);
+  if (d < 0.0) e += kWRepulsionD * d * d;
   if (bits & 1) {
-    if (d < 0.5) e += (double)kWHydrophobic;
-    else if (d < 1.5) e += (double)kWHydrophobic * (1.5 - d);
+    if (d < 0.5) e += kWHydrophobicD;
+    else if (d < 1.5) e += kWHydrophobicD * (1.5 - d);
   }
   if (bits & 2) {
-    if (d < -0.7) e += (double)kWHBond;
-    else if (d < 0.0) e += (double)kWHBond * (-d / 0.7);
+    if (d < -0.7) e += kWHBondD;
+    else if (d < 0.0) e += kWHBondD * (-d / 0.7);
   }
   return e;
 }

@@ -112,6 +112,14 @@ constexpr double kWRot = 0.0585;
 constexpr float kCutoff = 8.0f;
 constexpr float kWallSlope = 10.0f;
 
+// The same constants in double precision, for the FP64 rescoring.
+constexpr double kWGauss1D = -0.0356;
+constexpr double kWGauss2D = -0.00516;
+constexpr double kWRepulsionD = 0.840;
+constexpr double kWHydrophobicD = -0.0351;
+constexpr double kWHBondD = -0.587;
+constexpr double kCutoffD = 8.0;
+
 // Optimiser constants (BFGS: Armijo backtracking; BB: BB1 step with clamps).
 constexpr float kArmijoC1 = 1e-4f;
 constexpr float kShrink = 0.5f;

@@ -129,9 +129,9 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
         if (fx * fx + fy * fy + fz * fz >= pre2) continue;
         const double dx = pos[s].x - (double)a.x, dy = pos[s].y - (double)a.y, dz = pos[s].z - (double)a.z;
         const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (!(r < (double)kCutoff)) continue;
+        if (!(r < kCutoffD)) continue;
         const int tj = min(__float_as_int(a.w), 8);
-        const double rs = (double)c_xs_radius[type[s]] + (double)c_xs_radius[tj];
+        const double rs = c_xs_radius_d[type[s]] + c_xs_radius_d[tj];
         e_inter += vina_pair_f64(r - rs, pair_bits(type[s], tj));
       }
     }
@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
     const double dx = s_xyz[warp][3 * i] - s_xyz[warp][3 * j], dy = s_xyz[warp][3 * i + 1] - s_xyz[warp][3 * j + 1],
                  dz = s_xyz[warp][3 * i + 2] - s_xyz[warp][3 * j + 2];
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (!(r < (double)kCutoff)) continue;
+    if (!(r < kCutoffD)) continue;
     const int ti = tp >> 3, tj = tp & 7;
-    e_intra += vina_pair_f64(r - ((double)c_xs_radius[ti] + (double)c_xs_radius[tj]), pair_bits(ti, tj));
+    e_intra += vina_pair_f64(r - (c_xs_radius_d[ti] + c_xs_radius_d[tj]), pair_bits(ti, tj));
   }
   e_inter = warp_sum_d(e_inter);
   e_intra = warp_sum_d(e_intra);

@@ -187,6 +187,47 @@ def _run_job(ctx, grid, lig, T, **kw):
 
 
 @pytest.mark.parametrize("optimizer", [dsdp.DSDP_OPT_BFGS, dsdp.DSDP_OPT_BB])
+def test_local_opt_short_horizon(ctx, chain_complex, optimizer):
+    """The first local optimisation of each chain (step 0) with 0, 1, 2, 3, 5 and 10
+    iterations: the initial pose comes from Philox, so with 0 iterations this is a
+    pure evaluation; each iteration adds a line search whose decisions can flip
+    only at near ties."""
+    cx = chain_complex
+    og = cx.oracle_grid()
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
+                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    nc = 32
+    nx = 7 + cx.T
+    agree = {}
+    try:
+        for iters in (0, 1, 2, 3, 5, 10):
+            res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=0, n_opt_iters=iters, seed=7,
+                           optimizer=optimizer, trace=1, top_k=1) if iters else None
+            if iters == 0:
+                # n_opt_iters = 0 means "default"; evaluate the initial poses instead
+                dp = oracle.dock_params_array(0, optimizer, 1.2, cx.box_lo(), cx.size)
+                confs = np.array([oracle.chain_init(cx.olig, dp, 7, c) for c in range(nc)])
+                e, _ = dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs)
+                ok = 0
+                for c in range(nc):
+                    t, _ = cx.olig.score_grid(og, 0, confs[c])
+                    ok += abs(e[c] - t.sum()) <= E_REL * max(cx.abs_terms(og, 0, confs[c]), 1.0)
+                agree[0] = ok
+                continue
+            dp = oracle.dock_params_array(0, optimizer, 1.2, cx.box_lo(), cx.size)
+            ok = 0
+            for c in range(nc):
+                ref = oracle.run_chain(cx.olig, og, 0, dp, 7, c, opt=dict(max_iters=iters))
+                scale = max(cx.abs_terms(og, 0, ref["trace_conf"][0]), 1.0)
+                ok += abs(res["trace"][c, 0, nx + 1] - ref["trace_rec"][0, 3]) <= E_REL * scale
+            agree[iters] = ok
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    print(f"optimizer {optimizer}: chains agreeing after k iterations {agree} of {nc}")
+    assert agree[0] == nc and agree[1] >= nc - 1 and agree[2] >= nc - 2, agree
+
+
+@pytest.mark.parametrize("optimizer", [dsdp.DSDP_OPT_BFGS, dsdp.DSDP_OPT_BB])
 def test_chains_step_for_step(ctx, chain_complex, optimizer):
     """Identical Philox streams: short chains agree with the oracle step by step.
     A Metropolis or best-iterate decision may flip only at a near tie; the chain
