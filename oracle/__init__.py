@@ -68,6 +68,7 @@ def lib():
             "orc_grid_dims": (None, [dp, d, ip]),
             "orc_receptor_field": (None, [i, dp, ip, i, i, dp, d, dp]),
             "orc_grid_build": (None, [i, dp, ip, dp, dp, d, d, i, dp]),
+            "orc_receptor_field_abs": (None, [i, dp, ip, i, i, dp, d, dp]),
             "orc_interpolate": (None, [dp, ip, dp, d, i, i, i, dp, dp, dp]),
             "orc_ligand_new": (vp, [i, dp, ip, i, ip, ip]),
             "orc_ligand_free": (None, [vp]),
@@ -157,6 +158,16 @@ def receptor_field(rec_xyz, rec_type, t, pts, cutoff=8.0):
     p, pp = _d(pts)
     out = np.zeros((len(p), 4))
     lib().orc_receptor_field(len(rt), rxp, rtp, int(t), len(p), pp, float(cutoff), _d(out)[1])
+    return out
+
+
+def receptor_field_abs(rec_xyz, rec_type, t, pts, cutoff=8.0):
+    """(sum |f|, sum |df/dr|) over the receptor atoms within the cutoff, per point."""
+    rx, rxp = _d(rec_xyz)
+    rt, rtp = _i(rec_type)
+    p, pp = _d(pts)
+    out = np.zeros((len(p), 2))
+    lib().orc_receptor_field_abs(len(rt), rxp, rtp, int(t), len(p), pp, float(cutoff), _d(out)[1])
     return out
 
 

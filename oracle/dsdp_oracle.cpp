@@ -985,6 +985,26 @@ void orc_receptor_field(int n_rec, const double* rec_xyz, const int* rec_type, i
                    out + 4 * p);
 }
 
+// Scale of the receptor sum at points, for tolerances: out[p*2] = sum_j |f|,
+// out[p*2 + 1] = sum_j |df/dr| over receptor atoms within the cutoff.
+void orc_receptor_field_abs(int n_rec, const double* rec_xyz, const int* rec_type, int t, int n_pts,
+                            const double* pts, double cutoff, double* out) {
+  for (int p = 0; p < n_pts; ++p) {
+    const V3 m = v3(pts[3 * p], pts[3 * p + 1], pts[3 * p + 2]);
+    double se = 0.0, sg = 0.0;
+    for (int j = 0; j < n_rec; ++j) {
+      const double r = norm(sub(m, v3(rec_xyz[3 * j], rec_xyz[3 * j + 1], rec_xyz[3 * j + 2])));
+      if (!(r < cutoff)) continue;
+      double e, dedr;
+      pair_term(t, rec_type[j], r, cutoff, &e, &dedr);
+      se += std::fabs(e);
+      sg += std::fabs(dedr);
+    }
+    out[2 * p] = se;
+    out[2 * p + 1] = sg;
+  }
+}
+
 // Full maps [K][nz][ny][nx][4]; vertices split over n_threads (same arithmetic per vertex).
 void orc_grid_build(int n_rec, const double* rec_xyz, const int* rec_type, const double* center,
                     const double* size, double h, double cutoff, int n_threads, double* maps) {

@@ -69,33 +69,35 @@ struct Conf {
 // Per-warp shared scratch (layout in warp_scratch_bytes).
 struct WarpScratch {
   float4* coords;  // [kMaxAtoms] atom positions
-  float* pre;      // [kMaxAtoms][6] inclusive prefix sums of (g, (r - p) x g)
+  float4* pre;     // [kMaxAtoms][2] inclusive prefix sums of (g, (r - p) x g): (gx, gy, gz, cx), (cy, cz, -, -)
   float* H;        // [kMaxDim][kMaxDim] BFGS inverse Hessian, row j owned by lane j
   float* cur;      // [7 + kMaxDim] current conformation
   float* best;     // [7 + kMaxDim] best conformation
-  float* pair_s;   // [n_pairs] dE/dr / r of each intra pair
+  float* pair;     // per intra pair: its force vector (float4, one atom per lane) or dE/dr / r (float)
 };
 
 constexpr int kConfFloats = 7 + kMaxDim;
 __host__ __device__ constexpr int warp_scratch_fixed_bytes() {
-  return 16 * kMaxAtoms + 24 * kMaxAtoms + ((4 * kMaxDim * kMaxDim + 15) & ~15) + 2 * ((4 * kConfFloats + 15) & ~15);
+  return 16 * kMaxAtoms + 32 * kMaxAtoms + ((4 * kMaxDim * kMaxDim + 15) & ~15) + 2 * ((4 * kConfFloats + 15) & ~15);
 }
-__host__ __device__ inline int warp_scratch_bytes(int n_pairs) {
-  return warp_scratch_fixed_bytes() + ((4 * n_pairs + 15) & ~15);
+// One atom per lane keeps each pair's force vector (16 B); two atoms per lane
+// (up to 2016 pairs) keep one scalar per pair (4 B) to bound shared memory.
+__host__ __device__ inline int warp_scratch_bytes(int n_pairs, int apl) {
+  return warp_scratch_fixed_bytes() + (((apl == 1 ? 16 : 4) * n_pairs + 15) & ~15);
 }
 __device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base) {
   WarpScratch W;
   W.coords = reinterpret_cast<float4*>(base);
   base += 16 * kMaxAtoms;
-  W.pre = reinterpret_cast<float*>(base);
-  base += 24 * kMaxAtoms;
+  W.pre = reinterpret_cast<float4*>(base);
+  base += 32 * kMaxAtoms;
   W.H = reinterpret_cast<float*>(base);
   base += (4 * kMaxDim * kMaxDim + 15) & ~15;
   W.cur = reinterpret_cast<float*>(base);
   base += (4 * kConfFloats + 15) & ~15;
   W.best = reinterpret_cast<float*>(base);
   base += (4 * kConfFloats + 15) & ~15;
-  W.pair_s = reinterpret_cast<float*>(base);
+  W.pair = reinterpret_cast<float*>(base);
   return W;
 }
 
@@ -120,7 +122,7 @@ __device__ __forceinline__ void body_frames(const LigView& L, const Conf& c, Qua
     O = c.p;
   } else if (child) {
     float s, co;
-    sincosf(0.5f * tb, &s, &co);
+    __sincosf(0.5f * tb, &s, &co);  // |theta / 2| <= pi / 2: absolute error < 4e-7
     Q = Quat{co, s * b1.x, s * b1.y, s * b1.z};
     O = make_float3(b0.x, b0.y, b0.z);
     ptr = __float_as_int(b0.w);
@@ -173,28 +175,28 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     g[s] = make_float3(0.f, 0.f, 0.f);
     if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) e_lane += sample_map<FMT>(M, type[s], pos[s], g[s]);
   }
-  // ---- intra: pairs once, forces gathered per atom
+  // ---- intra: each pair once, its force gathered by both atoms
   if (flags & DSDP_TERM_INTRA) {
 #pragma unroll
     for (int s = 0; s < APL; ++s)
       if (lane * APL + s < N) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
     __syncwarp();
+#pragma unroll 2
     for (int p = lane; p < L.n_pairs; p += 32) {
       const uint32_t pr = L.pairs[p];
-      const int i = pr & 0xff, j = (pr >> 8) & 0xff;
       const float2 tab = L.pair_tab[pr >> 16];
-      const float4 a = W.coords[i], b = W.coords[j];
+      const float4 a = W.coords[pr & 0xff], b = W.coords[(pr >> 8) & 0xff];
       const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
       float sp = 0.f;
       if (r2 < kCutoff * kCutoff) {
-        const float r = sqrtf(r2);
-        float e, de;
-        vina_pair(r - tab.x, __float_as_int(tab.y), e, de);
+        const float inv_r = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        float e;
+        vina_pair_r(r2 * inv_r, inv_r, tab.x, __float_as_int(tab.y), e, sp);
         e_lane += e;
-        sp = r > 0.f ? de / r : 0.f;
       }
-      W.pair_s[p] = sp;
+      if (APL == 1) reinterpret_cast<float4*>(W.pair)[p] = make_float4(sp * dx, sp * dy, sp * dz, 0.f);
+      else W.pair[p] = sp;
     }
     __syncwarp();
 #pragma unroll
@@ -203,14 +205,26 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       if (i >= N) continue;
       const int k0 = L.csr_start[i], k1 = L.csr_start[i + 1];
       float gx = 0.f, gy = 0.f, gz = 0.f;
+      if (APL == 1) {
 #pragma unroll 4
-      for (int k = k0; k < k1; ++k) {
-        const uint32_t e = L.csr[k];
-        const float sp = W.pair_s[e & 0xffff];
-        const float4 b = W.coords[e >> 16];
-        gx += sp * (pos[s].x - b.x);
-        gy += sp * (pos[s].y - b.y);
-        gz += sp * (pos[s].z - b.z);
+        for (int k = k0; k < k1; ++k) {
+          const uint32_t e = L.csr[k];
+          const float4 f = reinterpret_cast<const float4*>(W.pair)[e & 0x7fff];
+          const float sg = (e & 0x8000) ? -1.f : 1.f;
+          gx += sg * f.x;
+          gy += sg * f.y;
+          gz += sg * f.z;
+        }
+      } else {
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+          const uint32_t e = L.csr[k];
+          const float sp = W.pair[e & 0x7fff];
+          const float4 b = W.coords[e >> 16];
+          gx += sp * (pos[s].x - b.x);
+          gy += sp * (pos[s].y - b.y);
+          gz += sp * (pos[s].z - b.z);
+        }
       }
       g[s].x += gx;
       g[s].y += gy;
@@ -259,8 +273,8 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       run[3] += t.x;
       run[4] += t.y;
       run[5] += t.z;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) W.pre[6 * i + k] = run[k];
+      W.pre[2 * i] = make_float4(run[0], run[1], run[2], run[3]);
+      W.pre[2 * i + 1] = make_float4(run[4], run[5], 0.f, 0.f);
     }
   }
   __syncwarp();
@@ -269,17 +283,18 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     const float4* rec = reinterpret_cast<const float4*>(L.body + lane);
     const float4 b1 = rec[1];
     const int4 b2 = *reinterpret_cast<const int4*>(rec + 2);  // atom_begin, atom_end, depth, pad
-    const float* hi = W.pre + 6 * (b2.y - 1);
-    const float* lo = W.pre + 6 * (b2.x - 1);
-    const float3 G = make_float3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
-    const float3 C = make_float3(hi[3] - lo[3], hi[4] - lo[4], hi[5] - lo[5]);
+    const float4 h0 = W.pre[2 * (b2.y - 1)], h1 = W.pre[2 * (b2.y - 1) + 1];
+    const float4 l0 = W.pre[2 * (b2.x - 1)], l1 = W.pre[2 * (b2.x - 1) + 1];
+    const float3 G = make_float3(h0.x - l0.x, h0.y - l0.y, h0.z - l0.z);
+    const float3 C = make_float3(h0.w - l0.w, h1.x - l1.x, h1.y - l1.y);
     const float3 axis = qrot(Q, make_float3(b1.x, b1.y, b1.z));
     tor = dot3(axis, C - cross3(O - c.p, G));
   }
   const float tv = __shfl_sync(kFull, tor, R.tbody);
   float gl = 0.f;
   if (lane < 6) {
-    gl = W.pre[6 * (N - 1) + lane];
+    const float* tot = reinterpret_cast<const float*>(W.pre + 2 * (N - 1));
+    gl = tot[lane];
   } else if (lane < 6 + L.T) {
     gl = tv;
   }

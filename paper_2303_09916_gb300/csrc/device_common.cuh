@@ -95,18 +95,28 @@ __device__ __forceinline__ Quat qnormalize(const Quat& q) {
   return Quat{q.w * inv, q.x * inv, q.y * inv, q.z * inv};
 }
 
-// Unit quaternion of a rotation vector.
+// Unit quaternion of a rotation vector w: (cos(|w|/2), sin(|w|/2) w/|w|).  Below
+// |w| = 1/16 the Taylor series of cos(x/2) and sin(x/2)/x is used (truncation
+// error < 1e-12), above it sincosf.
 __device__ __forceinline__ Quat quat_from_rotvec(float wx, float wy, float wz) {
-  const float angle = sqrtf(wx * wx + wy * wy + wz * wz);
-  if (angle == 0.f) return Quat{1.f, 0.f, 0.f, 0.f};
-  float s, c;
-  sincosf(0.5f * angle, &s, &c);
-  const float k = s / angle;
+  const float a2 = wx * wx + wy * wy + wz * wz;
+  float c, k;
+  if (a2 < 1.f / 256.f) {
+    c = 1.f + a2 * (-1.f / 8.f + a2 * (1.f / 384.f));
+    k = 0.5f + a2 * (-1.f / 48.f + a2 * (1.f / 3840.f));
+  } else {
+    const float angle = sqrtf(a2);
+    float s;
+    sincosf(0.5f * angle, &s, &c);
+    k = s / angle;
+  }
   return Quat{c, wx * k, wy * k, wz * k};
 }
 
 // Wrap to (-pi, pi].
-__device__ __forceinline__ float wrap_angle(float t) { return t - kTwoPiF * ceilf((t - kPiF) / kTwoPiF); }
+__device__ __forceinline__ float wrap_angle(float t) {
+  return t - kTwoPiF * ceilf((t - kPiF) * (1.f / kTwoPiF));
+}
 
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -167,6 +177,27 @@ __device__ __forceinline__ void vina_pair(float d, int bits, float& e, float& de
   }
 }
 
+// The same terms without branches, from r and 1/r (intra-ligand pairs):
+// returns e and (de/dr) / r.  hydrophobic = min(max(1.5 - d, 0), 1) and
+// H-bond = min(max(-d / 0.7, 0), 1) equal the piecewise forms; their slopes are
+// taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in vina_pair.
+__device__ __forceinline__ void vina_pair_r(float r, float inv_r, float rsum, int bits, float& e, float& s) {
+  const float d = r - rsum;
+  const float a = 2.f * d;
+  const float g1 = __expf(-a * a);
+  const float b = 0.5f * (d - 3.f);
+  const float g2 = __expf(-b * b);
+  const float m = fminf(d, 0.f);
+  const float wh = (bits & 1) ? kWHydrophobic : 0.f;
+  const float wb = (bits & 2) ? kWHBond : 0.f;
+  e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * m * m + wh * fminf(fmaxf(1.5f - d, 0.f), 1.f) +
+      wb * fminf(fmaxf(-d * (1.0f / 0.7f), 0.f), 1.f);
+  float de = kWGauss1 * g1 * (-8.f * d) - kWGauss2 * g2 * b + 2.f * kWRepulsion * m;
+  if (d >= 0.5f && d < 1.5f) de -= wh;
+  if (d >= -0.7f && d < 0.f) de -= wb * (1.0f / 0.7f);
+  s = de * inv_r;
+}
+
 __device__ __forceinline__ int pair_bits(int ti, int tj) {
   const int a = c_xs_bits[ti], b = c_xs_bits[tj];
   int bits = (a & b & 1);
@@ -199,7 +230,7 @@ __host__ __device__ constexpr int fmt_channels(int fmt) { return fmt < 3 ? 4 : 1
 __host__ __device__ constexpr int fmt_elem_bytes(int fmt) { return (fmt % 3 == 0) ? 4 : 2; }
 
 template <int FMT>
-__device__ __forceinline__ float4 load_node(const void* maps, size_t idx) {
+__device__ __forceinline__ float4 load_node(const void* maps, unsigned idx) {
   if (FMT == 0) {
     return __ldg(reinterpret_cast<const float4*>(maps) + idx);
   } else if (FMT == 1 || FMT == 2) {
@@ -246,8 +277,9 @@ __device__ __forceinline__ float sample_map(const MapView& M, int t, float3 r, f
   const float cz = fminf(fmaxf(uz, 0.f), (float)(M.nz - 1));
   const int ix = min((int)cx, M.nx - 2), iy = min((int)cy, M.ny - 2), iz = min((int)cz, M.nz - 2);
   const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
-  const size_t sxy = (size_t)M.nx * M.ny;
-  const size_t base = (size_t)t * sxy * M.nz + (size_t)iz * sxy + (size_t)iy * M.nx + ix;
+  // 32-bit node indices: the host rejects grids with 8 nx ny nz >= 2^31 nodes.
+  const unsigned sxy = (unsigned)M.nx * (unsigned)M.ny;
+  const unsigned base = ((unsigned)t * (unsigned)M.nz + (unsigned)iz) * sxy + (unsigned)iy * (unsigned)M.nx + ix;
   const float4 v000 = load_node<FMT>(M.maps, base);
   const float4 v100 = load_node<FMT>(M.maps, base + 1);
   const float4 v010 = load_node<FMT>(M.maps, base + M.nx);

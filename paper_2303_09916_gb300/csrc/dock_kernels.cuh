@@ -10,7 +10,7 @@ namespace dsdp {
 // The job's ligand blob is staged into shared memory once per tile.
 // persistent != 0: CTAs pull tiles from *tile_counter until none are left.
 template <int APL, int FMT>
-__global__ void __launch_bounds__(256) dock_chains_kernel(const DevJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 2) dock_chains_kernel(const DevJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles, int n_tiles,
                                                           int* tile_counter, int persistent, int blob_smem,
                                                           int warp_smem) {

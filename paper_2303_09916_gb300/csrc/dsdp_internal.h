@@ -33,7 +33,7 @@ struct BlobHeader {
   uint32_t off_body;       // BodyRec[n_bodies]
   uint32_t off_pairs;      // uint32[n_pairs]: i | j << 8 | (type_i * 8 + type_j) << 16 (internal indices)
   uint32_t off_csr_start;  // uint16[n_atoms + 1]
-  uint32_t off_csr;        // uint32[2 n_pairs]: pair index | partner << 16
+  uint32_t off_csr;        // uint32[2 n_pairs]: pair index | 0x8000 if the atom is the pair's second | partner << 16
   uint32_t off_torsion_body;  // int32[n_torsions]: body driven by torsion k
   uint32_t off_atom64;     // double[n_atoms][3]: local xyz in FP64 (rescoring)
   uint32_t off_body64;     // double[n_bodies][6]: origin offset and unit axis in FP64 (rescoring)

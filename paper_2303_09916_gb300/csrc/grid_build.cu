@@ -235,6 +235,12 @@ dsdp_status validate_box(const dsdp_box* box) {
       return set_error(DSDP_ERR_INVALID_ARG, "box size %g must exceed the spacing %g", box->size[a], box->spacing);
     if (box->size[a] / box->spacing > 4096.0) return set_error(DSDP_ERR_INVALID_ARG, "box has > 4096 vertices per axis");
   }
+  int n[3];
+  double o[3];
+  grid_geometry(box, n, o);
+  if ((double)DSDP_NUM_MAP_TYPES * n[0] * n[1] * n[2] >= 2147483648.0)
+    return set_error(DSDP_ERR_INVALID_ARG, "grid of %d x %d x %d x 8 nodes exceeds 2^31 (32-bit map indices)", n[0],
+                     n[1], n[2]);
   return DSDP_OK;
 }
 

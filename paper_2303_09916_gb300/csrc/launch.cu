@@ -32,7 +32,7 @@ struct dsdp_plan {
 
 namespace dsdp {
 
-int warp_scratch_bytes_host(int n_pairs) { return warp_scratch_bytes(n_pairs); }
+int warp_scratch_bytes_host(int n_pairs, int apl) { return warp_scratch_bytes(n_pairs, apl); }
 
 dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) {
   if (!in) return set_error(DSDP_ERR_INVALID_ARG, "dock params NULL");
@@ -86,6 +86,8 @@ static dsdp_status check_view(const dsdp_grid_view* g) {
   for (int a = 0; a < 3; ++a)
     if (g->n[a] < 2) return set_error(DSDP_ERR_INVALID_ARG, "grid needs >= 2 vertices per axis");
   if (!(g->spacing > 0.0)) return set_error(DSDP_ERR_INVALID_ARG, "grid spacing must be positive");
+  if ((double)DSDP_NUM_MAP_TYPES * g->n[0] * g->n[1] * g->n[2] >= 2147483648.0)
+    return set_error(DSDP_ERR_INVALID_ARG, "grid exceeds 2^31 nodes (32-bit map indices)");
   return DSDP_OK;
 }
 
@@ -117,7 +119,7 @@ extern "C" dsdp_status dsdp_score_eval_device(const dsdp_grid_view* grid, const 
   a.flags = flags;
   a.apl = n_atoms <= 32 ? 1 : 2;
   a.blob_smem = (int)((const BlobHeader*)h_blob)->bytes;
-  a.warp_smem = warp_scratch_bytes_host(P);
+  a.warp_smem = warp_scratch_bytes_host(P, a.apl);
   return check_cuda(launch_score_dispatch(map_fmt(grid->dtype, grid->mode), a, (cudaStream_t)stream),
                     "score_eval_kernel launch");
 }
@@ -213,11 +215,12 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   std::vector<Tile> tiles;
   for (int f = 0; f < 6; ++f) {
     dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0};
+    for (int j = 0; j < n_jobs; ++j)
+      if (fmt[j] == f) g.apl = std::max(g.apl, apl[j]);  // the group runs at its largest ligand's tile
     for (int j = 0; j < n_jobs; ++j) {
       if (fmt[j] != f) continue;
-      g.apl = std::max(g.apl, apl[j]);
       g.blob_smem = std::max(g.blob_smem, blob_bytes[j]);
-      g.warp_smem = std::max(g.warp_smem, warp_scratch_bytes_host(pairs[j]));
+      g.warp_smem = std::max(g.warp_smem, warp_scratch_bytes_host(pairs[j], g.apl));
       for (int c = 0; c < dj[j].n_chains; c += W) tiles.push_back(Tile{j, c, std::min(W, dj[j].n_chains - c), 0});
     }
     g.n_tiles = (int)tiles.size() - g.first_tile;

@@ -48,6 +48,6 @@ MapView map_view_of(const dsdp_grid_view* g);
 cudaError_t launch_rescore(const void* jobs, const void* tiles, int n_tiles, cudaStream_t st);
 int rescore_tile_chains();
 cudaError_t launch_topk(const void* jobs, int n_jobs, int max_chains, cudaStream_t st);
-int warp_scratch_bytes_host(int n_pairs);
+int warp_scratch_bytes_host(int n_pairs, int apl);
 
 }  // namespace dsdp

@@ -253,7 +253,7 @@ dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
     for (int p = 0; p < P; ++p) {
       const int i = out.pairs[p] & 0xff, j = (out.pairs[p] >> 8) & 0xff;
       if (i == a) out.csr.push_back((uint32_t)p | ((uint32_t)j << 16));
-      else if (j == a) out.csr.push_back((uint32_t)p | ((uint32_t)i << 16));
+      else if (j == a) out.csr.push_back((uint32_t)p | 0x8000u | ((uint32_t)i << 16));
     }
   }
   out.csr_start[n] = (uint16_t)out.csr.size();

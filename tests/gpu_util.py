@@ -12,9 +12,12 @@ HYD = [1, 0, 0, 0, 0, 0, 0, 0, 0]
 DON = [0, 0, 0, 1, 0, 0, 1, 0, 1]
 ACC = [0, 0, 0, 0, 1, 1, 1, 0, 1]
 
-# Tolerances of the FP32 device path against the FP64 oracle (relative 1e-4):
-#   energy  |dE| <= 1e-4 * max(sum_i |e_i|, 1), e_i the per-atom and per-pair terms
-#   gradient ||dg||_inf <= 1e-4 * max(||g||_inf, 1e-2) + 1e-4 * (atom-term scale)
+# Tolerances of the FP32 device path against the FP64 oracle (relative 1e-4 of
+# the scale of the summed terms, since FP32 sums carry error relative to their
+# terms, not to a result that may cancel):
+#   conformation energy   |dE| <= 1e-4 * max(sum_i |e_i|, 1)  (per-atom grid and per-pair terms)
+#   conformation gradient ||dg||_inf <= 1e-4 * max(||g||_inf, 1e-2)
+#   map vertex            |dE| <= 1e-4 * max(sum_j |f_j|, 1), |dg| <= 1e-4 * max(sum_j |f'_j|, 1e-2)
 E_REL = 1e-4
 G_REL = 1e-4
 
@@ -134,3 +137,15 @@ def vertex_ambiguity(rec_xyz, rec_type, grid_origin, n, h, eps=5e-5):
                     amb[t, v] = True
                     break
     return amb.reshape(8, nz, ny, nx)
+
+
+def vertex_scales(cx, og):
+    """(8, nz, ny, nx, 2): sum_j |f| and sum_j |df/dr| at every vertex (oracle)."""
+    nx, ny, nz = og.n
+    zs, ys, xs = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pts = np.stack([og.origin[0] + og.h * xs, og.origin[1] + og.h * ys, og.origin[2] + og.h * zs],
+                   -1).reshape(-1, 3)
+    out = np.zeros((8, len(pts), 2))
+    for t in range(8):
+        out[t] = oracle.receptor_field_abs(cx.rec_xyz64, cx.rec.xs_type, t, pts)
+    return out.reshape(8, nz, ny, nx, 2)

@@ -67,7 +67,11 @@ def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
     # every atom's pair index lists each of its pairs once
     for a in range(n):
         entries = csr[csr_start[a]:csr_start[a + 1]]
-        mine = {int(e & 0xFFFF) for e in entries}
+        mine = {int(e & 0x7FFF) for e in entries}
+        for e in entries:  # sign bit: set when the atom is the pair's second atom
+            p = pairs[e & 0x7FFF]
+            assert bool(e & 0x8000) == (((p >> 8) & 0xFF) == a)
+            assert (e >> 16) == ((p >> 8) & 0xFF if (p & 0xFF) == a else p & 0xFF)
         expect = {k for k, p in enumerate(pairs) if (p & 0xFF) == a or ((p >> 8) & 0xFF) == a}
         assert mine == expect
     # bodies: depth-first order, subtree atom ranges contiguous and nested
