@@ -338,9 +338,24 @@ struct OptOut {
   uint32_t evals;
 };
 
+// Four warp sums at once (one butterfly, independent chains in flight).
+__device__ __forceinline__ void warp_sum4(float& a, float& b, float& c, float& d) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    b += __shfl_xor_sync(kFull, b, o);
+    c += __shfl_xor_sync(kFull, c, o);
+    d += __shfl_xor_sync(kFull, d, o);
+  }
+}
+
 // BFGS with Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1,
 // inverse-Hessian update Eq. 6.17).  Row j of H lives in shared memory and is
 // owned by lane j; vectors are held one component per lane.
+// One matrix-vector product per iteration: with d = -H g and y = g' - g,
+// H y = H g' + d, and the next direction -H' g' follows from H g' and the dot
+// products s.g', (Hy).g' without forming H' g' separately:
+//   H' g' = H g' - rho (s (Hy.g') + Hy (s.g')) + (rho^2 y.Hy + rho) s (s.g').
 template <int APL, int FMT>
 __device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, const LaneLig<APL>& R,
                                             const WarpScratch& W, Conf& x, int max_iters) {
@@ -352,14 +367,9 @@ __device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, 
   uint32_t evals = 1;
   if (lane < D)
     for (int k = 0; k < D; ++k) Hrow[k] = (k == lane) ? 1.f : 0.f;
-  __syncwarp();
+  float d = -g;  // H0 = I
+  float gd = -warp_sum(g * g);
   for (int it = 0; it < max_iters; ++it) {
-    float d = 0.f;
-    for (int k = 0; k < D; ++k) {
-      const float gk = __shfl_sync(kFull, g, k);
-      if (lane < D) d -= Hrow[k] * gk;
-    }
-    const float gd = warp_sum(g * d);
     float alpha = 1.f, et = 0.f, gt = 0.f;
     Conf xt;
     bool ok = false;
@@ -375,26 +385,31 @@ __device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, 
     }
     if (!ok) break;
     const float s = alpha * d, y = gt - g;
-    const float sy = warp_sum(s * y);
     x = xt;
     g = gt;
     e = et;
+    if (it + 1 == max_iters) break;  // no further direction needed
+    float hg = 0.f;  // (H g')_lane
+    for (int k = 0; k < D; ++k) {
+      const float gk = __shfl_sync(kFull, gt, k);
+      if (lane < D) hg += Hrow[k] * gk;
+    }
+    const float hy = lane < D ? hg + d : 0.f;
+    float sy = s * y, yhy = y * hy, hyg = hy * gt, sg = s * gt;
+    warp_sum4(sy, yhy, hyg, sg);
     if (sy > kMinCurvature) {
-      float hy = 0.f;
-      for (int k = 0; k < D; ++k) {
-        const float yk = __shfl_sync(kFull, y, k);
-        if (lane < D) hy += Hrow[k] * yk;
-      }
-      const float yhy = warp_sum(y * hy);
       const float rho = 1.f / sy;
       const float coef = rho * rho * yhy + rho;
-      __syncwarp();
       for (int k = 0; k < D; ++k) {
         const float sk = __shfl_sync(kFull, s, k), hk = __shfl_sync(kFull, hy, k);
         if (lane < D) Hrow[k] += coef * s * sk - rho * (s * hk + hy * sk);
       }
-      __syncwarp();
+      d = -(hg - rho * (s * hyg + hy * sg) + coef * s * sg);
+    } else {
+      d = -hg;
     }
+    if (lane >= D) d = 0.f;
+    gd = warp_sum(g * d);  // computed directly: the sufficient-decrease test must see the true slope
   }
   return OptOut{e, evals};
 }

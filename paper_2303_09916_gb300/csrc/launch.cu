@@ -204,12 +204,9 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   P->flags = flags;
   P->max_chains = max_chains;
   P->sms = ctx_sm_count(ctx);
-  int W = warps_per_cta;
-  if (W == 0) {
-    size_t total = 0;
-    for (int j = 0; j < n_jobs; ++j) total += dj[j].n_chains;
-    W = total <= (size_t)P->sms * 2 ? 1 : (total <= (size_t)P->sms * 8 ? 2 : 4);
-  }
+  // One warp per CTA by default: each chain is scheduled on its own, so no CTA
+  // slot waits for the slowest chain of a tile; the ligand is staged per chain.
+  int W = warps_per_cta > 0 ? warps_per_cta : 1;
   P->warps_per_cta = W;
   // chain tiles grouped by map format (one launch per format present)
   std::vector<Tile> tiles;
