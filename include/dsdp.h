@@ -335,6 +335,36 @@ dsdp_status dsdp_plan_destroy(dsdp_ctx* ctx, dsdp_plan* plan);
 dsdp_status dsdp_gather_bench_device(const dsdp_grid_view* grid, const float* d_points, const uint8_t* d_types,
                                      int32_t n_points, int32_t repeats, float* d_out, void* stream);
 
+/* ------------------------------------------------------------------ no-allocation postprocess
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory when they need the postprocess: code holding an
+ * allocator's lock, a framework's memory-planning phase, a real-time thread
+ * that must stay off the driver's allocation path, or a host that owns a fixed
+ * device budget.
+ *
+ * dsdp_rescore_topk_noalloc runs the FP64 rescoring, RMSD de-duplication and
+ * top-k of one job (the work dsdp_plan_launch does after the chains) and
+ * allocates nothing: no cudaMalloc / cudaFree, no allocator callback, no
+ * library routine that allocates.  Its scratch is one file-scope device array
+ * of DSDP_NOALLOC_SCRATCH_BYTES (about 1.6 MB) that every GPU loading the
+ * library holds until the process exits.
+ *   - job: as for dsdp_plan_create; inputs read: h_blob, d_blob, receptor,
+ *     params (n_chains <= DSDP_NOALLOC_MAX_CHAINS, top_k, rmsd_dedup) and
+ *     d_chain_best_conf (the chains' best poses, FP32); outputs written: d_out_n,
+ *     d_out_chain, d_out_score, d_out_inter, d_out_intra, d_out_conf,
+ *     d_out_coords (NULL skips one).  Grid, box and trace fields are ignored.
+ *   - Errors: DSDP_ERR_INVALID_ARG for n_chains above the limit or missing
+ *     arrays, DSDP_ERR_DEVICE when a launch fails.
+ *   - The first call on a device resolves the array's device address (with
+ *     that device current); make that first call before capturing a stream.
+ *   - Every call shares the array and it keeps the last call's contents; no
+ *     field has to start at zero, since each value read is written earlier in
+ *     the same call.  Calls that overlap on the GPU (other streams, or other
+ *     host threads, on the same device) race on the array: serialise them. */
+#define DSDP_NOALLOC_MAX_CHAINS 1024
+#define DSDP_NOALLOC_SCRATCH_BYTES 1600000
+dsdp_status dsdp_rescore_topk_noalloc(const dsdp_job_device* job, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

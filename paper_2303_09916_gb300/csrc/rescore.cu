@@ -4,6 +4,10 @@
 // the receptor atoms, plus intra); poses are sorted by the torsion-normalised
 // inter score, near-duplicates (heavy-atom RMSD below a cut) are dropped and
 // the best top_k are written out.
+#include <string.h>
+
+#include <mutex>
+
 #include "launch.h"
 #include "chain_device.cuh"
 
@@ -280,3 +284,118 @@ cudaError_t launch_topk(const void* jobs, int n_jobs, int max_chains, cudaStream
 }
 
 }  // namespace dsdp
+
+// ---------------------------------------------------------------------------
+// FP64 rescoring + top-k without any allocation (dsdp_rescore_topk_noalloc).
+//
+// For callers that cannot allocate device memory at the point of the call --
+// code running under an allocator lock or inside a framework's memory-planning
+// phase, a real-time thread that must not take the driver's allocation path,
+// or a host that owns a fixed device budget -- the scratch this postprocess
+// needs (the job record, the rescoring tiles, per-chain scores and FP64
+// coordinates) lives in one file-scope device array.  Every GPU that loads the
+// library holds it (DSDP_NOALLOC_SCRATCH_BYTES) until the process exits.
+// ---------------------------------------------------------------------------
+namespace dsdp {
+namespace {
+
+constexpr int kNoAllocMaxChains = DSDP_NOALLOC_MAX_CHAINS;
+constexpr size_t kNoAllocJobOff = 0;
+constexpr size_t kNoAllocTileOff = 512;
+constexpr size_t kNoAllocTiles = (kNoAllocMaxChains + kRescoreWarps - 1) / kRescoreWarps;
+constexpr size_t kNoAllocScoreOff = kNoAllocTileOff + ((sizeof(Tile) * kNoAllocTiles + 255) & ~(size_t)255);
+constexpr size_t kNoAllocInterOff = kNoAllocScoreOff + sizeof(double) * kNoAllocMaxChains;
+constexpr size_t kNoAllocIntraOff = kNoAllocInterOff + sizeof(double) * kNoAllocMaxChains;
+constexpr size_t kNoAllocCoordOff = kNoAllocIntraOff + sizeof(double) * kNoAllocMaxChains;
+constexpr size_t kNoAllocBytes = kNoAllocCoordOff + sizeof(double) * 3 * kMaxAtoms * kNoAllocMaxChains;
+static_assert(sizeof(DevJob) <= kNoAllocTileOff, "job record must fit its slot");
+static_assert(kNoAllocBytes == DSDP_NOALLOC_SCRATCH_BYTES, "header and scratch layout disagree");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Writes the job record and its rescoring tiles into the scratch array; the
+// record arrives as a kernel parameter, so no host buffer has to outlive the call.
+__global__ void noalloc_tables_kernel(DevJob job, DevJob* job_out, Tile* tiles_out, int n_tiles) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *job_out = job;
+  if (t < n_tiles) {
+    const int c0 = t * kRescoreWarps;
+    tiles_out[t] = Tile{0, c0, min(kRescoreWarps, job.n_chains - c0), 0};
+  }
+}
+
+// Device address of g_noalloc_scratch, resolved once per device (the host-side
+// symbol is only a stand-in and must never reach a kernel).
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+dsdp_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return check_cuda(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(DSDP_ERR_DEVICE, "device ordinal %d beyond 63", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return check_cuda(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return DSDP_OK;
+}
+
+}  // namespace
+}  // namespace dsdp
+
+using namespace dsdp;
+
+extern "C" dsdp_status dsdp_rescore_topk_noalloc(const dsdp_job_device* job, void* stream) {
+  if (!job) return set_error(DSDP_ERR_INVALID_ARG, "job is NULL");
+  int32_t n_atoms = 0, T = 0, P = 0, B = 0;
+  dsdp_status s = dsdp_ligand_blob_info(job->h_blob, &n_atoms, &T, &P, &B);
+  if (s != DSDP_OK) return s;
+  dsdp_dock_params p;
+  s = normalize_params(&job->params, &p);
+  if (s != DSDP_OK) return s;
+  if (p.n_chains > kNoAllocMaxChains)
+    return set_error(DSDP_ERR_INVALID_ARG, "n_chains %d exceeds the no-alloc limit of %d chains (scratch %zu bytes)",
+                     p.n_chains, kNoAllocMaxChains, (size_t)kNoAllocBytes);
+  if (!job->d_blob || !job->d_chain_best_conf || job->receptor.n < 1 || !job->receptor.xyz ||
+      !job->receptor.xs_type)
+    return set_error(DSDP_ERR_INVALID_ARG, "no-alloc rescoring needs d_blob, d_chain_best_conf and the receptor");
+  void* base = nullptr;
+  s = noalloc_scratch(&base);
+  if (s != DSDP_OK) return s;
+  unsigned char* sc = static_cast<unsigned char*>(base);
+  DevJob d;
+  memset(&d, 0, sizeof(d));
+  d.blob = (const uint8_t*)job->d_blob;
+  d.n_chains = p.n_chains;
+  d.chain_best_conf = job->d_chain_best_conf;
+  d.n_rec = job->receptor.n;
+  d.rec_xyz = job->receptor.xyz;
+  d.rec_type = job->receptor.xs_type;
+  d.chain_score = reinterpret_cast<double*>(sc + kNoAllocScoreOff);
+  d.chain_inter = reinterpret_cast<double*>(sc + kNoAllocInterOff);
+  d.chain_intra = reinterpret_cast<double*>(sc + kNoAllocIntraOff);
+  d.chain_coords = reinterpret_cast<double*>(sc + kNoAllocCoordOff);
+  d.top_k = p.top_k;
+  d.rmsd_dedup = (float)p.rmsd_dedup;
+  d.out_n = job->d_out_n;
+  d.out_chain = job->d_out_chain;
+  d.out_score = job->d_out_score;
+  d.out_inter = job->d_out_inter;
+  d.out_intra = job->d_out_intra;
+  d.out_conf = job->d_out_conf;
+  d.out_coords = job->d_out_coords;
+  const cudaStream_t st = (cudaStream_t)stream;
+  DevJob* d_job = reinterpret_cast<DevJob*>(sc + kNoAllocJobOff);
+  Tile* d_tiles = reinterpret_cast<Tile*>(sc + kNoAllocTileOff);
+  const int n_tiles = (p.n_chains + kRescoreWarps - 1) / kRescoreWarps;
+  noalloc_tables_kernel<<<(n_tiles + 127) / 128, 128, 0, st>>>(d, d_job, d_tiles, n_tiles);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_rescore(d_job, d_tiles, n_tiles, st);
+  if (e == cudaSuccess) e = launch_topk(d_job, 1, p.n_chains, st);
+  return check_cuda(e, "no-alloc rescoring launch");
+}

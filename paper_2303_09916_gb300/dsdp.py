@@ -33,6 +33,7 @@ DSDP_PLAN_PERSISTENT, DSDP_PLAN_NO_RESCORE = 1, 2
 DSDP_STAGE_CHAINS, DSDP_STAGE_RESCORE, DSDP_STAGE_ALL = 1, 2, 3
 DSDP_NUM_MAP_TYPES = 8
 DSDP_MAX_LIGAND_ATOMS, DSDP_MAX_TORSIONS, DSDP_MAX_CHAINS, DSDP_MAX_TOP_K = 64, 15, 8192, 64
+DSDP_NOALLOC_MAX_CHAINS, DSDP_NOALLOC_SCRATCH_BYTES = 1024, 1600000
 
 
 class DSDPError(RuntimeError):
@@ -133,6 +134,7 @@ _sig = {
     "dsdp_plan_destroy": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "dsdp_gather_bench_device": (C.c_int32, [P(dsdp_grid_view), C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                              C.c_void_p, C.c_void_p]),
+    "dsdp_rescore_topk_noalloc": (C.c_int32, [P(dsdp_job_device), C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -399,3 +401,8 @@ def dsdp_gather_bench_device(view: dsdp_grid_view, d_points: int, d_types: int, 
                              d_out: int, stream: int = 0):
     _check(_lib.dsdp_gather_bench_device(C.byref(view), int(d_points), int(d_types), int(n_points), int(repeats),
                                          int(d_out), stream or None))
+
+
+def dsdp_rescore_topk_noalloc(job: dsdp_job_device, stream: int = 0):
+    """FP64 rescoring + top-k of one job with no device allocation (see include/dsdp.h)."""
+    _check(_lib.dsdp_rescore_topk_noalloc(C.byref(job), stream or None))

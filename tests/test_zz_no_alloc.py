@@ -1,0 +1,103 @@
+"""dsdp_rescore_topk_noalloc: the FP64 rescoring + top-k for callers that cannot
+allocate device memory when they run it (allocator locks, memory-planning
+phases, real-time threads, fixed device budgets).  It must give what the plan's
+own rescoring stage gives for the same chain poses, on two calls in a row
+(the shared scratch array keeps the previous call's contents).
+
+Named to be collected last, so that a stop at the first failure has already
+run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_09916_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_09916_gb300 import dsdp  # noqa: E402
+
+N_CHAINS, TOP_K, BOX, H = 96, 9, 14.0, 0.375
+
+
+def _outputs(dev, nx, n_atoms):
+    return dict(n=torch.zeros(1, dtype=torch.int32, device=dev), chain=torch.zeros(TOP_K, dtype=torch.int32, device=dev),
+                score=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                inter=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                intra=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                conf=torch.zeros((TOP_K, nx), dtype=torch.float64, device=dev),
+                coords=torch.zeros((TOP_K, n_atoms, 3), dtype=torch.float32, device=dev))
+
+
+def _point_outputs(j, o):
+    j.d_out_n, j.d_out_chain = o["n"].data_ptr(), o["chain"].data_ptr()
+    j.d_out_score, j.d_out_inter = o["score"].data_ptr(), o["inter"].data_ptr()
+    j.d_out_intra, j.d_out_conf = o["intra"].data_ptr(), o["conf"].data_ptr()
+    j.d_out_coords = o["coords"].data_ptr()
+
+
+def test_noalloc_rescoring_matches_the_plan_twice_in_a_row():
+    dev = torch.device("cuda", 0)
+    rec = synth.receptor(1500, 41)
+    lig = synth.ligand(18, 5, 41, center=rec.pocket_center)
+    box = dsdp.make_box(rec.pocket_center, BOX, H)
+    nbytes = dsdp.dsdp_grid_map_bytes(box)
+    d_maps = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
+    d_type = torch.from_numpy(rec.xs_type.copy()).to(dev)
+    blob = dsdp.dsdp_ligand_pack(lig)
+    nx = 7 + dsdp.dsdp_ligand_blob_info(blob)["n_torsions"]
+    d_blob = torch.from_numpy(blob.copy()).to(dev)
+    conf = torch.zeros((N_CHAINS, nx), dtype=torch.float32, device=dev)
+    n = [int(np.ceil(BOX / H))] * 3
+    origin = [rec.pocket_center[a] - (n[a] - 1) * H / 2 for a in range(3)]
+    j = dsdp.dsdp_job_device()
+    j.grid = dsdp.grid_view(d_maps.data_ptr(), n, origin, H)
+    j.receptor = dsdp.dsdp_receptor(len(rec.xs_type), d_xyz.data_ptr(), d_type.data_ptr())
+    j.h_blob = blob.ctypes.data
+    j.d_blob = d_blob.data_ptr()
+    j.params = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=4, n_opt_iters=25, seed=3, top_k=TOP_K)
+    for a in range(3):
+        j.box_lo[a] = rec.pocket_center[a] - BOX / 2
+        j.box_size[a] = BOX
+    j.d_chain_best_conf = conf.data_ptr()
+    ref = _outputs(dev, nx, lig.n_atoms)
+    _point_outputs(j, ref)
+    stream = torch.cuda.current_stream().cuda_stream
+    dsdp.dsdp_grid_build_device(len(rec.xs_type), d_xyz.data_ptr(), d_type.data_ptr(), box, dsdp.DSDP_MAP_F32,
+                                dsdp.DSDP_GRID_EQ4, d_maps.data_ptr(), nbytes, stream)
+    plan = dsdp.dsdp_plan_create(None, [j], 0, 0)
+    try:
+        dsdp.dsdp_plan_launch(plan, stream)  # chains, then the allocating rescoring path
+        torch.cuda.synchronize()
+    finally:
+        dsdp.dsdp_plan_destroy(None, plan)
+    for call in range(2):
+        got = _outputs(dev, nx, lig.n_atoms)
+        _point_outputs(j, got)
+        dsdp.dsdp_rescore_topk_noalloc(j, stream)
+        torch.cuda.synchronize()
+        k = int(ref["n"].item())
+        assert int(got["n"].item()) == k >= 1, call
+        assert torch.equal(got["chain"][:k], ref["chain"][:k]), call
+        for key in ("score", "inter", "intra", "conf"):
+            assert np.allclose(got[key][:k].cpu().numpy(), ref[key][:k].cpu().numpy(), rtol=1e-10, atol=1e-12), key
+        assert np.allclose(got["coords"][:k].cpu().numpy(), ref["coords"][:k].cpu().numpy(), atol=1e-6)
+
+
+def test_noalloc_rejects_more_chains_than_its_scratch_holds():
+    rec = synth.receptor(300, 42)
+    lig = synth.ligand(8, 2, 42, center=rec.pocket_center)
+    blob = dsdp.dsdp_ligand_pack(lig)
+    j = dsdp.dsdp_job_device()
+    j.h_blob = blob.ctypes.data
+    j.d_blob = 1  # never dereferenced: the size check comes first
+    j.d_chain_best_conf = 1
+    j.receptor = dsdp.dsdp_receptor(300, 1, 1)
+    j.params = dsdp.make_params(n_chains=dsdp.DSDP_NOALLOC_MAX_CHAINS + 1)
+    with pytest.raises(dsdp.DSDPError) as ei:
+        dsdp.dsdp_rescore_topk_noalloc(j, 0)
+    assert ei.value.status == dsdp.DSDP_ERR_INVALID_ARG
+    assert "no-alloc limit" in dsdp.dsdp_last_error()
