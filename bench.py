@@ -200,6 +200,10 @@ def run_device(args, rank, world, dev, dist):
         jobs.append(j)
         keep.append((d_maps, d_xyz, d_type, blob, d_blob, outs))
     plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
+    for (d_maps, d_xyz, d_type, *_), box in zip(keep, boxes):
+        dsdp.dsdp_grid_build_device(N_REC, d_xyz.data_ptr(), d_type.data_ptr(), box, dtype, dsdp.DSDP_GRID_EQ4,
+                                    d_maps.data_ptr(), d_maps.numel(), sptr)
+    tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 1)  # picks register budget and work queue by measurement
     n_plan_kernels = dsdp.dsdp_plan_kernel_count(plan)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -270,7 +274,7 @@ def run_device(args, rank, world, dev, dist):
     torch.cuda.synchronize()
     gather_gbs = 5 * npts * reps * (128 if dtype == 0 else 64) / (ga.elapsed_time(gb) * 1e-3) / 1e9
     dsdp.dsdp_plan_destroy(None, plan)
-    return dict(elapsed_ms=elapsed_ms, grid_ms=grid_ms, chain_ms=chain_ms, rescore_ms=rescore_ms,
+    return dict(tile_config=tile_config, elapsed_ms=elapsed_ms, grid_ms=grid_ms, chain_ms=chain_ms, rescore_ms=rescore_ms,
                 total_evals=total_evals, flops=flops, gather_bytes=gather_bytes, clocks=clk,
                 launches_per_step=args.batch + n_plan_kernels, results_ok=results_ok, gather_gbs=gather_gbs)
 
@@ -431,7 +435,9 @@ def main():
         "config": {"workload": "typical-4k", "systems_per_step": args.batch, "receptor_atoms": N_REC,
                    "grid": "80^3 x 8", "map_dtype": args.map_dtype, "ligand": f"{N_LIG} atoms / {T_LIG} torsions",
                    "chains": N_CHAINS, "mc_steps": N_STEPS, "opt_iters": N_ITERS, "optimizer": args.optimizer,
-                   "top_k": TOP_K, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                   "top_k": TOP_K, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
+                   "chain_kernel": {1: "128 regs", 2: "96 regs", 3: "128 regs, work queue",
+                                    4: "96 regs, work queue"}.get(r["tile_config"], "?")},
         "evals_per_s": world * r["total_evals"] * args.steps / (r["elapsed_ms"] * 1e-3),
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
         "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,

@@ -311,10 +311,20 @@ enum {
   DSDP_PLAN_NO_RESCORE = 2  /* stop after the chains (no FP64 rescoring / top-k) */
 };
 /* Prepare a launch of n_jobs jobs (uneven ligands allowed): uploads job and
- * tile tables, sizes scratch (allocated with the ctx allocator).  warps_per_cta
- * 0 = automatic (the autotuned choice if one was recorded). */
+ * tile tables, sizes scratch (allocated with the ctx allocator; ctx may be NULL
+ * for plain cudaMalloc).  One warp runs one chain, one chain per CTA.
+ * tile_config: 0 = automatic (the choice dsdp_plan_autotune recorded for a plan
+ * of the same shape -- map formats, atoms per lane, chain count rounded up to
+ * a power of two -- else the 128-register kernel), 1 = chain kernel limited to
+ * 128 registers (16 warps per SM), 2 = limited to 96 registers (20 warps per
+ * SM). */
 dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
-                             int32_t warps_per_cta, dsdp_plan** out);
+                             int32_t tile_config, dsdp_plan** out);
+/* Autotuner: runs the plan's chain stage `repeats` times for each register
+ * budget, with and without the persistent work queue, keeps the fastest for
+ * this plan and records it for later plans of the same shape (process-wide).
+ * *chosen = 1 + variant + 2 * persistent.  Synchronises the stream. */
+dsdp_status dsdp_plan_autotune(dsdp_plan* plan, void* stream, int32_t repeats, int32_t* chosen);
 /* Enqueue the plan's kernels on `stream` (chains, then FP64 rescoring and
  * top-k).  No allocation and no host synchronisation: a launch can be
  * captured into a CUDA graph and replayed. */

@@ -6,11 +6,25 @@
 
 namespace dsdp {
 
+// Register budgets of the chain kernel: variant 0 caps at 128 registers (16
+// warps per SM, no spills), variant 1 at 96 (20 warps, a few spills); the
+// autotuner picks per plan by measurement.
+template <int VAR>
+struct ChainOcc;
+template <>
+struct ChainOcc<0> {
+  static constexpr int kMinBlocks = 16;  // with 32-thread CTAs: 65536 / (32 * 16) = 128 registers
+};
+template <>
+struct ChainOcc<1> {
+  static constexpr int kMinBlocks = 20;  // 102 -> 96 registers
+};
+
 // Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
 // The job's ligand blob is staged into shared memory once per tile.
 // persistent != 0: CTAs pull tiles from *tile_counter until none are left.
-template <int APL, int FMT>
-__global__ void __launch_bounds__(256, 2) dock_chains_kernel(const DevJob* __restrict__ jobs,
+template <int APL, int FMT, int VAR>
+__global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_kernel(const DevJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles, int n_tiles,
                                                           int* tile_counter, int persistent, int blob_smem,
                                                           int warp_smem) {
@@ -74,24 +88,33 @@ __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_
   if (grad && lane < 6 + T) grad[(size_t)c * (6 + T) + lane] = g;
 }
 
+template <int APL, int FMT, int VAR>
+cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
+  const dim3 block(32);
+  const size_t smem = (size_t)a.blob_smem + (size_t)a.warp_smem;
+  auto k = dock_chains_kernel<APL, FMT, VAR>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = a.grid;
+  if (a.persistent) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32, smem);
+    if (e != cudaSuccess) return e;
+    grid = per_sm * sms < a.n_tiles ? per_sm * sms : a.n_tiles;
+    if (grid < 1) grid = 1;
+  }
+  k<<<grid, block, smem, st>>>(reinterpret_cast<const DevJob*>(a.jobs), reinterpret_cast<const Tile*>(a.tiles),
+                               a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.warp_smem);
+  return cudaGetLastError();
+}
+
 template <int FMT>
 cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
-  const dim3 block(32 * a.warps_per_cta);
-  const size_t smem = (size_t)a.blob_smem + (size_t)a.warps_per_cta * a.warp_smem;
-  const DevJob* jobs = reinterpret_cast<const DevJob*>(a.jobs);
-  const Tile* tiles = reinterpret_cast<const Tile*>(a.tiles);
-  if (a.apl == 1) {
-    auto k = dock_chains_kernel<1, FMT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<a.grid, block, smem, st>>>(jobs, tiles, a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.warp_smem);
-  } else {
-    auto k = dock_chains_kernel<2, FMT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<a.grid, block, smem, st>>>(jobs, tiles, a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.warp_smem);
-  }
-  return cudaGetLastError();
+  if (a.warps_per_cta != 1) return cudaErrorInvalidValue;  // one warp (one chain) per CTA
+  if (a.apl == 1) return a.variant ? launch_chains_var<1, FMT, 1>(a, st) : launch_chains_var<1, FMT, 0>(a, st);
+  return a.variant ? launch_chains_var<2, FMT, 1>(a, st) : launch_chains_var<2, FMT, 0>(a, st);
 }
 
 template <int FMT>

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "launch.h"
@@ -13,7 +14,9 @@ struct dsdp_plan {
   dsdp_ctx* ctx = nullptr;
   int n_jobs = 0;
   uint32_t flags = 0;
-  int warps_per_cta = 2;
+  int warps_per_cta = 1;
+  int variant = 0;        // chain kernel register budget (0: 128, 1: 96)
+  uint64_t tune_key = 0;  // shape key for the autotuner's choice
   int max_chains = 0;
   // one device arena holding job table, tiles, counters and scratch
   void* arena = nullptr;
@@ -93,6 +96,44 @@ static dsdp_status check_view(const dsdp_grid_view* g) {
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Autotuner choices by plan shape: (format mask, atoms-per-lane, log2 of the
+// chain count) -> (variant, persistent).  Written by dsdp_plan_autotune, read
+// by plans created with tile_config 0.
+struct TuneEntry {
+  uint64_t key;
+  int variant, persistent;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+static uint64_t tune_key(uint32_t fmt_mask, int apl, size_t chains) {
+  int lg = 0;
+  while ((size_t(1) << lg) < chains) ++lg;
+  return ((uint64_t)fmt_mask << 16) | ((uint64_t)apl << 8) | (uint64_t)lg;
+}
+
+static bool tune_lookup(uint64_t key, int* variant, int* persistent) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const TuneEntry& t : g_tune)
+    if (t.key == key) {
+      *variant = t.variant;
+      *persistent = t.persistent;
+      return true;
+    }
+  return false;
+}
+
+static void tune_store(uint64_t key, int variant, int persistent) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (TuneEntry& t : g_tune)
+    if (t.key == key) {
+      t.variant = variant;
+      t.persistent = persistent;
+      return;
+    }
+  g_tune.push_back(TuneEntry{key, variant, persistent});
+}
+
 }  // namespace dsdp
 
 using namespace dsdp;
@@ -125,11 +166,11 @@ extern "C" dsdp_status dsdp_score_eval_device(const dsdp_grid_view* grid, const 
 }
 
 extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
-                                        int32_t warps_per_cta, dsdp_plan** out) {
+                                        int32_t tile_config, dsdp_plan** out) {
   if (!out) return set_error(DSDP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_jobs < 1 || !jobs) return set_error(DSDP_ERR_INVALID_ARG, "plan needs >= 1 job");
-  if (warps_per_cta < 0 || warps_per_cta > 8) return set_error(DSDP_ERR_INVALID_ARG, "warps_per_cta outside 0..8");
+  if (tile_config < 0 || tile_config > 2) return set_error(DSDP_ERR_INVALID_ARG, "tile_config outside 0..2");
   std::vector<DevJob> dj(n_jobs);
   std::vector<int> fmt(n_jobs), apl(n_jobs), blob_bytes(n_jobs), pairs(n_jobs), atoms(n_jobs), tors(n_jobs);
   size_t scratch = 0;
@@ -204,9 +245,9 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   P->flags = flags;
   P->max_chains = max_chains;
   P->sms = ctx_sm_count(ctx);
-  // One warp per CTA by default: each chain is scheduled on its own, so no CTA
+  // One warp (one chain) per CTA: each chain is scheduled on its own, so no CTA
   // slot waits for the slowest chain of a tile; the ligand is staged per chain.
-  int W = warps_per_cta > 0 ? warps_per_cta : 1;
+  const int W = 1;
   P->warps_per_cta = W;
   // chain tiles grouped by map format (one launch per format present)
   std::vector<Tile> tiles;
@@ -222,6 +263,22 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
     }
     g.n_tiles = (int)tiles.size() - g.first_tile;
     if (g.n_tiles > 0) P->groups.push_back(g);
+  }
+  {
+    uint32_t fmt_mask = 0;
+    int apl_max = 1;
+    for (const dsdp_plan::Group& g : P->groups) {
+      fmt_mask |= 1u << g.fmt;
+      apl_max = std::max(apl_max, g.apl);
+    }
+    P->tune_key = tune_key(fmt_mask, apl_max, tiles.size());
+    int var = 0, pers = (flags & DSDP_PLAN_PERSISTENT) ? 1 : 0;
+    if (tile_config == 0) {
+      if (tune_lookup(P->tune_key, &var, &pers) && pers) P->flags |= DSDP_PLAN_PERSISTENT;
+    } else {
+      var = tile_config - 1;
+    }
+    P->variant = var;
   }
   std::vector<Tile> rtiles;
   const int rw = rescore_tile_chains();
@@ -300,13 +357,8 @@ extern "C" dsdp_status dsdp_plan_launch_stage(dsdp_plan* P, uint32_t stages, voi
     a.apl = g.apl;
     a.blob_smem = (g.blob_smem + 15) & ~15;
     a.warp_smem = g.warp_smem;
-    if (persistent) {
-      int per_sm = 0;
-      per_sm = std::max(1, 8 / P->warps_per_cta);
-      a.grid = std::min(g.n_tiles, P->sms * per_sm);
-    } else {
-      a.grid = g.n_tiles;
-    }
+    a.variant = P->variant;
+    a.grid = g.n_tiles;  // a persistent launch sizes its grid from the occupancy
     cudaError_t e = launch_chains_dispatch(g.fmt, a, st);
     if (e != cudaSuccess) return check_cuda(e, "dock_chains_kernel launch");
   }
@@ -321,6 +373,50 @@ extern "C" dsdp_status dsdp_plan_launch_stage(dsdp_plan* P, uint32_t stages, voi
 
 extern "C" dsdp_status dsdp_plan_launch(dsdp_plan* P, void* stream) {
   return dsdp_plan_launch_stage(P, DSDP_STAGE_ALL, stream);
+}
+
+extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t repeats, int32_t* chosen) {
+  if (!P) return set_error(DSDP_ERR_INVALID_ARG, "plan is NULL");
+  if (repeats < 1) repeats = 1;
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e != cudaSuccess) return check_cuda(e, "autotune events");
+  const uint32_t base_flags = P->flags & ~(uint32_t)DSDP_PLAN_PERSISTENT;
+  float best = 1e30f;
+  int best_var = P->variant, best_pers = (P->flags & DSDP_PLAN_PERSISTENT) ? 1 : 0;
+  dsdp_status s = DSDP_OK;
+  for (int var = 0; var < 2 && s == DSDP_OK; ++var)
+    for (int pers = 0; pers < 2 && s == DSDP_OK; ++pers) {
+      P->variant = var;
+      P->flags = base_flags | (pers ? DSDP_PLAN_PERSISTENT : 0u);
+      s = dsdp_plan_launch_stage(P, DSDP_STAGE_CHAINS, stream);  // warm-up
+      if (s != DSDP_OK) break;
+      cudaEventRecord(a, st);
+      for (int r = 0; r < repeats && s == DSDP_OK; ++r) s = dsdp_plan_launch_stage(P, DSDP_STAGE_CHAINS, stream);
+      cudaEventRecord(b, st);
+      e = cudaEventSynchronize(b);
+      if (e != cudaSuccess) {
+        s = check_cuda(e, "autotune run");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) {
+        best = ms;
+        best_var = var;
+        best_pers = pers;
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  P->variant = best_var;
+  P->flags = base_flags | (best_pers ? DSDP_PLAN_PERSISTENT : 0u);
+  if (s != DSDP_OK) return s;
+  tune_store(P->tune_key, best_var, best_pers);
+  if (chosen) *chosen = 1 + best_var + 2 * best_pers;
+  return DSDP_OK;
 }
 
 extern "C" dsdp_status dsdp_plan_destroy(dsdp_ctx* ctx, dsdp_plan* P) {

@@ -18,6 +18,7 @@ struct ChainLaunch {
   int apl;            // atoms per lane: 1 (<= 32 atoms) or 2 (<= 64)
   int blob_smem;      // bytes reserved for the largest blob
   int warp_smem;      // bytes of per-warp scratch
+  int variant;        // register budget of the chain kernel (0: 128, 1: 96)
 };
 
 struct ScoreLaunch {

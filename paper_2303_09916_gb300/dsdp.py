@@ -131,6 +131,7 @@ _sig = {
     "dsdp_plan_launch": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "dsdp_plan_launch_stage": (C.c_int32, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "dsdp_plan_kernel_count": (C.c_int32, [C.c_void_p]),
+    "dsdp_plan_autotune": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, P(C.c_int32)]),
     "dsdp_plan_destroy": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "dsdp_gather_bench_device": (C.c_int32, [P(dsdp_grid_view), C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                              C.c_void_p, C.c_void_p]),
@@ -374,11 +375,17 @@ def dsdp_score_eval_device(view: dsdp_grid_view, h_blob, d_blob: int, d_conf: in
                                        int(d_energy), int(d_grad) or None, int(flags), stream or None))
 
 
-def dsdp_plan_create(ctx, jobs, flags=0, warps_per_cta=0):
+def dsdp_plan_create(ctx, jobs, flags=0, tile_config=0):
     arr = (dsdp_job_device * len(jobs))(*jobs)
     out = C.c_void_p()
-    _check(_lib.dsdp_plan_create(ctx, len(jobs), arr, int(flags), int(warps_per_cta), C.byref(out)))
+    _check(_lib.dsdp_plan_create(ctx, len(jobs), arr, int(flags), int(tile_config), C.byref(out)))
     return out.value
+
+
+def dsdp_plan_autotune(plan, stream: int = 0, repeats: int = 1) -> int:
+    chosen = C.c_int32()
+    _check(_lib.dsdp_plan_autotune(plan, stream or None, int(repeats), C.byref(chosen)))
+    return chosen.value
 
 
 def dsdp_plan_launch(plan, stream: int = 0):

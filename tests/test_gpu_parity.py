@@ -374,3 +374,59 @@ def test_determinism_and_batch_independence(ctx):
         assert np.array_equal(r["chain_best_e"], r1["chain_best_e"])
         assert np.array_equal(r["chain_best_conf"], r1["chain_best_conf"])
         assert np.array_equal(r["score"], r1["score"]) and list(r["chain"]) == list(r1["chain"])
+
+
+def test_plan_launch_configurations_agree(ctx):
+    """One uneven batch (ligands of 10-60 atoms, 0-15 torsions, two map formats)
+    through the device plan in every launch configuration the autotuner chooses
+    from -- 128- or 96-register chain kernel, with or without the persistent work
+    queue -- gives bitwise the same chains, and the autotuner returns one of them."""
+    dev = torch.device("cuda", 0)
+    rec = synth.receptor(2000, 51)
+    stream = torch.cuda.current_stream().cuda_stream
+    keep, jobs = [], []
+    for i, (n_atoms, T, dtype) in enumerate([(10, 0, 0), (24, 5, 0), (33, 9, 1), (60, 15, 0), (45, 12, 1)]):
+        lig = synth.ligand(n_atoms, T, 60 + i, center=rec.pocket_center)
+        box = dsdp.make_box(rec.pocket_center, 16.0, 0.375)
+        nb = dsdp.dsdp_grid_map_bytes(box, dtype)
+        maps = torch.empty(nb, dtype=torch.uint8, device=dev)
+        xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
+        ty = torch.from_numpy(rec.xs_type.copy()).to(dev)
+        dsdp.dsdp_grid_build_device(len(ty), xyz.data_ptr(), ty.data_ptr(), box, dtype, 0, maps.data_ptr(), nb, stream)
+        blob = dsdp.dsdp_ligand_pack(lig)
+        nx = 7 + dsdp.dsdp_ligand_blob_info(blob)["n_torsions"]
+        dblob = torch.from_numpy(blob.copy()).to(dev)
+        conf = torch.zeros((48, nx), dtype=torch.float32, device=dev)
+        e = torch.zeros(48, dtype=torch.float32, device=dev)
+        n = [int(np.ceil(16.0 / 0.375))] * 3
+        j = dsdp.dsdp_job_device()
+        j.grid = dsdp.grid_view(maps.data_ptr(), n, [rec.pocket_center[a] - (n[a] - 1) * 0.375 / 2 for a in range(3)],
+                                0.375, dtype)
+        j.receptor = dsdp.dsdp_receptor(len(ty), xyz.data_ptr(), ty.data_ptr())
+        j.h_blob, j.d_blob = blob.ctypes.data, dblob.data_ptr()
+        j.params = dsdp.make_params(n_chains=48, n_mc_steps=3, n_opt_iters=15, seed=i)
+        for a in range(3):
+            j.box_lo[a] = rec.pocket_center[a] - 8.0
+            j.box_size[a] = 16.0
+        j.d_chain_best_conf, j.d_chain_best_e = conf.data_ptr(), e.data_ptr()
+        jobs.append(j)
+        keep.append((maps, xyz, ty, blob, dblob, conf, e))
+    results = []
+    for tile_config in (1, 2):
+        for flags in (0, dsdp.DSDP_PLAN_PERSISTENT):
+            plan = dsdp.dsdp_plan_create(None, jobs, flags | dsdp.DSDP_PLAN_NO_RESCORE, tile_config)
+            try:
+                dsdp.dsdp_plan_launch(plan, stream)
+                torch.cuda.synchronize()
+            finally:
+                dsdp.dsdp_plan_destroy(None, plan)
+            results.append([(k[5].cpu().numpy().copy(), k[6].cpu().numpy().copy()) for k in keep])
+    for other in results[1:]:
+        for (c0, e0), (c1, e1) in zip(results[0], other):
+            assert np.array_equal(c0, c1) and np.array_equal(e0, e1)
+    plan = dsdp.dsdp_plan_create(None, jobs, dsdp.DSDP_PLAN_NO_RESCORE, 0)
+    try:
+        chosen = dsdp.dsdp_plan_autotune(plan, stream, 1)
+    finally:
+        dsdp.dsdp_plan_destroy(None, plan)
+    assert chosen in (1, 2, 3, 4)
