@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--map-dtype", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--tile-config", type=int, default=-1,
+                   help="chain kernel launch configuration: -1 autotune (default), 1/2 fixed register budget")
     return p.parse_args()
 
 
@@ -203,7 +205,12 @@ def run_device(args, rank, world, dev, dist):
     for (d_maps, d_xyz, d_type, *_), box in zip(keep, boxes):
         dsdp.dsdp_grid_build_device(N_REC, d_xyz.data_ptr(), d_type.data_ptr(), box, dtype, dsdp.DSDP_GRID_EQ4,
                                     d_maps.data_ptr(), d_maps.numel(), sptr)
-    tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 1)  # picks register budget and work queue by measurement
+    if args.tile_config < 0:
+        tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 1)  # picks register budget and work queue by measurement
+    else:
+        dsdp.dsdp_plan_destroy(None, plan)
+        plan = dsdp.dsdp_plan_create(None, jobs, 0, args.tile_config)
+        tile_config = args.tile_config
     n_plan_kernels = dsdp.dsdp_plan_kernel_count(plan)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 

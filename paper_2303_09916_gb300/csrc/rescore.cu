@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
                                                                      const Tile* __restrict__ tiles) {
   __shared__ float4 s_rec[kRecTile];
   __shared__ double s_xyz[kRescoreWarps][kMaxAtoms * 3];
+  __shared__ int s_type[kRescoreWarps][kMaxAtoms];
+  __shared__ uint32_t s_list[kRescoreWarps][64];
   const Tile tile = tiles[blockIdx.x];
   const DevJob& J = jobs[tile.job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
                                  : make_double3(0.0, 0.0, 0.0);
       pos[s] = make_double3(Ob.x + r.x, Ob.y + r.y, Ob.z + r.z);
       if (valid[s]) {
+        s_type[warp][i] = type[s];
         s_xyz[warp][3 * i + 0] = pos[s].x;
         s_xyz[warp][3 * i + 1] = pos[s].y;
         s_xyz[warp][3 * i + 2] = pos[s].z;
@@ -110,10 +113,28 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
     type[0] = type[1] = 0;
     pos[0] = pos[1] = make_double3(0.0, 0.0, 0.0);
   }
-  const float pfx[2] = {(float)pos[0].x, (float)pos[1].x}, pfy[2] = {(float)pos[0].y, (float)pos[1].y},
-              pfz[2] = {(float)pos[0].z, (float)pos[1].z};
+  // Inter, exact: for each receptor tile staged in shared memory, the warp scans
+  // (ligand atom, receptor atom) pairs with an FP32 pre-filter (cutoff + 0.05 A),
+  // compacts the survivors into a per-warp list by ballot, and evaluates them in
+  // FP64 32 at a time with every lane busy.
   const float pre2 = (kCutoff + 0.05f) * (kCutoff + 0.05f);
+  uint32_t* list = s_list[warp];
+  int n_list = 0;
   double e_inter = 0.0;
+  auto flush = [&](int count) {
+    if (lane < count) {
+      const uint32_t ent = list[lane];
+      const int i = ent >> 16, k = ent & 0xffff;
+      const float4 a = s_rec[k];
+      const double dx = s_xyz[warp][3 * i] - (double)a.x, dy = s_xyz[warp][3 * i + 1] - (double)a.y,
+                   dz = s_xyz[warp][3 * i + 2] - (double)a.z;
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      if (r < kCutoffD) {
+        const int ti = s_type[warp][i], tj = min(__float_as_int(a.w), 8);
+        e_inter += vina_pair_f64(r - (c_xs_radius_d[ti] + c_xs_radius_d[tj]), pair_bits(ti, tj));
+      }
+    }
+  };
   for (int r0 = 0; r0 < J.n_rec; r0 += kRecTile) {
     const int cnt = min(kRecTile, J.n_rec - r0);
     __syncthreads();
@@ -124,21 +145,35 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
     }
     __syncthreads();
     if (!has_chain) continue;
-    for (int k = 0; k < cnt; ++k) {
-      const float4 a = s_rec[k];
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        if (!valid[s]) continue;
-        const float fx = pfx[s] - a.x, fy = pfy[s] - a.y, fz = pfz[s] - a.z;
-        if (fx * fx + fy * fy + fz * fz >= pre2) continue;
-        const double dx = pos[s].x - (double)a.x, dy = pos[s].y - (double)a.y, dz = pos[s].z - (double)a.z;
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (!(r < kCutoffD)) continue;
-        const int tj = min(__float_as_int(a.w), 8);
-        const double rs = c_xs_radius_d[type[s]] + c_xs_radius_d[tj];
-        e_inter += vina_pair_f64(r - rs, pair_bits(type[s], tj));
+    for (int i = 0; i < N; ++i) {
+      const float px = (float)s_xyz[warp][3 * i], py = (float)s_xyz[warp][3 * i + 1],
+                  pz = (float)s_xyz[warp][3 * i + 2];
+      for (int k0 = 0; k0 < cnt; k0 += 32) {
+        const int k = k0 + lane;
+        bool pass = false;
+        if (k < cnt) {
+          const float4 a = s_rec[k];
+          const float fx = px - a.x, fy = py - a.y, fz = pz - a.z;
+          pass = fx * fx + fy * fy + fz * fz < pre2;
+        }
+        const unsigned bal = __ballot_sync(kFull, pass);
+        if (pass) list[n_list + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)i << 16) | (uint32_t)k;
+        n_list += __popc(bal);
+        __syncwarp();
+        if (n_list >= 32) {
+          flush(32);
+          __syncwarp();
+          const uint32_t rest = lane < n_list - 32 ? list[32 + lane] : 0u;
+          __syncwarp();
+          if (lane < n_list - 32) list[lane] = rest;
+          n_list -= 32;
+          __syncwarp();
+        }
       }
     }
+    flush(n_list);  // the list refers to this tile: empty it before the next one is staged
+    n_list = 0;
+    __syncwarp();
   }
   if (!has_chain) return;
   __syncwarp();
