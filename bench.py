@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--map-dtype", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-forms", dest="forms", action="store_false",
+                   help="skip the one-job-per-launch and uneven-batch (CUDA graph) measurements")
     p.add_argument("--tile-config", type=int, default=-1,
                    help="chain kernel launch configuration: -1 autotune (default), 1/2 fixed register budget")
     return p.parse_args()
@@ -286,6 +288,131 @@ def run_device(args, rank, world, dev, dist):
                 launches_per_step=args.batch + n_plan_kernels, results_ok=results_ok, gather_gbs=gather_gbs)
 
 
+# ---------------------------------------------------------------- other forms of the same work
+def make_device_job(dsdp, torch, dev, rec, lig, seed, box_size, spacing, dtype, n_chains, n_steps, n_iters, top_k,
+                    grid=None):
+    """Device buffers and a dsdp_job_device for one docking job (caller-owned memory)."""
+    box = dsdp.make_box(rec.pocket_center, box_size, spacing)
+    if grid is None:
+        nbytes = dsdp.dsdp_grid_map_bytes(box, dtype, dsdp.DSDP_GRID_EQ4)
+        grid = dict(box=box, maps=torch.empty(nbytes, dtype=torch.uint8, device=dev),
+                    xyz=torch.from_numpy(rec.xyz.copy()).to(dev), type=torch.from_numpy(rec.xs_type.copy()).to(dev))
+    blob = dsdp.dsdp_ligand_pack(lig)
+    info = dsdp.dsdp_ligand_blob_info(blob)
+    nx = 7 + info["n_torsions"]
+    keep = dict(grid=grid, blob=blob, d_blob=torch.from_numpy(blob.copy()).to(dev), info=info,
+                conf=torch.empty((n_chains, nx), dtype=torch.float32, device=dev),
+                e=torch.empty(n_chains, dtype=torch.float32, device=dev),
+                evals=torch.zeros(n_chains, dtype=torch.int32, device=dev),
+                n=torch.zeros(1, dtype=torch.int32, device=dev),
+                chain=torch.zeros(top_k, dtype=torch.int32, device=dev),
+                score=torch.zeros(top_k, dtype=torch.float64, device=dev))
+    n = [int(np.ceil(box_size / spacing))] * 3
+    j = dsdp.dsdp_job_device()
+    j.grid = dsdp.grid_view(grid["maps"].data_ptr(), n,
+                            [rec.pocket_center[a] - (n[a] - 1) * spacing / 2 for a in range(3)], spacing, dtype,
+                            dsdp.DSDP_GRID_EQ4)
+    j.receptor = dsdp.dsdp_receptor(len(rec.xs_type), grid["xyz"].data_ptr(), grid["type"].data_ptr())
+    j.h_blob = blob.ctypes.data
+    j.d_blob = keep["d_blob"].data_ptr()
+    j.params = dsdp.make_params(n_chains=n_chains, n_mc_steps=n_steps, n_opt_iters=n_iters, seed=seed, top_k=top_k)
+    for a in range(3):
+        j.box_lo[a] = rec.pocket_center[a] - box_size / 2
+        j.box_size[a] = box_size
+    j.d_chain_best_conf, j.d_chain_best_e = keep["conf"].data_ptr(), keep["e"].data_ptr()
+    j.d_chain_evals = keep["evals"].data_ptr()
+    j.d_out_n, j.d_out_chain, j.d_out_score = keep["n"].data_ptr(), keep["chain"].data_ptr(), keep["score"].data_ptr()
+    return j, keep
+
+
+def build_grid(dsdp, grid, dtype, sptr):
+    dsdp.dsdp_grid_build_device(len(grid["type"]), grid["xyz"].data_ptr(), grid["type"].data_ptr(), grid["box"],
+                                dtype, dsdp.DSDP_GRID_EQ4, grid["maps"].data_ptr(), grid["maps"].numel(), sptr)
+
+
+def run_one_job_per_launch(args, rank, dev, steps):
+    """The plain form: each system alone -- its grid, then a one-job plan -- one after another."""
+    import torch
+    from paper_2303_09916_gb300 import dsdp
+
+    sptr = torch.cuda.current_stream().cuda_stream
+    dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
+    items = []
+    for seed, rec, lig in systems(rank, args.batch):
+        j, keep = make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dtype, N_CHAINS, N_STEPS, N_ITERS,
+                                  TOP_K)
+        items.append((dsdp.dsdp_plan_create(None, [j], 0, 1), keep))
+    lat = []
+
+    def one_pass(record):
+        for plan, keep in items:
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            build_grid(dsdp, keep["grid"], dtype, sptr)
+            dsdp.dsdp_plan_launch(plan, sptr)
+            b.record()
+            if record:
+                lat.append((a, b))
+
+    one_pass(False)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    t0.record()
+    for _ in range(steps):
+        one_pass(True)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in lat]
+    for plan, _ in items:
+        dsdp.dsdp_plan_destroy(None, plan)
+    return dict(systems_per_s=steps * len(items) / (t0.elapsed_time(t1) * 1e-3),
+                latency_p50_ms=float(np.percentile(ms, 50)), latency_p99_ms=float(np.percentile(ms, 99)))
+
+
+def run_uneven_graph(args, dev, steps=3):
+    """Batched uneven launch: one 5,000-atom receptor, 256 ligands of 10-60 atoms and
+    0-15 torsions, 128 chains each, all in one plan replayed from a captured CUDA graph."""
+    import torch
+    from paper_2303_09916_gb300 import dsdp, synth
+
+    cfg = synth.config("uneven-5k", seed=0)
+    rec = cfg.receptor
+    sptr = torch.cuda.current_stream().cuda_stream
+    jobs, keeps, grid = [], [], None
+    for i, lig in enumerate(cfg.ligands):
+        j, keep = make_device_job(dsdp, torch, dev, rec, lig, i, 26.0, SPACING, dsdp.DSDP_MAP_F32, cfg.n_chains,
+                                  cfg.n_mc_steps, N_ITERS, TOP_K, grid=grid)
+        grid = keep["grid"]
+        jobs.append(j)
+        keeps.append(keep)
+    build_grid(dsdp, grid, dsdp.DSDP_MAP_F32, sptr)
+    plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
+    chosen = dsdp.dsdp_plan_autotune(plan, sptr, 1)
+    cap = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=cap):
+        dsdp.dsdp_plan_launch(plan, cap.cuda_stream)
+    graph.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+    a.record()
+    for _ in range(steps):
+        graph.replay()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    evals = sum(int(k["evals"].sum().item()) for k in keeps)
+    ok = all(int(k["n"].item()) >= 1 for k in keeps)
+    dsdp.dsdp_plan_destroy(None, plan)
+    atoms = [lig.n_atoms for lig in cfg.ligands]
+    return dict(ligands_per_s=len(jobs) / (ms * 1e-3), ms_per_launch=ms, evals_per_s=evals / (ms * 1e-3),
+                ligand_atoms=f"{min(atoms)}-{max(atoms)}", chains_per_ligand=cfg.n_chains,
+                chain_kernel={1: "128 regs", 2: "96 regs", 3: "128 regs, work queue",
+                              4: "96 regs, work queue"}.get(chosen, "?"), launch="captured CUDA graph",
+                results_ok=ok)
+
+
 # ---------------------------------------------------------------- host API (end to end)
 def run_e2e(args, rank, dev):
     import torch
@@ -419,6 +546,8 @@ def main():
         dist.barrier()
     r = run_device(args, rank, world, local, dist)
     e2e = run_e2e(args, rank, local) if args.e2e_steps > 0 else None
+    single = run_one_job_per_launch(args, rank, local, 2) if args.forms else None
+    uneven = run_uneven_graph(args, local) if args.forms and rank == 0 else None
     if dist:
         t = torch.tensor([e2e["value"] if e2e else 0.0], dtype=torch.float64, device=local)
         dist.all_reduce(t)
@@ -462,6 +591,14 @@ def main():
         line["e2e"] = {"value": e2e["value"], "unit": "systems/s", "h2d_bytes_per_step": e2e["h2d"],
                        "d2h_bytes_per_step": e2e["d2h"], "latency_p50_ms": e2e["p50_ms"],
                        "latency_p99_ms": e2e["p99_ms"]}
+    if single:
+        line["forms"] = {"batched_plan": {"systems_per_s": value, "note": f"{args.batch} systems per launch"},
+                         "one_job_per_launch": single,
+                         "served_host_api": {"systems_per_s": e2e["value"] if e2e else None,
+                                             "latency_p50_ms": e2e["p50_ms"] if e2e else None,
+                                             "latency_p99_ms": e2e["p99_ms"] if e2e else None}}
+    if uneven:
+        line["uneven_5k_batch"] = uneven
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

@@ -66,7 +66,7 @@ struct Conf {
   float th;
 };
 
-// Per-warp shared scratch (layout in warp_scratch_bytes).
+// Per-warp shared scratch (layout in scratch_layout).
 struct WarpScratch {
   float4* coords;  // [kMaxAtoms] atom positions
   float4* pre;     // [kMaxAtoms][2] inclusive prefix sums of (g, (r - p) x g): (gx, gy, gz, cx), (cy, cz, -, -)
@@ -77,27 +77,34 @@ struct WarpScratch {
 };
 
 constexpr int kConfFloats = 7 + kMaxDim;
-__host__ __device__ constexpr int warp_scratch_fixed_bytes() {
-  return 16 * kMaxAtoms + 32 * kMaxAtoms + ((4 * kMaxDim * kMaxDim + 15) & ~15) + 2 * ((4 * kConfFloats + 15) & ~15);
-}
+__host__ __device__ constexpr int align16i(int x) { return (x + 15) & ~15; }
+// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions, pairs).
 // One atom per lane keeps each pair's force vector (16 B); two atoms per lane
 // (up to 2016 pairs) keep one scalar per pair (4 B) to bound shared memory.
-__host__ __device__ inline int warp_scratch_bytes(int n_pairs, int apl) {
-  return warp_scratch_fixed_bytes() + (((apl == 1 ? 16 : 4) * n_pairs + 15) & ~15);
+// H rows keep the stride kMaxDim (odd: lanes hit distinct banks).
+struct ScratchLayout {
+  int coords, pre, H, cur, best, pair, bytes;
+};
+__host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsions, int n_pairs, int apl) {
+  ScratchLayout l;
+  const int D = 6 + n_torsions;
+  l.coords = 0;
+  l.pre = l.coords + align16i(16 * n_atoms);
+  l.H = l.pre + align16i(32 * n_atoms);
+  l.cur = l.H + align16i(4 * kMaxDim * D);
+  l.best = l.cur + align16i(4 * kConfFloats);
+  l.pair = l.best + align16i(4 * kConfFloats);
+  l.bytes = l.pair + align16i((apl == 1 ? 16 : 4) * n_pairs);
+  return l;
 }
-__device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base) {
+__device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base, const ScratchLayout& l) {
   WarpScratch W;
-  W.coords = reinterpret_cast<float4*>(base);
-  base += 16 * kMaxAtoms;
-  W.pre = reinterpret_cast<float4*>(base);
-  base += 32 * kMaxAtoms;
-  W.H = reinterpret_cast<float*>(base);
-  base += (4 * kMaxDim * kMaxDim + 15) & ~15;
-  W.cur = reinterpret_cast<float*>(base);
-  base += (4 * kConfFloats + 15) & ~15;
-  W.best = reinterpret_cast<float*>(base);
-  base += (4 * kConfFloats + 15) & ~15;
-  W.pair = reinterpret_cast<float*>(base);
+  W.coords = reinterpret_cast<float4*>(base + l.coords);
+  W.pre = reinterpret_cast<float4*>(base + l.pre);
+  W.H = reinterpret_cast<float*>(base + l.H);
+  W.cur = reinterpret_cast<float*>(base + l.cur);
+  W.best = reinterpret_cast<float*>(base + l.best);
+  W.pair = reinterpret_cast<float*>(base + l.pair);
   return W;
 }
 
@@ -167,14 +174,18 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     const float3 Ob = shfl3(O, b);
     pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
   }
-  // ---- inter: grid maps
+  // ---- inter, part 1: locate each atom's cell and ask L2 for its 8 corners now,
+  //      so that the pair terms below overlap the gather latency
+  MapCell cell[APL];
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    cell[s] = map_cell(M, pos[s]);
+    if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) map_prefetch<FMT>(M, type[s], cell[s]);
+  }
   float e_lane = 0.f;
   float3 g[APL];
 #pragma unroll
-  for (int s = 0; s < APL; ++s) {
-    g[s] = make_float3(0.f, 0.f, 0.f);
-    if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) e_lane += sample_map<FMT>(M, type[s], pos[s], g[s]);
-  }
+  for (int s = 0; s < APL; ++s) g[s] = make_float3(0.f, 0.f, 0.f);
   // ---- intra: each pair once, its force gathered by both atoms
   if (flags & DSDP_TERM_INTRA) {
 #pragma unroll
@@ -229,6 +240,15 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       g[s].x += gx;
       g[s].y += gy;
       g[s].z += gz;
+    }
+  }
+  // ---- inter, part 2: trilinear score and gradient (Eq. 2, Eq. 4 / Eq. 3)
+#pragma unroll
+  for (int s = 0; s < APL; ++s) {
+    if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) {
+      float3 gi;
+      e_lane += map_interp<FMT>(M, type[s], cell[s], gi);
+      g[s] = g[s] + gi;
     }
   }
   const float E = warp_sum(e_lane);

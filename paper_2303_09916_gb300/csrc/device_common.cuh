@@ -264,22 +264,62 @@ struct MapView {
   float h, inv_h;
 };
 
-// Trilinear score (Eq. 2) and gradient (Eq. 4 from the gradient maps, or
-// Eq. 3 as the derivative of the interpolant) at r for map type t, with the
-// out-of-grid wall: evaluated at the clamped point plus kWallSlope per
-// Angstrom of excess along each axis; along such an axis the gradient is the
-// wall slope.
-template <int FMT>
-__device__ __forceinline__ float sample_map(const MapView& M, int t, float3 r, float3& g) {
+// Cell of a point in the grid: clamped position u = (r - origin) / h in
+// [0, n - 1], cell index (lower corner, at most n - 2), fractions within the
+// cell, and the signed excess (Angstrom) along each axis outside the grid.
+struct MapCell {
+  unsigned base;     // node index of corner (ix, iy, iz) of type 0; add type * nxyz
+  float fx, fy, fz;
+  float ex, ey, ez;
+};
+
+__device__ __forceinline__ MapCell map_cell(const MapView& M, float3 r) {
   const float ux = (r.x - M.ox) * M.inv_h, uy = (r.y - M.oy) * M.inv_h, uz = (r.z - M.oz) * M.inv_h;
   const float cx = fminf(fmaxf(ux, 0.f), (float)(M.nx - 1));
   const float cy = fminf(fmaxf(uy, 0.f), (float)(M.ny - 1));
   const float cz = fminf(fmaxf(uz, 0.f), (float)(M.nz - 1));
   const int ix = min((int)cx, M.nx - 2), iy = min((int)cy, M.ny - 2), iz = min((int)cz, M.nz - 2);
-  const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
+  MapCell c;
   // 32-bit node indices: the host rejects grids with 8 nx ny nz >= 2^31 nodes.
+  c.base = ((unsigned)iz * (unsigned)M.ny + (unsigned)iy) * (unsigned)M.nx + (unsigned)ix;
+  c.fx = cx - (float)ix;
+  c.fy = cy - (float)iy;
+  c.fz = cz - (float)iz;
+  c.ex = (ux - cx) * M.h;
+  c.ey = (uy - cy) * M.h;
+  c.ez = (uz - cz) * M.h;
+  return c;
+}
+
+// Ask L2 to fetch the 8 corners of a cell for map type t (no registers held;
+// the loads of map_interp later find them there).
+template <int FMT>
+__device__ __forceinline__ void map_prefetch(const MapView& M, int t, const MapCell& c) {
   const unsigned sxy = (unsigned)M.nx * (unsigned)M.ny;
-  const unsigned base = ((unsigned)t * (unsigned)M.nz + (unsigned)iz) * sxy + (unsigned)iy * (unsigned)M.nx + ix;
+  const unsigned b = (unsigned)t * sxy * (unsigned)M.nz + c.base;
+  const unsigned nb = (unsigned)(fmt_channels(FMT) * fmt_elem_bytes(FMT));
+  const char* p = reinterpret_cast<const char*>(M.maps);
+  const unsigned off[4] = {b, b + M.nx, b + sxy, b + sxy + M.nx};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    // corners x and x + 1 are adjacent: one prefetch per 128-byte line they touch
+    const char* a0 = p + (size_t)off[k] * nb;
+    const char* a1 = a0 + 2 * nb - 1;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a0));
+    if ((reinterpret_cast<uintptr_t>(a0) >> 7) != (reinterpret_cast<uintptr_t>(a1) >> 7))
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a1));
+  }
+}
+
+// Trilinear score (Eq. 2) and gradient (Eq. 4 from the gradient maps, or
+// Eq. 3 as the derivative of the interpolant) for map type t in cell c, with the
+// out-of-grid wall: evaluated at the clamped point plus kWallSlope per
+// Angstrom of excess along each axis; along such an axis the gradient is the
+// wall slope.
+template <int FMT>
+__device__ __forceinline__ float map_interp(const MapView& M, int t, const MapCell& c, float3& g) {
+  const unsigned sxy = (unsigned)M.nx * (unsigned)M.ny;
+  const unsigned base = (unsigned)t * sxy * (unsigned)M.nz + c.base;
   const float4 v000 = load_node<FMT>(M.maps, base);
   const float4 v100 = load_node<FMT>(M.maps, base + 1);
   const float4 v010 = load_node<FMT>(M.maps, base + M.nx);
@@ -288,6 +328,7 @@ __device__ __forceinline__ float sample_map(const MapView& M, int t, float3 r, f
   const float4 v101 = load_node<FMT>(M.maps, base + sxy + 1);
   const float4 v011 = load_node<FMT>(M.maps, base + sxy + M.nx);
   const float4 v111 = load_node<FMT>(M.maps, base + sxy + M.nx + 1);
+  const float fx = c.fx, fy = c.fy, fz = c.fz;
   const float gx0 = 1.f - fx, gy0 = 1.f - fy, gz0 = 1.f - fz;
   const float w000 = gx0 * gy0 * gz0, w100 = fx * gy0 * gz0, w010 = gx0 * fy * gz0, w110 = fx * fy * gz0;
   const float w001 = gx0 * gy0 * fz, w101 = fx * gy0 * fz, w011 = gx0 * fy * fz, w111 = fx * fy * fz;
@@ -312,20 +353,24 @@ __device__ __forceinline__ float sample_map(const MapView& M, int t, float3 r, f
     g.y = (e1 - e0) * M.inv_h;
     g.z = (d1 - d0) * M.inv_h;
   }
-  const float ex = (ux - cx) * M.h, ey = (uy - cy) * M.h, ez = (uz - cz) * M.h;
-  if (ex != 0.f) {
-    e += kWallSlope * fabsf(ex);
-    g.x = ex > 0.f ? kWallSlope : -kWallSlope;
+  if (c.ex != 0.f) {
+    e += kWallSlope * fabsf(c.ex);
+    g.x = c.ex > 0.f ? kWallSlope : -kWallSlope;
   }
-  if (ey != 0.f) {
-    e += kWallSlope * fabsf(ey);
-    g.y = ey > 0.f ? kWallSlope : -kWallSlope;
+  if (c.ey != 0.f) {
+    e += kWallSlope * fabsf(c.ey);
+    g.y = c.ey > 0.f ? kWallSlope : -kWallSlope;
   }
-  if (ez != 0.f) {
-    e += kWallSlope * fabsf(ez);
-    g.z = ez > 0.f ? kWallSlope : -kWallSlope;
+  if (c.ez != 0.f) {
+    e += kWallSlope * fabsf(c.ez);
+    g.z = c.ez > 0.f ? kWallSlope : -kWallSlope;
   }
   return e;
+}
+
+template <int FMT>
+__device__ __forceinline__ float sample_map(const MapView& M, int t, float3 r, float3& g) {
+  return map_interp<FMT>(M, t, map_cell(M, r), g);
 }
 
 __host__ __device__ inline MapView make_map_view(const DevJob& J) {

@@ -27,12 +27,12 @@ template <int APL, int FMT, int VAR>
 __global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_kernel(const DevJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles, int n_tiles,
                                                           int* tile_counter, int persistent, int blob_smem,
-                                                          int warp_smem) {
+                                                          ScratchLayout lay) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_tile;
   __shared__ int s_job;
   const int warp = threadIdx.x >> 5;
-  const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * warp_smem);
+  const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * lay.bytes, lay);
   if (threadIdx.x == 0) s_job = -1;
   __syncthreads();
   int t = blockIdx.x;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_ker
     const DevJob& J = jobs[tile.job];
     if (s_job != tile.job) {  // uniform: s_job only changes between barriers
       __syncthreads();
-      const int words = reinterpret_cast<const BlobHeader*>(J.blob)->bytes / 16;
+      const int words = reinterpret_cast<const BlobHeader*>(J.blob)->stage_bytes / 16;
       for (int i = threadIdx.x; i < words; i += blockDim.x)
         reinterpret_cast<int4*>(smem)[i] = __ldg(reinterpret_cast<const int4*>(J.blob) + i);
       __syncthreads();
@@ -66,15 +66,15 @@ template <int APL, int FMT>
 __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_t* __restrict__ blob,
                                                          const float* __restrict__ conf, int n_conf,
                                                          float* __restrict__ energy, float* __restrict__ grad,
-                                                         uint32_t flags, int blob_smem, int warp_smem) {
+                                                         uint32_t flags, int blob_smem, ScratchLayout lay) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int words = reinterpret_cast<const BlobHeader*>(blob)->bytes / 16;
+  const int words = reinterpret_cast<const BlobHeader*>(blob)->stage_bytes / 16;
   for (int i = threadIdx.x; i < words; i += blockDim.x)
     reinterpret_cast<int4*>(smem)[i] = __ldg(reinterpret_cast<const int4*>(blob) + i);
   __syncthreads();
   const LigView L = view_blob(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * warp_smem);
+  const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * lay.bytes, lay);
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= n_conf) return;
   LaneLig<APL> R;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_
 template <int APL, int FMT, int VAR>
 cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
   const dim3 block(32);
-  const size_t smem = (size_t)a.blob_smem + (size_t)a.warp_smem;
+  const size_t smem = (size_t)a.blob_smem + (size_t)a.scratch.bytes;
   auto k = dock_chains_kernel<APL, FMT, VAR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -106,7 +106,7 @@ cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
     if (grid < 1) grid = 1;
   }
   k<<<grid, block, smem, st>>>(reinterpret_cast<const DevJob*>(a.jobs), reinterpret_cast<const Tile*>(a.tiles),
-                               a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.warp_smem);
+                               a.n_tiles, a.tile_counter, a.persistent, a.blob_smem, a.scratch);
   return cudaGetLastError();
 }
 
@@ -121,18 +121,18 @@ template <int FMT>
 cudaError_t launch_score_impl(const ScoreLaunch& a, cudaStream_t st) {
   const int wpc = 4;
   const dim3 block(32 * wpc), grid((a.n_conf + wpc - 1) / wpc);
-  const size_t smem = (size_t)a.blob_smem + (size_t)wpc * a.warp_smem;
+  const size_t smem = (size_t)a.blob_smem + (size_t)wpc * a.scratch.bytes;
   const MapView M = a.map;
   if (a.apl == 1) {
     auto k = score_eval_kernel<1, FMT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, block, smem, st>>>(M, a.blob, a.conf, a.n_conf, a.energy, a.grad, a.flags, a.blob_smem, a.warp_smem);
+    k<<<grid, block, smem, st>>>(M, a.blob, a.conf, a.n_conf, a.energy, a.grad, a.flags, a.blob_smem, a.scratch);
   } else {
     auto k = score_eval_kernel<2, FMT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, block, smem, st>>>(M, a.blob, a.conf, a.n_conf, a.energy, a.grad, a.flags, a.blob_smem, a.warp_smem);
+    k<<<grid, block, smem, st>>>(M, a.blob, a.conf, a.n_conf, a.energy, a.grad, a.flags, a.blob_smem, a.scratch);
   }
   return cudaGetLastError();
 }

@@ -38,7 +38,8 @@ struct BlobHeader {
   uint32_t off_atom64;     // double[n_atoms][3]: local xyz in FP64 (rescoring)
   uint32_t off_body64;     // double[n_bodies][6]: origin offset and unit axis in FP64 (rescoring)
   uint32_t off_pair_tab;   // float2[64]: for type pair t_i * 8 + t_j: (R_i + R_j, bits 1 hydrophobic | 2 H-bond)
-  int32_t pad[2];
+  uint32_t stage_bytes;    // prefix the FP32 kernels stage into shared memory (the FP64 geometry follows it)
+  int32_t pad[1];
 };
 static_assert(sizeof(BlobHeader) % 16 == 0, "blob header alignment");
 

@@ -8,7 +8,6 @@
 #include <vector>
 
 #include "launch.h"
-#include "chain_device.cuh"
 
 struct dsdp_plan {
   dsdp_ctx* ctx = nullptr;
@@ -22,7 +21,7 @@ struct dsdp_plan {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   struct Group {
-    int fmt, apl, first_tile, n_tiles, blob_smem, warp_smem;
+    int fmt, apl, first_tile, n_tiles, blob_smem, max_atoms, max_torsions, max_pairs;
   };
   std::vector<Group> groups;
   void* d_jobs = nullptr;
@@ -34,8 +33,6 @@ struct dsdp_plan {
 };
 
 namespace dsdp {
-
-int warp_scratch_bytes_host(int n_pairs, int apl) { return warp_scratch_bytes(n_pairs, apl); }
 
 dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) {
   if (!in) return set_error(DSDP_ERR_INVALID_ARG, "dock params NULL");
@@ -159,8 +156,8 @@ extern "C" dsdp_status dsdp_score_eval_device(const dsdp_grid_view* grid, const 
   a.grad = d_grad;
   a.flags = flags;
   a.apl = n_atoms <= 32 ? 1 : 2;
-  a.blob_smem = (int)((const BlobHeader*)h_blob)->bytes;
-  a.warp_smem = warp_scratch_bytes_host(P, a.apl);
+  a.blob_smem = (int)((const BlobHeader*)h_blob)->stage_bytes;
+  a.scratch = scratch_layout(n_atoms, T, P, a.apl);
   return check_cuda(launch_score_dispatch(map_fmt(grid->dtype, grid->mode), a, (cudaStream_t)stream),
                     "score_eval_kernel launch");
 }
@@ -193,7 +190,7 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
     if (p.trace && !J.d_trace) return set_error(DSDP_ERR_INVALID_ARG, "job %d: trace requested without d_trace", j);
     fmt[j] = map_fmt(J.grid.dtype, J.grid.mode);
     apl[j] = atoms[j] <= 32 ? 1 : 2;
-    blob_bytes[j] = (int)((const BlobHeader*)J.h_blob)->bytes;
+    blob_bytes[j] = (int)((const BlobHeader*)J.h_blob)->stage_bytes;
     max_chains = std::max(max_chains, p.n_chains);
     const int nx = 7 + tors[j];
     if (!J.d_chain_best_conf) scratch += up256(sizeof(float) * (size_t)p.n_chains * nx);
@@ -252,13 +249,15 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   // chain tiles grouped by map format (one launch per format present)
   std::vector<Tile> tiles;
   for (int f = 0; f < 6; ++f) {
-    dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0};
+    dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0, 0, 0};
     for (int j = 0; j < n_jobs; ++j)
       if (fmt[j] == f) g.apl = std::max(g.apl, apl[j]);  // the group runs at its largest ligand's tile
     for (int j = 0; j < n_jobs; ++j) {
       if (fmt[j] != f) continue;
       g.blob_smem = std::max(g.blob_smem, blob_bytes[j]);
-      g.warp_smem = std::max(g.warp_smem, warp_scratch_bytes_host(pairs[j], g.apl));
+      g.max_atoms = std::max(g.max_atoms, atoms[j]);
+      g.max_torsions = std::max(g.max_torsions, tors[j]);
+      g.max_pairs = std::max(g.max_pairs, pairs[j]);
       for (int c = 0; c < dj[j].n_chains; c += W) tiles.push_back(Tile{j, c, std::min(W, dj[j].n_chains - c), 0});
     }
     g.n_tiles = (int)tiles.size() - g.first_tile;
@@ -356,7 +355,7 @@ extern "C" dsdp_status dsdp_plan_launch_stage(dsdp_plan* P, uint32_t stages, voi
     a.warps_per_cta = P->warps_per_cta;
     a.apl = g.apl;
     a.blob_smem = (g.blob_smem + 15) & ~15;
-    a.warp_smem = g.warp_smem;
+    a.scratch = scratch_layout(g.max_atoms, g.max_torsions, g.max_pairs, g.apl);
     a.variant = P->variant;
     a.grid = g.n_tiles;  // a persistent launch sizes its grid from the occupancy
     cudaError_t e = launch_chains_dispatch(g.fmt, a, st);

@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "device_common.cuh"
+#include "chain_device.cuh"
 
 namespace dsdp {
 
@@ -16,8 +16,8 @@ struct ChainLaunch {
   int grid;           // CTAs
   int warps_per_cta;
   int apl;            // atoms per lane: 1 (<= 32 atoms) or 2 (<= 64)
-  int blob_smem;      // bytes reserved for the largest blob
-  int warp_smem;      // bytes of per-warp scratch
+  int blob_smem;      // bytes reserved for the largest staged blob prefix
+  ScratchLayout scratch;  // per-warp scratch, sized for the group's largest ligand
   int variant;        // register budget of the chain kernel (0: 128, 1: 96)
 };
 
@@ -31,7 +31,7 @@ struct ScoreLaunch {
   uint32_t flags;
   int apl;
   int blob_smem;
-  int warp_smem;
+  ScratchLayout scratch;
 };
 
 #define DSDP_DECLARE_FMT(F)                                               \
@@ -49,6 +49,5 @@ MapView map_view_of(const dsdp_grid_view* g);
 cudaError_t launch_rescore(const void* jobs, const void* tiles, int n_tiles, cudaStream_t st);
 int rescore_tile_chains();
 cudaError_t launch_topk(const void* jobs, int n_jobs, int max_chains, cudaStream_t st);
-int warp_scratch_bytes_host(int n_pairs, int apl);
 
 }  // namespace dsdp

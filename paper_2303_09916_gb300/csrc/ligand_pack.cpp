@@ -301,12 +301,13 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   off = align16(off + 4 * (size_t)p.csr.size());
   h.off_torsion_body = (uint32_t)off;
   off = align16(off + 4 * (size_t)p.T);
+  h.off_pair_tab = (uint32_t)off;
+  off = align16(off + 8 * 64);
+  h.stage_bytes = (uint32_t)off;  // the chain kernels stage only this prefix
   h.off_atom64 = (uint32_t)off;
   off = align16(off + 8 * 3 * (size_t)p.n);
   h.off_body64 = (uint32_t)off;
   off = align16(off + 8 * 6 * (size_t)p.B);
-  h.off_pair_tab = (uint32_t)off;
-  off = align16(off + 8 * 64);
   h.magic = kBlobMagic;
   h.bytes = (uint32_t)off;
   h.n_atoms = p.n;

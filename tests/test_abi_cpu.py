@@ -35,9 +35,10 @@ def test_status_strings_and_version():
 
 
 def _parse_blob(blob):
-    hdr = struct.unpack_from("<2I5if3fi9I", blob, 0)
+    hdr = struct.unpack_from("<2I5if3fi11I", blob, 0)
     keys = ["magic", "bytes", "n_atoms", "T", "n_bodies", "n_pairs", "rounds", "gyr", "rx", "ry", "rz", "root_atom",
-            "off_atom", "off_user", "off_body", "off_pairs", "off_csr_start", "off_csr", "off_tb", "off_a64", "off_b64"]
+            "off_atom", "off_user", "off_body", "off_pairs", "off_csr_start", "off_csr", "off_tb", "off_a64", "off_b64",
+            "off_tab", "stage_bytes"]
     h = dict(zip(keys, hdr))
     n, P = h["n_atoms"], h["n_pairs"]
     user = np.frombuffer(blob, dtype=np.int32, count=n, offset=h["off_user"])
@@ -57,6 +58,10 @@ def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
     h, user, body, pairs, csr_start, csr, brec = _parse_blob(bytes(blob))
     ol = oracle.Ligand(lig.xyz.astype(np.float64), lig.xs_type, lig.bonds, lig.rotatable)
     assert h["magic"] == 0x50445344 and h["bytes"] == len(blob) and h["bytes"] % 16 == 0
+    # the FP32 kernels stage a prefix holding every table they read; the FP64 geometry follows it
+    assert h["stage_bytes"] % 16 == 0 and h["stage_bytes"] <= h["off_a64"] < h["off_b64"] < h["bytes"]
+    assert max(h["off_atom"], h["off_user"], h["off_body"], h["off_pairs"], h["off_csr_start"], h["off_csr"],
+               h["off_tb"], h["off_tab"]) < h["stage_bytes"]
     assert (h["n_atoms"], h["T"], h["n_bodies"], h["n_pairs"]) == (ol.n_atoms, ol.T, ol.n_bodies, ol.n_pairs)
     assert h["root_atom"] == ol.root_atom
     assert h["gyr"] == pytest.approx(ol.gyration_radius, rel=1e-6)

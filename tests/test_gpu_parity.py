@@ -430,3 +430,62 @@ def test_plan_launch_configurations_agree(ctx):
     finally:
         dsdp.dsdp_plan_destroy(None, plan)
     assert chosen in (1, 2, 3, 4)
+
+
+def test_plan_replayed_from_a_cuda_graph_matches_the_eager_launch(ctx):
+    """A plan launch captured into a CUDA graph (persistent work queue included)
+    replays with bitwise the eager results, twice in a row."""
+    dev = torch.device("cuda", 0)
+    rec = synth.receptor(1500, 71)
+    stream = torch.cuda.current_stream().cuda_stream
+    box = dsdp.make_box(rec.pocket_center, 14.0, 0.375)
+    nb = dsdp.dsdp_grid_map_bytes(box)
+    maps = torch.empty(nb, dtype=torch.uint8, device=dev)
+    xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
+    ty = torch.from_numpy(rec.xs_type.copy()).to(dev)
+    dsdp.dsdp_grid_build_device(len(ty), xyz.data_ptr(), ty.data_ptr(), box, 0, 0, maps.data_ptr(), nb, stream)
+    keep, jobs = [], []
+    for i, (na, T) in enumerate([(14, 3), (37, 10), (22, 6)]):
+        lig = synth.ligand(na, T, 80 + i, center=rec.pocket_center)
+        blob = dsdp.dsdp_ligand_pack(lig)
+        nx = 7 + dsdp.dsdp_ligand_blob_info(blob)["n_torsions"]
+        d = dict(blob=blob, dblob=torch.from_numpy(blob.copy()).to(dev),
+                 conf=torch.zeros((40, nx), dtype=torch.float32, device=dev),
+                 e=torch.zeros(40, dtype=torch.float32, device=dev), n=torch.zeros(1, dtype=torch.int32, device=dev),
+                 chain=torch.zeros(4, dtype=torch.int32, device=dev),
+                 score=torch.zeros(4, dtype=torch.float64, device=dev))
+        n = [int(np.ceil(14.0 / 0.375))] * 3
+        j = dsdp.dsdp_job_device()
+        j.grid = dsdp.grid_view(maps.data_ptr(), n, [rec.pocket_center[a] - (n[a] - 1) * 0.375 / 2 for a in range(3)],
+                                0.375)
+        j.receptor = dsdp.dsdp_receptor(len(ty), xyz.data_ptr(), ty.data_ptr())
+        j.h_blob, j.d_blob = blob.ctypes.data, d["dblob"].data_ptr()
+        j.params = dsdp.make_params(n_chains=40, n_mc_steps=3, n_opt_iters=15, seed=i, top_k=4)
+        for a in range(3):
+            j.box_lo[a] = rec.pocket_center[a] - 7.0
+            j.box_size[a] = 14.0
+        j.d_chain_best_conf, j.d_chain_best_e = d["conf"].data_ptr(), d["e"].data_ptr()
+        j.d_out_n, j.d_out_chain, j.d_out_score = d["n"].data_ptr(), d["chain"].data_ptr(), d["score"].data_ptr()
+        jobs.append(j)
+        keep.append(d)
+    plan = dsdp.dsdp_plan_create(None, jobs, dsdp.DSDP_PLAN_PERSISTENT, 1)
+    try:
+        dsdp.dsdp_plan_launch(plan, stream)
+        torch.cuda.synchronize()
+        eager = [{k: v.cpu().numpy().copy() for k, v in d.items() if torch.is_tensor(v)} for d in keep]
+        for d in keep:
+            for k in ("conf", "e", "score"):
+                d[k].zero_()
+        cap = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=cap):
+            dsdp.dsdp_plan_launch(plan, cap.cuda_stream)
+        for _ in range(2):
+            graph.replay()
+            torch.cuda.synchronize()
+            for d, ref in zip(keep, eager):
+                for k in ("conf", "e", "n", "chain", "score"):
+                    assert np.array_equal(d[k].cpu().numpy(), ref[k]), k
+    finally:
+        dsdp.dsdp_plan_destroy(None, plan)
