@@ -161,6 +161,7 @@ typedef struct {
                              (candidate E, current E, mode, accepted) */
   uint64_t n_evals;   /* out: score+gradient evaluations of the whole job */
   double device_ms;   /* out: device time from launch to completion */
+  double latency_ms;  /* out: host time from dsdp_dock_submit to the job's retirement (queueing included) */
 } dsdp_dock_result;
 
 /* ------------------------------------------------------------------ context */

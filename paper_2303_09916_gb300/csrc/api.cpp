@@ -64,6 +64,7 @@ struct Job {
   int stream = 0;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   float device_ms = 0.f;
+  std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -310,6 +311,7 @@ void progress_loop(dsdp_ctx* ctx) {
         cudaEventElapsedTime(&j->device_ms, j->ev_start, j->ev_done);
         ctx->stats.completed++;
       }
+      j->t_done = std::chrono::steady_clock::now();
       job_release_device(ctx, j);
       ctx->in_use -= j->d_bytes + j->plan_bytes;
       const_cast<dsdp_grid*>(j->grid)->users--;
@@ -738,6 +740,7 @@ extern "C" dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, co
                        (unsigned long long)ctx->budget);
     }
     j->id = ctx->next_id++;
+    j->t_submit = std::chrono::steady_clock::now();
     const_cast<dsdp_grid*>(grid)->users++;
     ctx->jobs[j->id] = j;
     ctx->queue.push_back(j->id);
@@ -790,6 +793,7 @@ extern "C" dsdp_status dsdp_dock_poll(dsdp_ctx* ctx, uint64_t job_id, dsdp_dock_
     if (out) {
       copy_results(j, out);
       out->device_ms = j->device_ms;
+      out->latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
     }
   } else if (j->state == JobState::Cancelled) {
     s = set_error(DSDP_ERR_CANCELLED, "job %llu was cancelled", (unsigned long long)job_id);

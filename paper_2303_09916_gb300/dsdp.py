@@ -67,7 +67,7 @@ class dsdp_dock_result(C.Structure):
                 ("score", C.c_void_p), ("inter", C.c_void_p), ("intra", C.c_void_p), ("conf", C.c_void_p),
                 ("coords", C.c_void_p), ("chain", C.c_void_p), ("chain_best_e", C.c_void_p),
                 ("chain_best_conf", C.c_void_p), ("trace", C.c_void_p), ("n_evals", C.c_uint64),
-                ("device_ms", C.c_double)]
+                ("device_ms", C.c_double), ("latency_ms", C.c_double)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -318,8 +318,8 @@ def dsdp_dock_poll(ctx, job_id, bufs: dict, wait_ms=-1):
     _check(s)
     out = DockResult({k: (v[: r.n_out] if k in ("score", "inter", "intra", "conf", "coords", "chain") else v)
                       for k, v in bufs.items()})
-    out.update(n_out=r.n_out, n_evals=int(r.n_evals), device_ms=r.device_ms, n_atoms=r.n_atoms,
-               n_torsions=r.n_torsions)
+    out.update(n_out=r.n_out, n_evals=int(r.n_evals), device_ms=r.device_ms, latency_ms=r.latency_ms,
+               n_atoms=r.n_atoms, n_torsions=r.n_torsions)
     return out
 
 
