@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_ker
   }
 }
 
-// Score + gradient of a batch of conformations: one warp per conformation.
+// Score + gradient of a batch of conformations: one warp per conformation,
+// warps striding over the batch (the ligand is staged once per CTA).
 template <int APL, int FMT>
 __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_t* __restrict__ blob,
                                                          const float* __restrict__ conf, int n_conf,
@@ -75,17 +76,18 @@ __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_
   const LigView L = view_blob(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpScratch W = warp_scratch_at(smem + blob_smem + warp * lay.bytes, lay);
-  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (c >= n_conf) return;
   LaneLig<APL> R;
   load_lane_lig<APL>(L, R);
   const int T = L.T;
-  Conf x = load_conf(conf + (size_t)c * (7 + T), T);
-  x.q = qnormalize(x.q);
-  float g;
-  const float e = eval_conf<APL, FMT>(M, L, R, W, x, g, flags);
-  if (lane == 0 && energy) energy[c] = e;
-  if (grad && lane < 6 + T) grad[(size_t)c * (6 + T) + lane] = g;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int c = blockIdx.x * (blockDim.x >> 5) + warp; c < n_conf; c += warps) {  // warp-uniform loop
+    Conf x = load_conf(conf + (size_t)c * (7 + T), T);
+    x.q = qnormalize(x.q);
+    float g;
+    const float e = eval_conf<APL, FMT>(M, L, R, W, x, g, flags);
+    if (lane == 0 && energy) energy[c] = e;
+    if (grad && lane < 6 + T) grad[(size_t)c * (6 + T) + lane] = g;
+  }
 }
 
 template <int APL, int FMT, int VAR>
@@ -120,7 +122,11 @@ cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
 template <int FMT>
 cudaError_t launch_score_impl(const ScoreLaunch& a, cudaStream_t st) {
   const int wpc = 4;
-  const dim3 block(32 * wpc), grid((a.n_conf + wpc - 1) / wpc);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int want = (a.n_conf + wpc - 1) / wpc, cap = sms * 8;  // warps stride over the conformations
+  const dim3 block(32 * wpc), grid(want < cap ? want : cap);
   const size_t smem = (size_t)a.blob_smem + (size_t)wpc * a.scratch.bytes;
   const MapView M = a.map;
   if (a.apl == 1) {
