@@ -73,15 +73,14 @@ struct WarpScratch {
   float* H;        // [kMaxDim][kMaxDim] BFGS inverse Hessian, row j owned by lane j
   float* cur;      // [7 + kMaxDim] current conformation
   float* best;     // [7 + kMaxDim] best conformation
-  float* pair;     // per intra pair: its force vector (float4, one atom per lane) or dE/dr / r (float)
+  float* pair;     // per intra pair: (dE/dr) / r
 };
 
 constexpr int kConfFloats = 7 + kMaxDim;
 __host__ __device__ constexpr int align16i(int x) { return (x + 15) & ~15; }
-// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions, pairs).
-// One atom per lane keeps each pair's force vector (16 B); two atoms per lane
-// (up to 2016 pairs) keep one scalar per pair (4 B) to bound shared memory.
-// H rows keep the stride kMaxDim (odd: lanes hit distinct banks).
+// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions, pairs):
+// one scalar per intra pair (4 B); H rows keep the stride kMaxDim (odd: lanes
+// hit distinct banks).
 struct ScratchLayout {
   int coords, pre, H, cur, best, pair, bytes;
 };
@@ -94,7 +93,7 @@ __host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsi
   l.cur = l.H + align16i(4 * kMaxDim * D);
   l.best = l.cur + align16i(4 * kConfFloats);
   l.pair = l.best + align16i(4 * kConfFloats);
-  l.bytes = l.pair + align16i((apl == 1 ? 16 : 4) * n_pairs);
+  l.bytes = l.pair + align16i(4 * n_pairs);
   return l;
 }
 __device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base, const ScratchLayout& l) {
@@ -192,22 +191,23 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     for (int s = 0; s < APL; ++s)
       if (lane * APL + s < N) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
     __syncwarp();
+    // all lanes run the same number of iterations (the votes inside need the full warp)
+    const int n_iter = (L.n_pairs + 31) >> 5;
 #pragma unroll 2
-    for (int p = lane; p < L.n_pairs; p += 32) {
-      const uint32_t pr = L.pairs[p];
+    for (int it = 0; it < n_iter; ++it) {
+      const int p = (it << 5) + lane;
+      const bool live = p < L.n_pairs;
+      const uint32_t pr = live ? L.pairs[p] : 0u;
       const float2 tab = L.pair_tab[pr >> 16];
       const float4 a = W.coords[pr & 0xff], b = W.coords[(pr >> 8) & 0xff];
       const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
-      float sp = 0.f;
-      if (r2 < kCutoff * kCutoff) {
-        const float inv_r = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        float e;
-        vina_pair_r(r2 * inv_r, inv_r, tab.x, __float_as_int(tab.y), e, sp);
-        e_lane += e;
-      }
-      if (APL == 1) reinterpret_cast<float4*>(W.pair)[p] = make_float4(sp * dx, sp * dy, sp * dz, 0.f);
-      else W.pair[p] = sp;
+      const bool in = live && r2 < kCutoff * kCutoff;
+      const float inv_r = (in && r2 > 0.f) ? rsqrtf(r2) : 0.f;
+      float e, sp;
+      vina_pair_r(r2 * inv_r, inv_r, tab.x, in ? __float_as_int(tab.y) : 0, e, sp);
+      if (in) e_lane += e;
+      if (live) W.pair[p] = in ? sp : 0.f;
     }
     __syncwarp();
 #pragma unroll
@@ -216,26 +216,14 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       if (i >= N) continue;
       const int k0 = L.csr_start[i], k1 = L.csr_start[i + 1];
       float gx = 0.f, gy = 0.f, gz = 0.f;
-      if (APL == 1) {
 #pragma unroll 4
-        for (int k = k0; k < k1; ++k) {
-          const uint32_t e = L.csr[k];
-          const float4 f = reinterpret_cast<const float4*>(W.pair)[e & 0x7fff];
-          const float sg = (e & 0x8000) ? -1.f : 1.f;
-          gx += sg * f.x;
-          gy += sg * f.y;
-          gz += sg * f.z;
-        }
-      } else {
-#pragma unroll 4
-        for (int k = k0; k < k1; ++k) {
-          const uint32_t e = L.csr[k];
-          const float sp = W.pair[e & 0x7fff];
-          const float4 b = W.coords[e >> 16];
-          gx += sp * (pos[s].x - b.x);
-          gy += sp * (pos[s].y - b.y);
-          gz += sp * (pos[s].z - b.z);
-        }
+      for (int k = k0; k < k1; ++k) {
+        const uint32_t e = L.csr[k];
+        const float sp = W.pair[e & 0x7fff];
+        const float4 b = W.coords[e >> 16];
+        gx += sp * (pos[s].x - b.x);
+        gy += sp * (pos[s].y - b.y);
+        gz += sp * (pos[s].z - b.z);
       }
       g[s].x += gx;
       g[s].y += gy;

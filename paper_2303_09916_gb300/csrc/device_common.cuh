@@ -177,10 +177,12 @@ __device__ __forceinline__ void vina_pair(float d, int bits, float& e, float& de
   }
 }
 
-// The same terms without branches, from r and 1/r (intra-ligand pairs):
-// returns e and (de/dr) / r.  hydrophobic = min(max(1.5 - d, 0), 1) and
-// H-bond = min(max(-d / 0.7, 0), 1) equal the piecewise forms; their slopes are
-// taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in vina_pair.
+// The same terms from r and 1/r (intra-ligand pairs), without per-lane
+// branches: returns e and (de/dr) / r.  hydrophobic = min(max(1.5 - d, 0), 1)
+// and H-bond = min(max(-d / 0.7, 0), 1) equal the piecewise forms; their
+// slopes are taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in
+// vina_pair.  The optional terms are skipped when no lane of the warp has them
+// (pair lists are grouped by term class, so that is the common case).
 __device__ __forceinline__ void vina_pair_r(float r, float inv_r, float rsum, int bits, float& e, float& s) {
   const float d = r - rsum;
   const float a = 2.f * d;
@@ -188,13 +190,18 @@ __device__ __forceinline__ void vina_pair_r(float r, float inv_r, float rsum, in
   const float b = 0.5f * (d - 3.f);
   const float g2 = __expf(-b * b);
   const float m = fminf(d, 0.f);
-  const float wh = (bits & 1) ? kWHydrophobic : 0.f;
-  const float wb = (bits & 2) ? kWHBond : 0.f;
-  e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * m * m + wh * fminf(fmaxf(1.5f - d, 0.f), 1.f) +
-      wb * fminf(fmaxf(-d * (1.0f / 0.7f), 0.f), 1.f);
+  e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * m * m;
   float de = kWGauss1 * g1 * (-8.f * d) - kWGauss2 * g2 * b + 2.f * kWRepulsion * m;
-  if (d >= 0.5f && d < 1.5f) de -= wh;
-  if (d >= -0.7f && d < 0.f) de -= wb * (1.0f / 0.7f);
+  if (__any_sync(kFull, bits & 1)) {
+    const float wh = (bits & 1) ? kWHydrophobic : 0.f;
+    e += wh * fminf(fmaxf(1.5f - d, 0.f), 1.f);
+    if (d >= 0.5f && d < 1.5f) de -= wh;
+  }
+  if (__any_sync(kFull, bits & 2)) {
+    const float wb = (bits & 2) ? kWHBond : 0.f;
+    e += wb * fminf(fmaxf(-d * (1.0f / 0.7f), 0.f), 1.f);
+    if (d >= -0.7f && d < 0.f) de -= wb * (1.0f / 0.7f);
+  }
   s = de * inv_r;
 }
 

@@ -238,13 +238,24 @@ dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
         if (dist[c] < 0) dist[c] = dist[q[qi]] + 1, q.push_back(c);
     for (int j = 0; j < n; ++j) topo[i][j] = dist[j] < 0 ? (1 << 20) : dist[j];
   }
-  for (int ii = 0; ii < n; ++ii)
-    for (int jj = ii + 1; jj < n; ++jj) {
-      const int i = out.user_of[ii], j = out.user_of[jj];
-      if (comp[i] != comp[j] && topo[i][j] > 3)
-        out.pairs.push_back((uint32_t)ii | ((uint32_t)jj << 8) |
-                            ((uint32_t)(out.type[ii] * DSDP_NUM_MAP_TYPES + out.type[jj]) << 16));
-    }
+  // Pairs grouped by which optional terms they carry (none, hydrophobic, H-bond),
+  // each group in (i, j) order: a warp taking 32 consecutive pairs then mostly
+  // sees one group and can skip the terms none of its pairs has.
+  {
+    static const int xs_bits[8] = {1, 0, 0, 2, 4, 4, 6, 0};  // 1 hydrophobic, 2 donor, 4 acceptor
+    std::vector<uint32_t> by_class[4];
+    for (int ii = 0; ii < n; ++ii)
+      for (int jj = ii + 1; jj < n; ++jj) {
+        const int i = out.user_of[ii], j = out.user_of[jj];
+        if (comp[i] == comp[j] || topo[i][j] <= 3) continue;
+        const int a = xs_bits[out.type[ii]], b = xs_bits[out.type[jj]];
+        const int cls = (a & b & 1) | ((((a & 2) && (b & 4)) || ((a & 4) && (b & 2))) ? 2 : 0);
+        by_class[cls].push_back((uint32_t)ii | ((uint32_t)jj << 8) |
+                                ((uint32_t)(out.type[ii] * DSDP_NUM_MAP_TYPES + out.type[jj]) << 16));
+      }
+    out.pairs.clear();
+    for (int c = 0; c < 4; ++c) out.pairs.insert(out.pairs.end(), by_class[c].begin(), by_class[c].end());
+  }
   const int P = (int)out.pairs.size();
   out.csr_start.assign(n + 1, 0);
   out.csr.clear();
