@@ -16,12 +16,11 @@ struct LigView {
   const float4* atom;
   const int32_t* atom_user;
   const BodyRec* body;
-  const uint32_t* pairs;
+  const uint2* pair_rec;
   const uint16_t* csr_start;
   const uint32_t* csr;
   const int32_t* torsion_body;
-  const float2* pair_tab;
-  int n_atoms, T, n_bodies, n_pairs, rounds;
+  int n_atoms, T, n_bodies, n_pairs, rounds, pair_hyd, pair_hb;
 };
 
 __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
@@ -30,16 +29,17 @@ __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
   v.atom = reinterpret_cast<const float4*>(b + v.h->off_atom);
   v.atom_user = reinterpret_cast<const int32_t*>(b + v.h->off_atom_user);
   v.body = reinterpret_cast<const BodyRec*>(b + v.h->off_body);
-  v.pairs = reinterpret_cast<const uint32_t*>(b + v.h->off_pairs);
+  v.pair_rec = reinterpret_cast<const uint2*>(b + v.h->off_pairs);
   v.csr_start = reinterpret_cast<const uint16_t*>(b + v.h->off_csr_start);
   v.csr = reinterpret_cast<const uint32_t*>(b + v.h->off_csr);
   v.torsion_body = reinterpret_cast<const int32_t*>(b + v.h->off_torsion_body);
-  v.pair_tab = reinterpret_cast<const float2*>(b + v.h->off_pair_tab);
   v.n_atoms = v.h->n_atoms;
   v.T = v.h->n_torsions;
   v.n_bodies = v.h->n_bodies;
   v.n_pairs = v.h->n_pairs;
   v.rounds = v.h->rounds;
+  v.pair_hyd = v.h->pair_hyd_begin;
+  v.pair_hb = v.h->pair_hb_begin;
   return v;
 }
 
@@ -68,18 +68,18 @@ struct Conf {
 
 // Per-warp shared scratch (layout in scratch_layout).
 struct WarpScratch {
-  float4* coords;  // [kMaxAtoms] atom positions
+  float4* coords;  // [n_atoms + 1] atom positions; slot n_atoms: a far sentinel (padding pairs)
   float4* pre;     // [kMaxAtoms][2] inclusive prefix sums of (g, (r - p) x g): (gx, gy, gz, cx), (cy, cz, -, -)
   float* H;        // [kMaxDim][kMaxDim] BFGS inverse Hessian, row j owned by lane j
   float* cur;      // [7 + kMaxDim] current conformation
   float* best;     // [7 + kMaxDim] best conformation
-  float* pair;     // per intra pair: (dE/dr) / r
+  float* pair;     // per intra pair slot: (dE/dr) / r
 };
 
 constexpr int kConfFloats = 7 + kMaxDim;
 __host__ __device__ constexpr int align16i(int x) { return (x + 15) & ~15; }
 // Per-warp scratch sized for a group's largest ligand (n_atoms, torsions, pairs):
-// one scalar per intra pair (4 B); H rows keep the stride kMaxDim (odd: lanes
+// one scalar per intra pair slot (4 B); H rows keep the stride kMaxDim (odd: lanes
 // hit distinct banks).
 struct ScratchLayout {
   int coords, pre, H, cur, best, pair, bytes;
@@ -88,12 +88,12 @@ __host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsi
   ScratchLayout l;
   const int D = 6 + n_torsions;
   l.coords = 0;
-  l.pre = l.coords + align16i(16 * n_atoms);
+  l.pre = l.coords + align16i(16 * (n_atoms + 1));
   l.H = l.pre + align16i(32 * n_atoms);
   l.cur = l.H + align16i(4 * kMaxDim * D);
   l.best = l.cur + align16i(4 * kConfFloats);
   l.pair = l.best + align16i(4 * kConfFloats);
-  l.bytes = l.pair + align16i(4 * n_pairs);
+  l.bytes = l.pair + align16i(4 * pair_slots(n_pairs));
   return l;
 }
 __device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base, const ScratchLayout& l) {
@@ -190,43 +190,57 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
 #pragma unroll
     for (int s = 0; s < APL; ++s)
       if (lane * APL + s < N) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
+    if (lane == 0) W.coords[N] = make_float4(kFarCoord, kFarCoord, kFarCoord, 0.f);
     __syncwarp();
-    // all lanes run the same number of iterations (the votes inside need the full warp)
-    const int n_iter = (L.n_pairs + 31) >> 5;
-#pragma unroll 2
-    for (int it = 0; it < n_iter; ++it) {
-      const int p = (it << 5) + lane;
-      const bool live = p < L.n_pairs;
-      const uint32_t pr = live ? L.pairs[p] : 0u;
-      const float2 tab = L.pair_tab[pr >> 16];
-      const float4 a = W.coords[pr & 0xff], b = W.coords[(pr >> 8) & 0xff];
-      const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      const bool in = live && r2 < kCutoff * kCutoff;
-      const float inv_r = (in && r2 > 0.f) ? rsqrtf(r2) : 0.f;
-      float e, sp;
-      vina_pair_r(r2 * inv_r, inv_r, tab.x, in ? __float_as_int(tab.y) : 0, e, sp);
-      if (in) e_lane += e;
-      if (live) W.pair[p] = in ? sp : 0.f;
+    // blocks of 64 pair slots, two per lane (packed arithmetic); the record holds
+    // the two atoms' byte offsets into W.coords and -(R_i + R_j)
+    const uint8_t* cb = reinterpret_cast<const uint8_t*>(W.coords);
+    const int n_blk = pair_slots(L.n_pairs) >> 6;
+    float2 e_pair = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int blk = 0; blk < n_blk; ++blk) {
+      const int p0 = (blk << 6) + lane, p1 = p0 + 32;
+      const uint2 q0 = L.pair_rec[p0], q1 = L.pair_rec[p1];
+      const float4 a0 = *reinterpret_cast<const float4*>(cb + (q0.x & 0xffffu));
+      const float4 b0 = *reinterpret_cast<const float4*>(cb + (q0.x >> 16));
+      const float4 a1 = *reinterpret_cast<const float4*>(cb + (q1.x & 0xffffu));
+      const float4 b1 = *reinterpret_cast<const float4*>(cb + (q1.x >> 16));
+      const float dx0 = a0.x - b0.x, dy0 = a0.y - b0.y, dz0 = a0.z - b0.z;
+      const float dx1 = a1.x - b1.x, dy1 = a1.y - b1.y, dz1 = a1.z - b1.z;
+      const float2 r2 = make_float2(dx0 * dx0 + dy0 * dy0 + dz0 * dz0, dx1 * dx1 + dy1 * dy1 + dz1 * dz1);
+      // pairs are grouped by term class: [0, hyd) none, [hyd, hb) hydrophobic, [hb, n) H-bond
+      const int lo = blk << 6, hi = lo + 64;
+      const bool use_hyd = hi > L.pair_hyd && lo < L.pair_hb;
+      const bool use_hb = hi > L.pair_hb && L.pair_hb < L.n_pairs;
+      const float2 wh = make_float2(p0 >= L.pair_hyd && p0 < L.pair_hb ? kWHydrophobic : 0.f,
+                                    p1 >= L.pair_hyd && p1 < L.pair_hb ? kWHydrophobic : 0.f);
+      const float2 wb = make_float2(p0 >= L.pair_hb ? kWHBond : 0.f, p1 >= L.pair_hb ? kWHBond : 0.f);
+      float2 e, sp;
+      vina_pair_x2(r2, make_float2(__uint_as_float(q0.y), __uint_as_float(q1.y)), wh, wb, use_hyd, use_hb, e, sp);
+      e_pair = __fadd2_rn(e_pair, e);
+      W.pair[p0] = sp.x;
+      W.pair[p1] = sp.y;
     }
+    e_lane += e_pair.x + e_pair.y;
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < APL; ++s) {
       const int i = lane * APL + s;
       if (i >= N) continue;
       const int k0 = L.csr_start[i], k1 = L.csr_start[i + 1];
-      float gx = 0.f, gy = 0.f, gz = 0.f;
+      const float2 pxy = make_float2(pos[s].x, pos[s].y);
+      float2 gxy = make_float2(0.f, 0.f);
+      float gz = 0.f;
 #pragma unroll 4
       for (int k = k0; k < k1; ++k) {
         const uint32_t e = L.csr[k];
         const float sp = W.pair[e & 0x7fff];
         const float4 b = W.coords[e >> 16];
-        gx += sp * (pos[s].x - b.x);
-        gy += sp * (pos[s].y - b.y);
-        gz += sp * (pos[s].z - b.z);
+        gxy = __ffma2_rn(splat2(sp), __ffma2_rn(make_float2(b.x, b.y), splat2(-1.f), pxy), gxy);
+        gz = fmaf(sp, pos[s].z - b.z, gz);
       }
-      g[s].x += gx;
-      g[s].y += gy;
+      g[s].x += gxy.x;
+      g[s].y += gxy.y;
       g[s].z += gz;
     }
   }

@@ -177,32 +177,62 @@ __device__ __forceinline__ void vina_pair(float d, int bits, float& e, float& de
   }
 }
 
-// The same terms from r and 1/r (intra-ligand pairs), without per-lane
-// branches: returns e and (de/dr) / r.  hydrophobic = min(max(1.5 - d, 0), 1)
-// and H-bond = min(max(-d / 0.7, 0), 1) equal the piecewise forms; their
-// slopes are taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in
-// vina_pair.  The optional terms are skipped when no lane of the warp has them
-// (pair lists are grouped by term class, so that is the common case).
-__device__ __forceinline__ void vina_pair_r(float r, float inv_r, float rsum, int bits, float& e, float& s) {
-  const float d = r - rsum;
-  const float a = 2.f * d;
-  const float g1 = __expf(-a * a);
-  const float b = 0.5f * (d - 3.f);
-  const float g2 = __expf(-b * b);
-  const float m = fminf(d, 0.f);
-  e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * m * m;
-  float de = kWGauss1 * g1 * (-8.f * d) - kWGauss2 * g2 * b + 2.f * kWRepulsion * m;
-  if (__any_sync(kFull, bits & 1)) {
-    const float wh = (bits & 1) ? kWHydrophobic : 0.f;
-    e += wh * fminf(fmaxf(1.5f - d, 0.f), 1.f);
-    if (d >= 0.5f && d < 1.5f) de -= wh;
+// 2^x by the ex2.approx instruction (PTX ISA: relative error about 2^-22,
+// subnormal results flushed to zero).  exp(x) = 2^(x / ln 2): callers fold the
+// 1 / ln 2 into their constants.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2E = 1.44269504088896340736f;  // 1 / ln 2
+constexpr float kFarD = 100.f;                     // surface distance where every term and slope is 0
+constexpr float kFarCoord = 1e18f;                 // sentinel atom: squared distances ~3e36, beyond the cutoff
+
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
+// Two intra-ligand pairs per lane in packed FP32x2 arithmetic (fma / mul / add
+// .f32x2 of sm_100+): the terms of vina_pair without per-lane branches, with
+// d = r2 / r + nrs, nrs = -(R_i + R_j), returning e and (de/dd) / r.
+// hydrophobic = min(max(1.5 - d, 0), 1) and H-bond = min(max(-d / 0.7, 0), 1)
+// equal the piecewise forms; their slopes are taken on the half-open intervals
+// [0.5, 1.5) and [-0.7, 0), as in vina_pair.  Pairs at or beyond the cutoff
+// (and padding slots) take d = kFarD, where every term and slope is exactly
+// zero.  wh / wb: weight of the hydrophobic / H-bond term of each pair (0 where
+// the pair does not carry it); use_hyd / use_hb: warp-uniform, false when no
+// pair of the warp's block carries the term.
+__device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, float2 wb, bool use_hyd, bool use_hb,
+                                             float2& e, float2& s) {
+  const float2 ir = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+  float2 d = __ffma2_rn(r2, ir, nrs);
+  d.x = r2.x < kCutoff * kCutoff ? d.x : kFarD;
+  d.y = r2.y < kCutoff * kCutoff ? d.y : kFarD;
+  const float2 u1 = __fmul2_rn(__fmul2_rn(d, d), splat2(-4.f * kLog2E));  // -(d / 0.5)^2 / ln 2
+  const float2 b = __ffma2_rn(d, splat2(0.5f), splat2(-1.5f));             // (d - 3) / 2
+  const float2 u2 = __fmul2_rn(__fmul2_rn(b, b), splat2(-kLog2E));        // -b^2 / ln 2
+  const float2 g1 = make_float2(ex2_approx(u1.x), ex2_approx(u1.y));
+  const float2 g2 = make_float2(ex2_approx(u2.x), ex2_approx(u2.y));
+  const float2 m = make_float2(fminf(d.x, 0.f), fminf(d.y, 0.f));
+  float2 ee = __fmul2_rn(g1, splat2(kWGauss1));
+  ee = __ffma2_rn(g2, splat2(kWGauss2), ee);
+  ee = __ffma2_rn(__fmul2_rn(m, m), splat2(kWRepulsion), ee);
+  float2 de = __fmul2_rn(g1, __fmul2_rn(d, splat2(-8.f * kWGauss1)));
+  de = __ffma2_rn(g2, __fmul2_rn(b, splat2(-kWGauss2)), de);
+  de = __ffma2_rn(m, splat2(2.f * kWRepulsion), de);
+  if (use_hyd) {  // min(max(1.5 - d, 0), 1), slope on [0.5, 1.5)
+    const float2 t = __ffma2_rn(d, splat2(-1.f), splat2(1.5f));
+    ee = __ffma2_rn(wh, make_float2(__saturatef(t.x), __saturatef(t.y)), ee);
+    if (d.x >= 0.5f && d.x < 1.5f) de.x -= wh.x;
+    if (d.y >= 0.5f && d.y < 1.5f) de.y -= wh.y;
   }
-  if (__any_sync(kFull, bits & 2)) {
-    const float wb = (bits & 2) ? kWHBond : 0.f;
-    e += wb * fminf(fmaxf(-d * (1.0f / 0.7f), 0.f), 1.f);
-    if (d >= -0.7f && d < 0.f) de -= wb * (1.0f / 0.7f);
+  if (use_hb) {  // min(max(-d / 0.7, 0), 1), slope on [-0.7, 0)
+    const float2 t = __fmul2_rn(d, splat2(-1.f / 0.7f));
+    ee = __ffma2_rn(wb, make_float2(__saturatef(t.x), __saturatef(t.y)), ee);
+    if (d.x >= -0.7f && d.x < 0.f) de.x -= wb.x * (1.f / 0.7f);
+    if (d.y >= -0.7f && d.y < 0.f) de.y -= wb.y * (1.f / 0.7f);
   }
-  s = de * inv_r;
+  e = ee;
+  s = __fmul2_rn(de, ir);
 }
 
 __device__ __forceinline__ int pair_bits(int ti, int tj) {

@@ -11,6 +11,8 @@ constexpr int kMaxAtoms = DSDP_MAX_LIGAND_ATOMS;
 constexpr int kMaxBodies = DSDP_MAX_TORSIONS + 1;
 constexpr int kMaxDim = 6 + DSDP_MAX_TORSIONS;  // gradient / step dimension
 constexpr int kMaxPairs = kMaxAtoms * (kMaxAtoms - 1) / 2;
+// Pair records are padded to whole blocks of 64 (two pairs per lane per pass).
+__host__ __device__ constexpr int pair_slots(int n_pairs) { return (n_pairs + 63) & ~63; }
 
 // Packed ligand (dsdp_ligand_pack).  Internal atom order: rigid bodies in
 // depth-first pre-order from the root (children by torsion index), atoms of a
@@ -31,15 +33,17 @@ struct BlobHeader {
                            //   w = int bits: map type | body << 8
   uint32_t off_atom_user;  // int32[n_atoms]: input index of internal atom i
   uint32_t off_body;       // BodyRec[n_bodies]
-  uint32_t off_pairs;      // uint32[n_pairs]: i | j << 8 | (type_i * 8 + type_j) << 16 (internal indices)
+  uint32_t off_pairs;      // uint2[pair_slots(n_pairs)] intra pair records (internal indices i < j):
+                           //   x = 16 i | 16 j << 16 (byte offsets of float4 slots), y = float -(R_i + R_j);
+                           //   slots past n_pairs pair atom slot n_atoms (a far sentinel) with atom 0
   uint32_t off_csr_start;  // uint16[n_atoms + 1]
   uint32_t off_csr;        // uint32[2 n_pairs]: pair index | 0x8000 if the atom is the pair's second | partner << 16
   uint32_t off_torsion_body;  // int32[n_torsions]: body driven by torsion k
   uint32_t off_atom64;     // double[n_atoms][3]: local xyz in FP64 (rescoring)
   uint32_t off_body64;     // double[n_bodies][6]: origin offset and unit axis in FP64 (rescoring)
-  uint32_t off_pair_tab;   // float2[64]: for type pair t_i * 8 + t_j: (R_i + R_j, bits 1 hydrophobic | 2 H-bond)
+  int32_t pair_hyd_begin;  // pairs [pair_hyd_begin, pair_hb_begin) carry the hydrophobic term,
   uint32_t stage_bytes;    // prefix the FP32 kernels stage into shared memory (the FP64 geometry follows it)
-  int32_t pad[1];
+  int32_t pair_hb_begin;   //   pairs [pair_hb_begin, n_pairs) the H-bond term, the others neither
 };
 static_assert(sizeof(BlobHeader) % 16 == 0, "blob header alignment");
 

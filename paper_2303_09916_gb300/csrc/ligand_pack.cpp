@@ -31,6 +31,7 @@ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct Prepared {
   int n = 0, T = 0, B = 0, P = 0, rounds = 0, root_atom = 0;
+  int hyd_begin = 0, hb_begin = 0;  // class boundaries of the grouped pair list
   float gyr = 1.0f;
   std::vector<int> user_of;         // internal -> input index
   std::vector<float> local;         // [n][3]
@@ -38,7 +39,7 @@ struct Prepared {
   std::vector<double> body64;       // [B][6]: offset, axis
   std::vector<int> type, body;      // per internal atom
   std::vector<BodyRec> bodies;      // DFS pre-order
-  std::vector<uint32_t> pairs;
+  std::vector<uint32_t> pairs;      // i | j << 8 | (type_i * 8 + type_j) << 16
   std::vector<uint16_t> csr_start;
   std::vector<uint32_t> csr;
   std::vector<int> torsion_body;
@@ -253,8 +254,12 @@ dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
         by_class[cls].push_back((uint32_t)ii | ((uint32_t)jj << 8) |
                                 ((uint32_t)(out.type[ii] * DSDP_NUM_MAP_TYPES + out.type[jj]) << 16));
       }
+    // a pair is never both (hydrophobic atoms are neither donors nor acceptors)
+    if (!by_class[3].empty()) return set_error(DSDP_ERR_INTERNAL, "pair with both optional terms");
     out.pairs.clear();
-    for (int c = 0; c < 4; ++c) out.pairs.insert(out.pairs.end(), by_class[c].begin(), by_class[c].end());
+    for (int c = 0; c < 3; ++c) out.pairs.insert(out.pairs.end(), by_class[c].begin(), by_class[c].end());
+    out.hyd_begin = (int)by_class[0].size();
+    out.hb_begin = out.hyd_begin + (int)by_class[1].size();
   }
   const int P = (int)out.pairs.size();
   out.csr_start.assign(n + 1, 0);
@@ -305,15 +310,13 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   h.off_body = (uint32_t)off;
   off = align16(off + sizeof(BodyRec) * (size_t)p.B);
   h.off_pairs = (uint32_t)off;
-  off = align16(off + 4 * (size_t)p.P);
+  off = align16(off + 8 * (size_t)pair_slots(p.P));
   h.off_csr_start = (uint32_t)off;
   off = align16(off + 2 * (size_t)(p.n + 1));
   h.off_csr = (uint32_t)off;
   off = align16(off + 4 * (size_t)p.csr.size());
   h.off_torsion_body = (uint32_t)off;
   off = align16(off + 4 * (size_t)p.T);
-  h.off_pair_tab = (uint32_t)off;
-  off = align16(off + 8 * 64);
   h.stage_bytes = (uint32_t)off;  // the chain kernels stage only this prefix
   h.off_atom64 = (uint32_t)off;
   off = align16(off + 8 * 3 * (size_t)p.n);
@@ -325,6 +328,8 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   h.n_torsions = p.T;
   h.n_bodies = p.B;
   h.n_pairs = p.P;
+  h.pair_hyd_begin = p.hyd_begin;
+  h.pair_hb_begin = p.hb_begin;
   h.rounds = p.rounds;
   h.gyration_radius = p.gyr;
   for (int a = 0; a < 3; ++a) h.root_ref[a] = p.root_ref[a];
@@ -346,25 +351,27 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   }
   memcpy(b + h.off_atom_user, p.user_of.data(), 4 * (size_t)p.n);
   memcpy(b + h.off_body, p.bodies.data(), sizeof(BodyRec) * (size_t)p.B);
-  if (p.P) memcpy(b + h.off_pairs, p.pairs.data(), 4 * (size_t)p.P);
+  {
+    // Vina XS radii of the 8 ligand map types
+    static const double radius[8] = {1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0};
+    uint32_t* rec = (uint32_t*)(b + h.off_pairs);
+    for (int k = 0; k < pair_slots(p.P); ++k) {
+      if (k < p.P) {
+        const uint32_t pr = p.pairs[k], i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
+        const float nrs = (float)-(radius[tp / DSDP_NUM_MAP_TYPES] + radius[tp % DSDP_NUM_MAP_TYPES]);
+        rec[2 * k] = (i << 4) | (j << 20);
+        memcpy(&rec[2 * k + 1], &nrs, 4);
+      } else {
+        rec[2 * k] = (uint32_t)p.n << 4;  // far sentinel slot with atom 0: beyond the cutoff
+        rec[2 * k + 1] = 0u;
+      }
+    }
+  }
   memcpy(b + h.off_csr_start, p.csr_start.data(), 2 * (size_t)(p.n + 1));
   if (!p.csr.empty()) memcpy(b + h.off_csr, p.csr.data(), 4 * p.csr.size());
   if (p.T) memcpy(b + h.off_torsion_body, p.torsion_body.data(), 4 * (size_t)p.T);
   memcpy(b + h.off_atom64, p.local64.data(), 8 * 3 * (size_t)p.n);
   memcpy(b + h.off_body64, p.body64.data(), 8 * 6 * (size_t)p.B);
-  {
-    // Vina XS radii and bits (1 hydrophobic, 2 donor, 4 acceptor) of the 8 ligand map types
-    static const double radius[8] = {1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0};
-    static const int bits[8] = {1, 0, 0, 2, 4, 4, 6, 0};
-    float* tab = (float*)(b + h.off_pair_tab);
-    for (int ti = 0; ti < 8; ++ti)
-      for (int tj = 0; tj < 8; ++tj) {
-        int pb = (bits[ti] & bits[tj] & 1);
-        if (((bits[ti] & 2) && (bits[tj] & 4)) || ((bits[ti] & 4) && (bits[tj] & 2))) pb |= 2;
-        tab[2 * (ti * 8 + tj)] = (float)(radius[ti] + radius[tj]);
-        memcpy(&tab[2 * (ti * 8 + tj) + 1], &pb, 4);
-      }
-  }
   return DSDP_OK;
 }
 

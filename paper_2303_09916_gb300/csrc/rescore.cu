@@ -179,13 +179,13 @@ __global__ void __launch_bounds__(32 * kRescoreWarps) rescore_kernel(const DevJo
   __syncwarp();
   double e_intra = 0.0;
   for (int p = lane; p < L.n_pairs; p += 32) {
-    const uint32_t pr = L.pairs[p];
-    const int i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
+    const uint32_t pr = L.pair_rec[p].x;
+    const int i = (pr & 0xffff) >> 4, j = pr >> 20;
     const double dx = s_xyz[warp][3 * i] - s_xyz[warp][3 * j], dy = s_xyz[warp][3 * i + 1] - s_xyz[warp][3 * j + 1],
                  dz = s_xyz[warp][3 * i + 2] - s_xyz[warp][3 * j + 2];
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
     if (!(r < kCutoffD)) continue;
-    const int ti = tp >> 3, tj = tp & 7;
+    const int ti = __float_as_int(L.atom[i].w) & 0xff, tj = __float_as_int(L.atom[j].w) & 0xff;
     e_intra += vina_pair_f64(r - (c_xs_radius_d[ti] + c_xs_radius_d[tj]), pair_bits(ti, tj));
   }
   e_inter = warp_sum_d(e_inter);

@@ -35,16 +35,22 @@ def test_status_strings_and_version():
 
 
 def _parse_blob(blob):
-    hdr = struct.unpack_from("<2I5if3fi11I", blob, 0)
+    hdr = struct.unpack_from("<2I5if3fi9IiIi", blob, 0)
     keys = ["magic", "bytes", "n_atoms", "T", "n_bodies", "n_pairs", "rounds", "gyr", "rx", "ry", "rz", "root_atom",
             "off_atom", "off_user", "off_body", "off_pairs", "off_csr_start", "off_csr", "off_tb", "off_a64", "off_b64",
-            "off_tab", "stage_bytes"]
+            "hyd_begin", "stage_bytes", "hb_begin"]
     h = dict(zip(keys, hdr))
     n, P = h["n_atoms"], h["n_pairs"]
     user = np.frombuffer(blob, dtype=np.int32, count=n, offset=h["off_user"])
     atom = np.frombuffer(blob, dtype=np.float32, count=4 * n, offset=h["off_atom"]).reshape(n, 4)
     body = atom[:, 3].copy().view(np.int32) >> 8
-    pairs = np.frombuffer(blob, dtype=np.uint32, count=P, offset=h["off_pairs"])
+    slots = (P + 63) // 64 * 64
+    rec = np.frombuffer(blob, dtype=np.uint32, count=2 * slots, offset=h["off_pairs"]).reshape(slots, 2)
+    h["pad_records"] = rec[P:]
+    h["nrs"] = rec[:P, 1].copy().view(np.float32)
+    h["types"] = atom[:, 3].copy().view(np.int32) & 0xFF
+    # the records hold byte offsets (16 B per atom slot); give back i | j << 8 for the checks below
+    pairs = ((rec[:P, 0] & 0xFFFF) >> 4) | ((rec[:P, 0] >> 20) << 8)
     csr_start = np.frombuffer(blob, dtype=np.uint16, count=n + 1, offset=h["off_csr_start"])
     csr = np.frombuffer(blob, dtype=np.uint32, count=2 * P, offset=h["off_csr"])
     brec = np.frombuffer(blob, dtype=np.int32, count=12 * h["n_bodies"], offset=h["off_body"]).reshape(-1, 12)
@@ -61,7 +67,7 @@ def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
     # the FP32 kernels stage a prefix holding every table they read; the FP64 geometry follows it
     assert h["stage_bytes"] % 16 == 0 and h["stage_bytes"] <= h["off_a64"] < h["off_b64"] < h["bytes"]
     assert max(h["off_atom"], h["off_user"], h["off_body"], h["off_pairs"], h["off_csr_start"], h["off_csr"],
-               h["off_tb"], h["off_tab"]) < h["stage_bytes"]
+               h["off_tb"] + 4 * h["T"]) <= h["stage_bytes"]
     assert (h["n_atoms"], h["T"], h["n_bodies"], h["n_pairs"]) == (ol.n_atoms, ol.T, ol.n_bodies, ol.n_pairs)
     assert h["root_atom"] == ol.root_atom
     assert h["gyr"] == pytest.approx(ol.gyration_radius, rel=1e-6)
@@ -69,6 +75,19 @@ def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
     # same pair set (mapped back to input indices)
     got = {tuple(sorted((int(user[p & 0xFF]), int(user[(p >> 8) & 0xFF])))) for p in pairs}
     assert got == {tuple(p) for p in ol.pairs()}
+    # per pair -(R_i + R_j); term classes in three contiguous groups (none, hydrophobic, H-bond)
+    radius = np.array([1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0])
+    xs_bits = np.array([1, 0, 0, 2, 4, 4, 6, 0])
+    ti, tj = h["types"][pairs & 0xFF], h["types"][(pairs >> 8) & 0xFF]
+    assert np.array_equal(h["nrs"], (-(radius[ti] + radius[tj])).astype(np.float32))
+    hyd = (xs_bits[ti] & xs_bits[tj] & 1) > 0
+    hb = ((xs_bits[ti] & 2) & ((xs_bits[tj] & 4) >> 1)) | ((xs_bits[ti] & 4) >> 1 & (xs_bits[tj] & 2))
+    cls = np.where(hyd, 1, np.where(hb > 0, 2, 0))
+    P = h["n_pairs"]
+    assert 0 <= h["hyd_begin"] <= h["hb_begin"] <= P
+    assert np.array_equal(cls, np.repeat([0, 1, 2], [h["hyd_begin"], h["hb_begin"] - h["hyd_begin"], P - h["hb_begin"]]))
+    # padding slots pair the far sentinel slot (index n_atoms) with atom 0
+    assert np.all(h["pad_records"][:, 0] == n << 4) and np.all(h["pad_records"][:, 1] == 0)
     # every atom's pair index lists each of its pairs once
     for a in range(n):
         entries = csr[csr_start[a]:csr_start[a + 1]]
