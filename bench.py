@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--serve", action="store_true",
                    help="run the serving workload (Poisson arrivals, 8 receptors) and print its JSON line instead")
     p.add_argument("--serve-requests", type=int, default=4000)
+    p.add_argument("--serve-streams", type=int, default=8, help="batches in flight (one per stream)")
     p.add_argument("--no-forms", dest="forms", action="store_false",
                    help="skip the one-job-per-launch and uneven-batch (CUDA graph) measurements")
     p.add_argument("--tile-config", type=int, default=-1,
@@ -441,7 +442,7 @@ def run_serving(args):
     map_bytes = sum(dsdp.dsdp_grid_map_bytes(dsdp.make_box([0, 0, 0], b, SPACING), dsdp.DSDP_MAP_BF16) for _, b in recs)
     # grids (+ receptor copies) plus 48 MB for jobs: admission has to wait for memory as well as for slots
     budget = map_bytes + 8 * (1 << 20) + (48 << 20)
-    ctx = dsdp.dsdp_create(0, mem_budget_bytes=budget, n_streams=8, max_inflight_jobs=64)
+    ctx = dsdp.dsdp_create(0, mem_budget_bytes=budget, n_streams=args.serve_streams, max_inflight_jobs=64)
     out = {}
     try:
         grids = []
@@ -608,7 +609,8 @@ def main():
         res = run_serving(args)
         print(json.dumps({"metric": "serving: docked systems/s and p50/p99 latency (8 receptors, Poisson arrivals)",
                           "unit": "systems/s", "value": res["saturated"]["systems_per_s"], "n_gpus": 1,
-                          "requests": args.serve_requests, "dtype": "f32 accumulation, bf16 maps",
+                          "requests": args.serve_requests, "streams": args.serve_streams,
+                          "dtype": "f32 accumulation, bf16 maps",
                           "data": "synthetic", "serving": res}), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

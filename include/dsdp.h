@@ -160,7 +160,7 @@ typedef struct {
                              current conf after each step, then
                              (candidate E, current E, mode, accepted) */
   uint64_t n_evals;   /* out: score+gradient evaluations of the whole job */
-  double device_ms;   /* out: device time from launch to completion */
+  double device_ms;   /* out: device time of the job's batch, from launch to completion */
   double latency_ms;  /* out: host time from dsdp_dock_submit to the job's retirement (queueing included) */
 } dsdp_dock_result;
 
@@ -176,8 +176,8 @@ typedef void (*dsdp_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 typedef struct {
   int32_t device;             /* CUDA device ordinal */
   uint64_t mem_budget_bytes;  /* device bytes jobs and grids may hold; 0 = 80 % of free memory */
-  int32_t n_streams;          /* concurrent job streams [4] */
-  int32_t max_inflight_jobs;  /* jobs on the device at once [16] */
+  int32_t n_streams;          /* job streams, one batch in flight on each [4] */
+  int32_t max_inflight_jobs;  /* jobs on the device at once, all batches [16] */
   dsdp_alloc_fn alloc;        /* NULL = cudaMallocAsync */
   dsdp_free_fn free;
   void* alloc_user;
@@ -185,7 +185,11 @@ typedef struct {
 
 /* Create a context: owns streams, the job table and a progress thread that
  * admits queued jobs as device memory and slots free up (continuous
- * batching).  Thread-safe: any thread may call any function on a ctx. */
+ * batching): whenever a stream is free, every queued job that fits (in
+ * order; at most 64 x the SM count chains) is launched as one batch, a
+ * multi-job plan whose chains share one work queue, while earlier batches
+ * drain on the other streams.  Thread-safe: any thread may call any function
+ * on a ctx. */
 dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** out);
 /* Cancel queued jobs, wait for running ones, free everything. */
 dsdp_status dsdp_destroy(dsdp_ctx* ctx);

@@ -2,9 +2,10 @@
 // queue.  The queue realises the paper's asynchronous pipeline (Sec. 2 /
 // Fig. 4: copies prepared on the host, uploaded, run independently on the
 // GPU, results postprocessed) as a continuously batched service: a progress
-// thread admits queued jobs whenever device memory and job slots free up,
-// launches each on one of several streams so that jobs overlap on the device,
-// and retires finished jobs through CUDA events.
+// thread takes every queued job that device memory and the job slots admit
+// into one batch -- one multi-job plan, whose chains share one work queue --
+// launches it on the next free stream while earlier batches drain, and
+// retires each batch through a CUDA event.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -59,15 +60,23 @@ struct Job {
   size_t res_off = 0, res_bytes = 0;
   // offsets inside the results region
   size_t o_n, o_chain, o_score, o_inter, o_intra, o_conf, o_coords, o_cbe, o_cbc, o_evals, o_trace;
-  void* h_res = nullptr;  // pinned
-  dsdp_plan* plan = nullptr;
+  void* h_res = nullptr;  // pinned, from the context's pool
+  size_t h_cap = 0;
   int stream = 0;
-  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-  float device_ms = 0.f;
+  dsdp_job_device jd{};  // the job as the plan sees it
+  float device_ms = 0.f;  // device time of the batch the job ran in
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Jobs launched together: one plan, one stream, one completion event.
+struct Batch {
+  std::vector<Job*> jobs;
+  dsdp_plan* plan = nullptr;
+  int stream = 0;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
 
 }  // namespace
 
@@ -77,7 +86,8 @@ struct dsdp_ctx {
   uint64_t budget = 0;
   uint64_t in_use = 0;
   int max_inflight = 16;
-  std::vector<cudaStream_t> streams;
+  int max_batch_chains = 0;            // chains per batch: 4 x the resident chain slots
+  std::vector<cudaStream_t> streams;   // one batch in flight per stream
   cudaStream_t sync_stream = nullptr;   // synchronous calls
   cudaStream_t alloc_stream = nullptr;  // allocations done outside a job stream
   int next_stream = 0;
@@ -88,6 +98,9 @@ struct dsdp_ctx {
   std::condition_variable cv_work, cv_done;
   std::map<uint64_t, Job*> jobs;
   std::deque<uint64_t> queue;
+  std::vector<Batch*> batches;                 // in flight
+  std::multimap<size_t, void*> pinned_pool;    // capacity -> pinned host buffer
+  size_t pinned_pooled = 0;
   uint64_t next_id = 1;
   int running = 0;
   bool stop = false;
@@ -159,22 +172,41 @@ extern "C" const char* dsdp_version(void) { return "0.1.0"; }
 // ------------------------------------------------------------------ jobs
 namespace {
 
-// Frees a job's device resources (the caller adjusts ctx->in_use).
-void job_release_device(dsdp_ctx* ctx, Job* j) {
-  if (j->plan) {
-    dsdp_plan_destroy(ctx, j->plan);
-    j->plan = nullptr;
+// Pinned host buffers are pooled by power-of-two capacity: pinning pages is
+// slow and would otherwise sit on every job's path (ctx->mu held).
+constexpr size_t kPinnedPoolLimit = 256u << 20;
+void pinned_get(dsdp_ctx* ctx, Job* j, size_t bytes) {
+  size_t cap = 4096;
+  while (cap < bytes) cap <<= 1;
+  auto it = ctx->pinned_pool.find(cap);
+  if (it != ctx->pinned_pool.end()) {
+    j->h_res = it->second;
+    ctx->pinned_pooled -= cap;
+    ctx->pinned_pool.erase(it);
+  } else if (cudaMallocHost(&j->h_res, cap) != cudaSuccess) {
+    cudaGetLastError();
+    j->h_res = nullptr;
+    return;
   }
+  j->h_cap = cap;
+}
+void pinned_put(dsdp_ctx* ctx, Job* j) {
+  if (!j->h_res) return;
+  if (ctx->pinned_pooled + j->h_cap <= kPinnedPoolLimit) {
+    ctx->pinned_pool.emplace(j->h_cap, j->h_res);
+    ctx->pinned_pooled += j->h_cap;
+  } else {
+    cudaFreeHost(j->h_res);
+  }
+  j->h_res = nullptr;
+}
+
+// Frees a job's device memory (the caller adjusts ctx->in_use).
+void job_release_device(dsdp_ctx* ctx, Job* j) {
   if (j->d_mem) {
     ctx_free(ctx, j->d_mem, j->d_bytes, (void*)ctx->streams[j->stream]);
     j->d_mem = nullptr;
   }
-  if (j->ev_start) cudaEventDestroy(j->ev_start), j->ev_start = nullptr;
-  if (j->ev_done) cudaEventDestroy(j->ev_done), j->ev_done = nullptr;
-}
-
-void job_free_host(Job* j) {
-  if (j->h_res) cudaFreeHost(j->h_res), j->h_res = nullptr;
 }
 
 // Results region layout.
@@ -207,25 +239,25 @@ uint64_t plan_scratch_estimate(const Job* j) {
   return 4096 + 3 * 8 * C + 8 * C * j->n_atoms * 3 + 64 * C + 16 * C;
 }
 
-// Admit and launch one job (ctx->mu held).  Returns false if it could not start.
-bool job_launch(dsdp_ctx* ctx, Job* j) {
+// Device memory, pinned buffer and blob upload of one job on stream st, and
+// its dsdp_job_device (ctx->mu held).  Returns false (err / msg set, nothing
+// held) if a resource could not be had.
+bool job_prepare(dsdp_ctx* ctx, Job* j, int stream) {
   const dsdp_grid* g = j->grid;
-  j->stream = ctx->next_stream;
-  ctx->next_stream = (ctx->next_stream + 1) % (int)ctx->streams.size();
-  const cudaStream_t st = ctx->streams[j->stream];
+  j->stream = stream;
+  const cudaStream_t st = ctx->streams[stream];
   layout_results(j);
   j->res_off = up256(j->blob.size());
   j->d_bytes = j->res_off + j->res_bytes;
-  j->d_mem = ctx_alloc(ctx, j->d_bytes, (void*)st);
   auto fail = [&](dsdp_status s, const char* what) {
-    j->state = JobState::Failed;
     j->err = s;
     j->msg = what;
     return false;
   };
+  j->d_mem = ctx_alloc(ctx, j->d_bytes, (void*)st);
   if (!j->d_mem) return fail(DSDP_ERR_OUT_OF_MEMORY, "job device allocation failed");
-  if (cudaMallocHost(&j->h_res, std::max(j->res_bytes, j->blob.size())) != cudaSuccess) {
-    cudaGetLastError();
+  pinned_get(ctx, j, std::max(j->res_bytes, j->blob.size()));
+  if (!j->h_res) {
     ctx_free(ctx, j->d_mem, j->d_bytes, (void*)st);
     j->d_mem = nullptr;
     return fail(DSDP_ERR_OUT_OF_MEMORY, "pinned result buffer allocation failed");
@@ -236,8 +268,11 @@ bool job_launch(dsdp_ctx* ctx, Job* j) {
   uint8_t* res = dm + j->res_off;
   memcpy(j->h_res, j->blob.data(), j->blob.size());
   cudaError_t e = cudaMemcpyAsync(dm, j->h_res, j->blob.size(), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail(check_cuda(e, "blob upload"), dsdp_last_error());
-  dsdp_job_device jd;
+  if (e != cudaSuccess) {
+    job_release_device(ctx, j);
+    return fail(check_cuda(e, "blob upload"), dsdp_last_error());
+  }
+  dsdp_job_device& jd = j->jd;
   memset(&jd, 0, sizeof(jd));
   jd.grid.d_maps = g->d_maps;
   for (int a = 0; a < 3; ++a) {
@@ -266,77 +301,161 @@ bool job_launch(dsdp_ctx* ctx, Job* j) {
   jd.d_out_intra = (double*)(res + j->o_intra);
   jd.d_out_conf = (double*)(res + j->o_conf);
   jd.d_out_coords = (float*)(res + j->o_coords);
-  dsdp_status s = dsdp_plan_create(ctx, 1, &jd, 0, 0, &j->plan);
-  if (s != DSDP_OK) {
-    ctx_free(ctx, j->d_mem, j->d_bytes, (void*)st);
-    j->d_mem = nullptr;
-    return fail(s, dsdp_last_error());
-  }
-  cudaEventCreate(&j->ev_start);
-  cudaEventCreate(&j->ev_done);
-  cudaEventRecord(j->ev_start, st);
-  s = dsdp_plan_launch(j->plan, (void*)st);
+  return true;
+}
+
+void job_fail(dsdp_ctx* ctx, Job* j, dsdp_status s, std::string msg) {
+  j->state = JobState::Failed;
+  j->err = s;
+  j->msg = std::move(msg);
+  j->t_done = std::chrono::steady_clock::now();
+  ctx->stats.failed++;
+}
+
+// Plan, launch and result downloads of prepared jobs as one batch on stream
+// `stream` (ctx->mu held).  Returns the batch, or nullptr when its plan or
+// launch failed (the jobs stay prepared; the caller decides what to do).
+Batch* batch_launch(dsdp_ctx* ctx, const std::vector<Job*>& jobs, int stream) {
+  const cudaStream_t st = ctx->streams[stream];
+  std::vector<dsdp_job_device> jd(jobs.size());
+  for (size_t i = 0; i < jobs.size(); ++i) jd[i] = jobs[i]->jd;
+  Batch* b = new Batch();
+  b->jobs = jobs;
+  b->stream = stream;
+  dsdp_status s = dsdp_plan_create(ctx, (int32_t)jd.size(), jd.data(), 0, 0, &b->plan);
   if (s == DSDP_OK) {
-    e = cudaMemcpyAsync(j->h_res, res, j->res_bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaEventRecord(j->ev_done, st);
-    if (e != cudaSuccess) s = check_cuda(e, "result download");
+    cudaEventCreateWithFlags(&b->ev_start, cudaEventDefault);
+    cudaEventCreateWithFlags(&b->ev_done, cudaEventDefault);
+    cudaEventRecord(b->ev_start, st);
+    s = dsdp_plan_launch(b->plan, (void*)st);
+  }
+  if (s == DSDP_OK) {
+    for (Job* j : jobs) {
+      const cudaError_t e = cudaMemcpyAsync(j->h_res, (uint8_t*)j->d_mem + j->res_off, j->res_bytes,
+                                            cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) {
+        s = check_cuda(e, "result download");
+        break;
+      }
+    }
+    if (s == DSDP_OK) s = check_cuda(cudaEventRecord(b->ev_done, st), "batch event");
   }
   if (s != DSDP_OK) {
     cudaStreamSynchronize(st);
-    fail(s, dsdp_last_error());
-    return false;
+    if (b->plan) dsdp_plan_destroy(ctx, b->plan);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    delete b;
+    return nullptr;
   }
-  j->state = JobState::Running;
-  return true;
+  for (Job* j : jobs) j->state = JobState::Running;
+  return b;
+}
+
+// Retire a finished batch: results are in the jobs' pinned buffers.
+void batch_retire(dsdp_ctx* ctx, Batch* b, cudaError_t q) {
+  float ms = 0.f;
+  if (q == cudaSuccess) cudaEventElapsedTime(&ms, b->ev_start, b->ev_done);
+  const auto now = std::chrono::steady_clock::now();
+  for (Job* j : b->jobs) {
+    if (q != cudaSuccess) {
+      job_fail(ctx, j, check_cuda(q, "job execution"), dsdp_last_error());
+    } else {
+      j->state = JobState::Done;
+      j->device_ms = ms;
+      j->t_done = now;
+      ctx->stats.completed++;
+    }
+    job_release_device(ctx, j);
+    ctx->in_use -= j->d_bytes + j->plan_bytes;
+    const_cast<dsdp_grid*>(j->grid)->users--;
+    ctx->running--;
+  }
+  dsdp_plan_destroy(ctx, b->plan);
+  cudaEventDestroy(b->ev_start);
+  cudaEventDestroy(b->ev_done);
+  delete b;
 }
 
 void progress_loop(dsdp_ctx* ctx) {
   cudaSetDevice(ctx->device);
   std::unique_lock<std::mutex> lk(ctx->mu);
+  std::vector<char> busy;
   while (!ctx->stop) {
     bool changed = false;
-    // retire finished jobs
-    for (auto& kv : ctx->jobs) {
-      Job* j = kv.second;
-      if (j->state != JobState::Running) continue;
-      const cudaError_t q = cudaEventQuery(j->ev_done);
-      if (q == cudaErrorNotReady) continue;
-      if (q != cudaSuccess) {
-        j->state = JobState::Failed;
-        j->err = check_cuda(q, "job execution");
-        j->msg = dsdp_last_error();
-        ctx->stats.failed++;
-      } else {
-        j->state = JobState::Done;
-        cudaEventElapsedTime(&j->device_ms, j->ev_start, j->ev_done);
-        ctx->stats.completed++;
+    // retire finished batches
+    for (size_t i = 0; i < ctx->batches.size();) {
+      Batch* b = ctx->batches[i];
+      const cudaError_t q = cudaEventQuery(b->ev_done);
+      if (q == cudaErrorNotReady) {
+        ++i;
+        continue;
       }
-      j->t_done = std::chrono::steady_clock::now();
-      job_release_device(ctx, j);
-      ctx->in_use -= j->d_bytes + j->plan_bytes;
-      const_cast<dsdp_grid*>(j->grid)->users--;
-      ctx->running--;
+      batch_retire(ctx, b, q);
+      ctx->batches.erase(ctx->batches.begin() + i);
       changed = true;
     }
-    // admit queued jobs in order while slots and memory allow
+    // one new batch per free stream: the queued jobs, in order, that memory,
+    // the job slots and the batch size admit
+    busy.assign(ctx->streams.size(), 0);
+    for (Batch* b : ctx->batches) busy[b->stream] = 1;
     while (!ctx->queue.empty() && ctx->running < ctx->max_inflight) {
-      Job* j = ctx->jobs[ctx->queue.front()];
-      const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);
-      if (ctx->in_use + need > ctx->budget && ctx->running > 0) break;  // wait for memory
-      ctx->queue.pop_front();
-      if (job_launch(ctx, j)) {
+      int stream = -1;
+      for (size_t k = 0; k < busy.size(); ++k) {
+        const int c = (ctx->next_stream + (int)k) % (int)busy.size();
+        if (!busy[c]) {
+          stream = c;
+          break;
+        }
+      }
+      if (stream < 0) break;
+      std::vector<Job*> take;
+      int64_t chains = 0;
+      while (!ctx->queue.empty() && ctx->running + (int)take.size() < ctx->max_inflight) {
+        Job* j = ctx->jobs[ctx->queue.front()];
+        const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);
+        const bool alone = ctx->running == 0 && take.empty();
+        if (ctx->in_use + need > ctx->budget && !alone) break;  // wait for memory
+        if (!take.empty() && chains + j->params.n_chains > ctx->max_batch_chains) break;
+        ctx->queue.pop_front();
+        if (!job_prepare(ctx, j, stream)) {
+          job_fail(ctx, j, j->err, j->msg);
+          const_cast<dsdp_grid*>(j->grid)->users--;
+          changed = true;
+          continue;
+        }
         j->plan_bytes = plan_scratch_estimate(j);
         ctx->in_use += j->d_bytes + j->plan_bytes;
-        ctx->running++;
-      } else {
-        ctx->stats.failed++;
-        const_cast<dsdp_grid*>(j->grid)->users--;
-        job_release_device(ctx, j);
+        chains += j->params.n_chains;
+        take.push_back(j);
       }
+      if (take.empty()) break;
+      ctx->running += (int)take.size();
+      Batch* b = batch_launch(ctx, take, stream);
+      if (b) {
+        ctx->batches.push_back(b);
+      } else {
+        // a batch-wide failure: isolate it by running the jobs one by one
+        const std::string why = dsdp_last_error();
+        for (Job* j : take) {
+          Batch* one = batch_launch(ctx, {j}, stream);
+          if (one) {
+            ctx->batches.push_back(one);
+            continue;
+          }
+          job_fail(ctx, j, DSDP_ERR_DEVICE, why + "; alone: " + dsdp_last_error());
+          job_release_device(ctx, j);
+          ctx->in_use -= j->d_bytes + j->plan_bytes;
+          const_cast<dsdp_grid*>(j->grid)->users--;
+          ctx->running--;
+        }
+      }
+      busy[stream] = 1;
+      ctx->next_stream = (stream + 1) % (int)ctx->streams.size();
       changed = true;
     }
     if (changed) ctx->cv_done.notify_all();
-    if (ctx->running > 0) ctx->cv_work.wait_for(lk, std::chrono::microseconds(100));
+    if (!ctx->batches.empty()) ctx->cv_work.wait_for(lk, std::chrono::microseconds(100));
     else ctx->cv_work.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
   }
 }
@@ -370,6 +489,7 @@ extern "C" dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** 
   cudaMemGetInfo(&free_b, &total_b);
   ctx->budget = p.mem_budget_bytes ? p.mem_budget_bytes : (uint64_t)(0.8 * (double)free_b);
   ctx->max_inflight = p.max_inflight_jobs > 0 ? p.max_inflight_jobs : 16;
+  ctx->max_batch_chains = 4 * 16 * ctx->sms;  // 16 resident chains (warps) per SM
   const int ns = p.n_streams > 0 ? p.n_streams : 4;
   for (int i = 0; i < ns; ++i) {
     cudaStream_t s;
@@ -406,13 +526,22 @@ extern "C" dsdp_status dsdp_destroy(dsdp_ctx* ctx) {
   if (ctx->progress.joinable()) ctx->progress.join();
   cudaSetDevice(ctx->device);
   for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+  for (Batch* b : ctx->batches) {
+    for (Job* j : b->jobs) job_release_device(ctx, j);
+    dsdp_plan_destroy(ctx, b->plan);
+    cudaEventDestroy(b->ev_start);
+    cudaEventDestroy(b->ev_done);
+    delete b;
+  }
+  ctx->batches.clear();
   for (auto& kv : ctx->jobs) {
     Job* j = kv.second;
-    if (j->state == JobState::Running) job_release_device(ctx, j);
-    job_free_host(j);
+    if (j->h_res) cudaFreeHost(j->h_res);
     delete j;
   }
   ctx->jobs.clear();
+  for (auto& kv : ctx->pinned_pool) cudaFreeHost(kv.second);
+  ctx->pinned_pool.clear();
   for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s), cudaStreamDestroy(s);
   cudaStreamSynchronize(ctx->alloc_stream);
   cudaStreamDestroy(ctx->alloc_stream);
@@ -800,9 +929,9 @@ extern "C" dsdp_status dsdp_dock_poll(dsdp_ctx* ctx, uint64_t job_id, dsdp_dock_
   } else {
     s = set_error(j->err, "job %llu failed: %s", (unsigned long long)job_id, j->msg.c_str());
   }
+  pinned_put(ctx, j);
   ctx->jobs.erase(it);
   lk.unlock();
-  job_free_host(j);
   delete j;
   return s;
 }

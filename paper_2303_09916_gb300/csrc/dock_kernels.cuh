@@ -21,9 +21,13 @@ struct ChainOcc<1> {
 };
 
 // Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
-// The job's ligand blob is staged into shared memory once per tile.
+// The job's ligand blob is staged into shared memory once per tile; ligands of
+// up to 32 atoms run one atom per lane, larger ones two, whatever else the
+// launch holds (a chain's arithmetic depends on its own job only).  APLS: the
+// tiles compiled in (1 or 2; 3 = both, for launches that mix them -- each
+// single-tile kernel keeps its register allocation to itself).
 // persistent != 0: CTAs pull tiles from *tile_counter until none are left.
-template <int APL, int FMT, int VAR>
+template <int FMT, int VAR, int APLS>
 __global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_kernel(const DevJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles, int n_tiles,
                                                           int* tile_counter, int persistent, int blob_smem,
@@ -56,7 +60,10 @@ __global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_ker
       __syncthreads();
     }
     const LigView L = view_blob(smem);
-    if (warp < tile.count) run_chain<APL, FMT>(J, L, W, tile.chain0 + warp);
+    if (warp < tile.count) {
+      if (APLS == 1 || (APLS == 3 && L.n_atoms <= 32)) run_chain<1, FMT>(J, L, W, tile.chain0 + warp);
+      else run_chain<2, FMT>(J, L, W, tile.chain0 + warp);
+    }
     if (!persistent) break;
   }
 }
@@ -90,11 +97,11 @@ __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_
   }
 }
 
-template <int APL, int FMT, int VAR>
+template <int FMT, int VAR, int APLS>
 cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
   const dim3 block(32);
   const size_t smem = (size_t)a.blob_smem + (size_t)a.scratch.bytes;
-  auto k = dock_chains_kernel<APL, FMT, VAR>;
+  auto k = dock_chains_kernel<FMT, VAR, APLS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = a.grid;
@@ -115,8 +122,9 @@ cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
 template <int FMT>
 cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
   if (a.warps_per_cta != 1) return cudaErrorInvalidValue;  // one warp (one chain) per CTA
-  if (a.apl == 1) return a.variant ? launch_chains_var<1, FMT, 1>(a, st) : launch_chains_var<1, FMT, 0>(a, st);
-  return a.variant ? launch_chains_var<2, FMT, 1>(a, st) : launch_chains_var<2, FMT, 0>(a, st);
+  if (a.apl_mask == 1) return a.variant ? launch_chains_var<FMT, 1, 1>(a, st) : launch_chains_var<FMT, 0, 1>(a, st);
+  if (a.apl_mask == 2) return a.variant ? launch_chains_var<FMT, 1, 2>(a, st) : launch_chains_var<FMT, 0, 2>(a, st);
+  return launch_chains_var<FMT, 0, 3>(a, st);  // mixed tiles: the 128-register budget only
 }
 
 template <int FMT>

@@ -21,7 +21,7 @@ struct dsdp_plan {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   struct Group {
-    int fmt, apl, first_tile, n_tiles, blob_smem, max_atoms, max_torsions, max_pairs;
+    int fmt, apl, first_tile, n_tiles, blob_smem, max_atoms, max_torsions, max_pairs, apl_mask;
   };
   std::vector<Group> groups;
   void* d_jobs = nullptr;
@@ -249,9 +249,12 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   // chain tiles grouped by map format (one launch per format present)
   std::vector<Tile> tiles;
   for (int f = 0; f < 6; ++f) {
-    dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0, 0, 0};
+    dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0, 0, 0, 0};
     for (int j = 0; j < n_jobs; ++j)
-      if (fmt[j] == f) g.apl = std::max(g.apl, apl[j]);  // the group runs at its largest ligand's tile
+      if (fmt[j] == f) {
+        g.apl = std::max(g.apl, apl[j]);  // largest tile present: part of the autotuner key
+        g.apl_mask |= apl[j];             // each job runs at its own tile (see dock_chains_kernel)
+      }
     for (int j = 0; j < n_jobs; ++j) {
       if (fmt[j] != f) continue;
       g.blob_smem = std::max(g.blob_smem, blob_bytes[j]);
@@ -354,6 +357,7 @@ extern "C" dsdp_status dsdp_plan_launch_stage(dsdp_plan* P, uint32_t stages, voi
     a.persistent = persistent ? 1 : 0;
     a.warps_per_cta = P->warps_per_cta;
     a.apl = g.apl;
+    a.apl_mask = g.apl_mask;
     a.blob_smem = (g.blob_smem + 15) & ~15;
     a.scratch = scratch_layout(g.max_atoms, g.max_torsions, g.max_pairs, g.apl);
     a.variant = P->variant;

@@ -15,7 +15,8 @@ struct ChainLaunch {
   int persistent;
   int grid;           // CTAs
   int warps_per_cta;
-  int apl;            // atoms per lane: 1 (<= 32 atoms) or 2 (<= 64)
+  int apl;            // largest atoms-per-lane tile present
+  int apl_mask;       // tiles present: bit 0 one atom per lane (<= 32 atoms), bit 1 two (<= 64)
   int blob_smem;      // bytes reserved for the largest staged blob prefix
   ScratchLayout scratch;  // per-warp scratch, sized for the group's largest ligand
   int variant;        // register budget of the chain kernel (0: 128, 1: 96)

@@ -380,7 +380,9 @@ def test_plan_launch_configurations_agree(ctx):
     """One uneven batch (ligands of 10-60 atoms, 0-15 torsions, two map formats)
     through the device plan in every launch configuration the autotuner chooses
     from -- 128- or 96-register chain kernel, with or without the persistent work
-    queue -- gives bitwise the same chains, and the autotuner returns one of them."""
+    queue -- gives bitwise the same chains, and the autotuner returns one of them.
+    Each job run alone in a plan of its own gives bitwise what it gave in the
+    batch (the batch mixes one- and two-atoms-per-lane ligands on one map format)."""
     dev = torch.device("cuda", 0)
     rec = synth.receptor(2000, 51)
     stream = torch.cuda.current_stream().cuda_stream
@@ -424,6 +426,15 @@ def test_plan_launch_configurations_agree(ctx):
     for other in results[1:]:
         for (c0, e0), (c1, e1) in zip(results[0], other):
             assert np.array_equal(c0, c1) and np.array_equal(e0, e1)
+    for k, j in enumerate(jobs):
+        plan = dsdp.dsdp_plan_create(None, [j], dsdp.DSDP_PLAN_NO_RESCORE, 1)
+        try:
+            dsdp.dsdp_plan_launch(plan, stream)
+            torch.cuda.synchronize()
+        finally:
+            dsdp.dsdp_plan_destroy(None, plan)
+        assert np.array_equal(keep[k][5].cpu().numpy(), results[0][k][0]), k
+        assert np.array_equal(keep[k][6].cpu().numpy(), results[0][k][1]), k
     plan = dsdp.dsdp_plan_create(None, jobs, dsdp.DSDP_PLAN_NO_RESCORE, 0)
     try:
         chosen = dsdp.dsdp_plan_autotune(plan, stream, 1)
