@@ -141,6 +141,31 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# Sources that define the chain kernel; the committed ncu traffic figure is used
+# only while their hash matches the one recorded with it.
+CHAIN_SOURCES = ["chain_device.cuh", "device_common.cuh", "dock_kernels.cuh", "dsdp_internal.h", "launch.cu",
+                 "launch.h", "ligand_pack.cpp"]
+
+
+def chain_kernel_traffic(batch, map_dtype):
+    """DRAM bytes per chain-kernel launch from the committed ncu capture, or None
+    when the kernel sources changed since it was taken or the workload differs."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "dock_chains_kernel_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for name in CHAIN_SOURCES:
+        with open(os.path.join(ROOT, "paper_2303_09916_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("sources_sha256") or batch != 16 or map_dtype != "f32":
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
 def fp32_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -665,7 +690,8 @@ def main():
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
         "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": None,
+                     "traffic": chain_kernel_traffic(args.batch, args.map_dtype),
+                     "traffic_unit": "DRAM bytes per launch (ncu)",
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
                                     f"(clock from MEASURED_PEAKS.json, {peaks_src})"},
         "l2_gather": {"achieved_gbs": r["gather_bytes"] / per_launch_s / 1e9, "microbench_gbs": r["gather_gbs"],
