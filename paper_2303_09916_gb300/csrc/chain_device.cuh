@@ -16,11 +16,10 @@ struct LigView {
   const float4* atom;
   const int32_t* atom_user;
   const BodyRec* body;
-  const uint2* pair_rec;
-  const uint16_t* csr_start;
-  const uint32_t* csr;
+  const uint2* pair_rec;  // after the staged prefix: read from the global blob only
+  const uint2* steps;
   const int32_t* torsion_body;
-  int n_atoms, T, n_bodies, n_pairs, rounds, pair_hyd, pair_hb;
+  int n_atoms, T, n_bodies, n_pairs, n_steps, rounds;
 };
 
 __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
@@ -30,16 +29,14 @@ __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
   v.atom_user = reinterpret_cast<const int32_t*>(b + v.h->off_atom_user);
   v.body = reinterpret_cast<const BodyRec*>(b + v.h->off_body);
   v.pair_rec = reinterpret_cast<const uint2*>(b + v.h->off_pairs);
-  v.csr_start = reinterpret_cast<const uint16_t*>(b + v.h->off_csr_start);
-  v.csr = reinterpret_cast<const uint32_t*>(b + v.h->off_csr);
+  v.steps = reinterpret_cast<const uint2*>(b + v.h->off_steps);
   v.torsion_body = reinterpret_cast<const int32_t*>(b + v.h->off_torsion_body);
   v.n_atoms = v.h->n_atoms;
   v.T = v.h->n_torsions;
   v.n_bodies = v.h->n_bodies;
   v.n_pairs = v.h->n_pairs;
+  v.n_steps = v.h->n_steps;
   v.rounds = v.h->rounds;
-  v.pair_hyd = v.h->pair_hyd_begin;
-  v.pair_hb = v.h->pair_hb_begin;
   return v;
 }
 
@@ -68,42 +65,37 @@ struct Conf {
 
 // Per-warp shared scratch (layout in scratch_layout).
 struct WarpScratch {
-  float4* coords;  // [n_atoms + 1] atom positions; slot n_atoms: a far sentinel (padding pairs)
   float4* pre;     // [kMaxAtoms][2] inclusive prefix sums of (g, (r - p) x g): (gx, gy, gz, cx), (cy, cz, -, -)
   float* H;        // [kMaxDim][kMaxDim] BFGS inverse Hessian, row j owned by lane j
   float* cur;      // [7 + kMaxDim] current conformation
   float* best;     // [7 + kMaxDim] best conformation
-  float* pair;     // per intra pair slot: (dE/dr) / r
 };
 
 constexpr int kConfFloats = 7 + kMaxDim;
 __host__ __device__ constexpr int align16i(int x) { return (x + 15) & ~15; }
-// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions, pairs):
-// one scalar per intra pair slot (4 B); H rows keep the stride kMaxDim (odd: lanes
-// hit distinct banks).
+// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions); H rows
+// keep the stride kMaxDim (odd: lanes hit distinct banks).
 struct ScratchLayout {
-  int coords, pre, H, cur, best, pair, bytes;
+  int pre, H, cur, best, bytes;
 };
 __host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsions, int n_pairs, int apl) {
+  (void)n_pairs;
+  (void)apl;
   ScratchLayout l;
   const int D = 6 + n_torsions;
-  l.coords = 0;
-  l.pre = l.coords + align16i(16 * (n_atoms + 1));
+  l.pre = 0;
   l.H = l.pre + align16i(32 * n_atoms);
   l.cur = l.H + align16i(4 * kMaxDim * D);
   l.best = l.cur + align16i(4 * kConfFloats);
-  l.pair = l.best + align16i(4 * kConfFloats);
-  l.bytes = l.pair + align16i(4 * pair_slots(n_pairs));
+  l.bytes = l.best + align16i(4 * kConfFloats);
   return l;
 }
 __device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base, const ScratchLayout& l) {
   WarpScratch W;
-  W.coords = reinterpret_cast<float4*>(base + l.coords);
   W.pre = reinterpret_cast<float4*>(base + l.pre);
   W.H = reinterpret_cast<float*>(base + l.H);
   W.cur = reinterpret_cast<float*>(base + l.cur);
   W.best = reinterpret_cast<float*>(base + l.best);
-  W.pair = reinterpret_cast<float*>(base + l.pair);
   return W;
 }
 
@@ -185,64 +177,57 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   float3 g[APL];
 #pragma unroll
   for (int s = 0; s < APL; ++s) g[s] = make_float3(0.f, 0.f, 0.f);
-  // ---- intra: each pair once, its force gathered by both atoms
+  // ---- intra: the pair steps of the blob, two per pass (packed FP32x2 pair
+  //      terms).  In a step each lane computes at most one pair -- its active atom
+  //      against the passive atom of a partner lane, fetched by shuffle -- and takes
+  //      the reaction force of at most one pair back from the lane that computed it.
   if (flags & DSDP_TERM_INTRA) {
-#pragma unroll
-    for (int s = 0; s < APL; ++s)
-      if (lane * APL + s < N) W.coords[lane * APL + s] = make_float4(pos[s].x, pos[s].y, pos[s].z, 0.f);
-    if (lane == 0) W.coords[N] = make_float4(kFarCoord, kFarCoord, kFarCoord, 0.f);
-    __syncwarp();
-    // blocks of 64 pair slots, two per lane (packed arithmetic); the record holds
-    // the two atoms' byte offsets into W.coords and -(R_i + R_j)
-    const uint8_t* cb = reinterpret_cast<const uint8_t*>(W.coords);
-    const int n_blk = pair_slots(L.n_pairs) >> 6;
     float2 e_pair = make_float2(0.f, 0.f);
+    const uint2* tab = L.steps + lane;
 #pragma unroll 1
-    for (int blk = 0; blk < n_blk; ++blk) {
-      const int p0 = (blk << 6) + lane, p1 = p0 + 32;
-      const uint2 q0 = L.pair_rec[p0], q1 = L.pair_rec[p1];
-      const float4 a0 = *reinterpret_cast<const float4*>(cb + (q0.x & 0xffffu));
-      const float4 b0 = *reinterpret_cast<const float4*>(cb + (q0.x >> 16));
-      const float4 a1 = *reinterpret_cast<const float4*>(cb + (q1.x & 0xffffu));
-      const float4 b1 = *reinterpret_cast<const float4*>(cb + (q1.x >> 16));
-      const float dx0 = a0.x - b0.x, dy0 = a0.y - b0.y, dz0 = a0.z - b0.z;
-      const float dx1 = a1.x - b1.x, dy1 = a1.y - b1.y, dz1 = a1.z - b1.z;
-      const float2 r2 = make_float2(dx0 * dx0 + dy0 * dy0 + dz0 * dz0, dx1 * dx1 + dy1 * dy1 + dz1 * dz1);
-      // pairs are grouped by term class: [0, hyd) none, [hyd, hb) hydrophobic, [hb, n) H-bond
-      const int lo = blk << 6, hi = lo + 64;
-      const bool use_hyd = hi > L.pair_hyd && lo < L.pair_hb;
-      const bool use_hb = hi > L.pair_hb && L.pair_hb < L.n_pairs;
-      const float2 wh = make_float2(p0 >= L.pair_hyd && p0 < L.pair_hb ? kWHydrophobic : 0.f,
-                                    p1 >= L.pair_hyd && p1 < L.pair_hb ? kWHydrophobic : 0.f);
-      const float2 wb = make_float2(p0 >= L.pair_hb ? kWHBond : 0.f, p1 >= L.pair_hb ? kWHBond : 0.f);
+    for (int st = 0; st < L.n_steps; st += 2) {
+      const uint2 t0 = tab[st * 32], t1 = tab[st * 32 + 32];
+      const int pa0 = t0.x & 31, pa1 = t1.x & 31;
+      const int pr0 = (t0.x >> 5) & 31, pr1 = (t1.x >> 5) & 31;
+      float3 a0 = pos[0], a1 = pos[0], s0 = pos[0], s1 = pos[0];
+      if (APL == 2) {
+        if (t0.x & (1u << 10)) a0 = pos[APL - 1];
+        if (t1.x & (1u << 10)) a1 = pos[APL - 1];
+        if (t0.x & (1u << 11)) s0 = pos[APL - 1];
+        if (t1.x & (1u << 11)) s1 = pos[APL - 1];
+      }
+      const float3 b0 = shfl3(s0, pa0), b1 = shfl3(s1, pa1);
+      const float2 dx = make_float2(a0.x - b0.x, a1.x - b1.x);
+      const float2 dy = make_float2(a0.y - b0.y, a1.y - b1.y);
+      const float2 dz = make_float2(a0.z - b0.z, a1.z - b1.z);
+      const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+      const uint32_t both = t0.x | t1.x;  // bits 14 / 15: warp-uniform
+      const float2 wh = make_float2((t0.x & (1u << 12)) ? kWHydrophobic : 0.f, (t1.x & (1u << 12)) ? kWHydrophobic : 0.f);
+      const float2 wb = make_float2((t0.x & (1u << 13)) ? kWHBond : 0.f, (t1.x & (1u << 13)) ? kWHBond : 0.f);
       float2 e, sp;
-      vina_pair_x2(r2, make_float2(__uint_as_float(q0.y), __uint_as_float(q1.y)), wh, wb, use_hyd, use_hb, e, sp);
+      vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), wh, wb, (both >> 14) & 1,
+                   (both >> 15) & 1, e, sp);
       e_pair = __fadd2_rn(e_pair, e);
-      W.pair[p0] = sp.x;
-      W.pair[p1] = sp.y;
+      const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
+      // reaction forces of the pairs this lane is passive in
+      const float3 c0 = shfl3(make_float3(fx.x, fy.x, fz.x), pr0);
+      const float3 c1 = shfl3(make_float3(fx.y, fy.y, fz.y), pr1);
+      if (APL == 1) {
+        g[0].x += (fx.x + fx.y) - (c0.x + c1.x);
+        g[0].y += (fy.x + fy.y) - (c0.y + c1.y);
+        g[0].z += (fz.x + fz.y) - (c0.z + c1.z);
+      } else {
+        const bool ac0 = t0.x & (1u << 10), ac1 = t1.x & (1u << 10);
+        const bool pc0 = t0.x & (1u << 11), pc1 = t1.x & (1u << 11);
+        g[0].x += (ac0 ? 0.f : fx.x) + (ac1 ? 0.f : fx.y) - (pc0 ? 0.f : c0.x) - (pc1 ? 0.f : c1.x);
+        g[0].y += (ac0 ? 0.f : fy.x) + (ac1 ? 0.f : fy.y) - (pc0 ? 0.f : c0.y) - (pc1 ? 0.f : c1.y);
+        g[0].z += (ac0 ? 0.f : fz.x) + (ac1 ? 0.f : fz.y) - (pc0 ? 0.f : c0.z) - (pc1 ? 0.f : c1.z);
+        g[APL - 1].x += (ac0 ? fx.x : 0.f) + (ac1 ? fx.y : 0.f) - (pc0 ? c0.x : 0.f) - (pc1 ? c1.x : 0.f);
+        g[APL - 1].y += (ac0 ? fy.x : 0.f) + (ac1 ? fy.y : 0.f) - (pc0 ? c0.y : 0.f) - (pc1 ? c1.y : 0.f);
+        g[APL - 1].z += (ac0 ? fz.x : 0.f) + (ac1 ? fz.y : 0.f) - (pc0 ? c0.z : 0.f) - (pc1 ? c1.z : 0.f);
+      }
     }
     e_lane += e_pair.x + e_pair.y;
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < APL; ++s) {
-      const int i = lane * APL + s;
-      if (i >= N) continue;
-      const int k0 = L.csr_start[i], k1 = L.csr_start[i + 1];
-      const float2 pxy = make_float2(pos[s].x, pos[s].y);
-      float2 gxy = make_float2(0.f, 0.f);
-      float gz = 0.f;
-#pragma unroll 4
-      for (int k = k0; k < k1; ++k) {
-        const uint32_t e = L.csr[k];
-        const float sp = W.pair[e & 0x7fff];
-        const float4 b = W.coords[e >> 16];
-        gxy = __ffma2_rn(splat2(sp), __ffma2_rn(make_float2(b.x, b.y), splat2(-1.f), pxy), gxy);
-        gz = fmaf(sp, pos[s].z - b.z, gz);
-      }
-      g[s].x += gxy.x;
-      g[s].y += gxy.y;
-      g[s].z += gz;
-    }
   }
   // ---- inter, part 2: trilinear score and gradient (Eq. 2, Eq. 4 / Eq. 3)
 #pragma unroll
@@ -320,7 +305,7 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   } else if (lane < 6 + L.T) {
     gl = tv;
   }
-  __syncwarp();  // W.pre / W.coords are rewritten by the next evaluation
+  __syncwarp();  // W.pre is rewritten by the next evaluation
   grad = gl;
   return E;
 }

@@ -187,7 +187,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 constexpr float kLog2E = 1.44269504088896340736f;  // 1 / ln 2
 constexpr float kFarD = 100.f;                     // surface distance where every term and slope is 0
-constexpr float kFarCoord = 1e18f;                 // sentinel atom: squared distances ~3e36, beyond the cutoff
 
 __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 
@@ -197,10 +196,11 @@ __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 // hydrophobic = min(max(1.5 - d, 0), 1) and H-bond = min(max(-d / 0.7, 0), 1)
 // equal the piecewise forms; their slopes are taken on the half-open intervals
 // [0.5, 1.5) and [-0.7, 0), as in vina_pair.  Pairs at or beyond the cutoff
-// (and padding slots) take d = kFarD, where every term and slope is exactly
-// zero.  wh / wb: weight of the hydrophobic / H-bond term of each pair (0 where
-// the pair does not carry it); use_hyd / use_hb: warp-uniform, false when no
-// pair of the warp's block carries the term.
+// take d = kFarD, and idle slots get a surface distance at least kStepIdleNrs:
+// there every term and slope is exactly zero.  wh / wb: weight of the
+// hydrophobic / H-bond term of each pair (0 where the pair does not carry it);
+// use_hyd / use_hb: warp-uniform, false when no pair of the two steps carries
+// the term.
 __device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, float2 wb, bool use_hyd, bool use_hb,
                                              float2& e, float2& s) {
   const float2 ir = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);

@@ -11,8 +11,23 @@ constexpr int kMaxAtoms = DSDP_MAX_LIGAND_ATOMS;
 constexpr int kMaxBodies = DSDP_MAX_TORSIONS + 1;
 constexpr int kMaxDim = 6 + DSDP_MAX_TORSIONS;  // gradient / step dimension
 constexpr int kMaxPairs = kMaxAtoms * (kMaxAtoms - 1) / 2;
-// Pair records are padded to whole blocks of 64 (two pairs per lane per pass).
-__host__ __device__ constexpr int pair_slots(int n_pairs) { return (n_pairs + 63) & ~63; }
+// Atoms per lane of a warp holding one conformation: internal atom i sits in
+// lane i / APL, slot i % APL.
+__host__ __device__ constexpr int atoms_per_lane(int n_atoms) { return n_atoms <= 32 ? 1 : 2; }
+
+// Intra-pair step table: the pairs are split into steps in which every lane
+// computes at most one pair (its "active" atom against a partner lane's
+// "passive" atom) and receives at most one reaction force.  One entry per lane
+// per step (uint2):
+//   x bits 0-4   partner lane (the passive atom's lane; own lane when inactive)
+//        5-9    lane whose force this lane receives (the active atom's lane when
+//               this lane is passive, otherwise a lane inactive in this step)
+//        10     slot of the active atom in this lane, 11 slot of the passive atom
+//        12, 13 the active pair carries the hydrophobic / H-bond term
+//        14, 15 some pair of this step carries the hydrophobic / H-bond term
+//               (the same in every lane of the step)
+//   y    -(R_a + R_b) of the active pair as a float; kStepIdleNrs when inactive
+constexpr float kStepIdleNrs = 1.0e4f;  // surface distance where every term and slope is zero
 
 // Packed ligand (dsdp_ligand_pack).  Internal atom order: rigid bodies in
 // depth-first pre-order from the root (children by torsion index), atoms of a
@@ -33,11 +48,10 @@ struct BlobHeader {
                            //   w = int bits: map type | body << 8
   uint32_t off_atom_user;  // int32[n_atoms]: input index of internal atom i
   uint32_t off_body;       // BodyRec[n_bodies]
-  uint32_t off_pairs;      // uint2[pair_slots(n_pairs)] intra pair records (internal indices i < j):
-                           //   x = 16 i | 16 j << 16 (byte offsets of float4 slots), y = float -(R_i + R_j);
-                           //   slots past n_pairs pair atom slot n_atoms (a far sentinel) with atom 0
-  uint32_t off_csr_start;  // uint16[n_atoms + 1]
-  uint32_t off_csr;        // uint32[2 n_pairs]: pair index | 0x8000 if the atom is the pair's second | partner << 16
+  uint32_t off_pairs;      // uint2[n_pairs] intra pair records (internal indices i < j):
+                           //   x = 16 i | 16 j << 16, y = float -(R_i + R_j)  (after the staged prefix)
+  uint32_t off_steps;      // uint2[n_steps][32] intra-pair step table (see kStepIdleNrs)
+  int32_t n_steps;         // even
   uint32_t off_torsion_body;  // int32[n_torsions]: body driven by torsion k
   uint32_t off_atom64;     // double[n_atoms][3]: local xyz in FP64 (rescoring)
   uint32_t off_body64;     // double[n_bodies][6]: origin offset and unit axis in FP64 (rescoring)

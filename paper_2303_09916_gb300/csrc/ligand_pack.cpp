@@ -40,11 +40,161 @@ struct Prepared {
   std::vector<int> type, body;      // per internal atom
   std::vector<BodyRec> bodies;      // DFS pre-order
   std::vector<uint32_t> pairs;      // i | j << 8 | (type_i * 8 + type_j) << 16
-  std::vector<uint16_t> csr_start;
-  std::vector<uint32_t> csr;
+  std::vector<uint32_t> steps;       // [n_steps][32][2] step table (see kStepIdleNrs)
+  int n_steps = 0;
   std::vector<int> torsion_body;
   float root_ref[3];
 };
+
+// Intra-pair step schedule.  Each pair is computed by one lane (its "active"
+// atom) against an atom of a partner lane ("passive"), which receives the
+// reaction force by a shuffle.  A step may give each lane at most one active
+// and one passive role, so the pairs form a bipartite multigraph between lanes
+// as active and lanes as passive.  Its edges are oriented first so that every
+// lane is active about as often as it is passive (Euler circuits through an
+// extra vertex joined to the lanes of odd degree: |out - in| <= 1), then
+// coloured with max(out, in) colours by alternating-path recolouring (Konig's
+// edge-colouring theorem for bipartite multigraphs); a colour is a step.
+void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>& pj, const std::vector<int>& pc,
+                      const std::vector<float>& pn, std::vector<uint32_t>& table, int& n_steps) {
+  const int apl = atoms_per_lane(n), P = (int)pi.size(), V = 32, X = 32;  // X: the extra vertex
+  auto lane_of = [&](int a) { return a / apl; };
+  // ---- orientation: act[p] = the active atom of pair p
+  std::vector<int> act(P, -1);
+  {
+    struct E {
+      int u, v, pair;  // pair < 0: edge to the extra vertex
+    };
+    std::vector<E> edges;
+    std::vector<int> deg(V + 1, 0);
+    for (int p = 0; p < P; ++p) {
+      const int u = lane_of(pi[p]), v = lane_of(pj[p]);
+      if (u == v) {
+        act[p] = pi[p];  // both atoms in one lane: the lane is active and passive once
+        continue;
+      }
+      edges.push_back(E{u, v, p});
+      ++deg[u];
+      ++deg[v];
+    }
+    for (int v = 0; v < V; ++v)
+      if (deg[v] & 1) edges.push_back(E{v, X, -1});
+    std::vector<std::vector<int>> inc(V + 1);
+    for (int e = 0; e < (int)edges.size(); ++e) {
+      inc[edges[e].u].push_back(e);
+      inc[edges[e].v].push_back(e);
+    }
+    std::vector<char> used(edges.size(), 0);
+    std::vector<size_t> next(V + 1, 0);
+    for (int s0 = 0; s0 <= V; ++s0) {
+      std::vector<int> stack{s0};
+      while (!stack.empty()) {
+        const int x = stack.back();
+        while (next[x] < inc[x].size() && used[inc[x][next[x]]]) ++next[x];
+        if (next[x] == inc[x].size()) {
+          stack.pop_back();
+          continue;
+        }
+        const int e = inc[x][next[x]];
+        used[e] = 1;
+        const int y = edges[e].u == x ? edges[e].v : edges[e].u;
+        const int p = edges[e].pair;
+        if (p >= 0) act[p] = lane_of(pi[p]) == x ? pi[p] : pj[p];  // walked x -> y: x's atom is active
+        stack.push_back(y);
+      }
+    }
+  }
+  // ---- colouring
+  int delta = 0;
+  {
+    std::vector<int> out_d(V, 0), in_d(V, 0);
+    for (int p = 0; p < P; ++p) {
+      const int a = act[p], b = a == pi[p] ? pj[p] : pi[p];
+      ++out_d[lane_of(a)];
+      ++in_d[lane_of(b)];
+    }
+    for (int v = 0; v < V; ++v) delta = std::max(delta, std::max(out_d[v], in_d[v]));
+  }
+  std::vector<int> colour(P, -1);
+  std::vector<int> at_act((size_t)V * std::max(delta, 1), -1), at_pas((size_t)V * std::max(delta, 1), -1);
+  auto A = [&](int lane, int c) -> int& { return at_act[(size_t)lane * delta + c]; };
+  auto B = [&](int lane, int c) -> int& { return at_pas[(size_t)lane * delta + c]; };
+  auto ends = [&](int p, int& u, int& v) {
+    const int a = act[p], b = a == pi[p] ? pj[p] : pi[p];
+    u = lane_of(a);
+    v = lane_of(b);
+  };
+  for (int p = 0; p < P; ++p) {
+    int u, v;
+    ends(p, u, v);
+    int c1 = 0, c2 = 0;
+    while (A(u, c1) >= 0) ++c1;
+    while (B(v, c2) >= 0) ++c2;
+    if (B(v, c1) >= 0) {
+      // swap c1 / c2 along the path from v (passive side) that starts with colour c1
+      std::vector<int> path;
+      int x = v, col = c1;
+      bool passive_side = true;
+      for (;;) {
+        const int q = passive_side ? B(x, col) : A(x, col);
+        if (q < 0) break;
+        path.push_back(q);
+        int qu, qv;
+        ends(q, qu, qv);
+        x = passive_side ? qu : qv;
+        passive_side = !passive_side;
+        col = col == c1 ? c2 : c1;
+      }
+      for (int q : path) {
+        int qu, qv;
+        ends(q, qu, qv);
+        A(qu, colour[q]) = -1;
+        B(qv, colour[q]) = -1;
+      }
+      for (int q : path) {
+        int qu, qv;
+        ends(q, qu, qv);
+        colour[q] = colour[q] == c1 ? c2 : c1;
+        A(qu, colour[q]) = q;
+        B(qv, colour[q]) = q;
+      }
+    }
+    colour[p] = c1;
+    A(u, c1) = p;
+    B(v, c1) = p;
+  }
+  // ---- table
+  n_steps = (delta + 1) & ~1;
+  table.assign((size_t)n_steps * V * 2, 0u);
+  for (int c = 0; c < n_steps; ++c) {
+    uint32_t step_bits = 0;
+    int idle = -1;
+    for (int v = 0; v < V && c < delta; ++v) {
+      if (A(v, c) < 0 && idle < 0) idle = v;
+      if (A(v, c) >= 0) step_bits |= (pc[A(v, c)] == 1 ? 1u << 14 : 0u) | (pc[A(v, c)] == 2 ? 1u << 15 : 0u);
+    }
+    for (int v = 0; v < V; ++v) {
+      uint32_t x = (uint32_t)v | ((uint32_t)(idle >= 0 ? idle : v) << 5);
+      float nrs = kStepIdleNrs;
+      if (c < delta && A(v, c) >= 0) {
+        const int p = A(v, c), a = act[p], b = a == pi[p] ? pj[p] : pi[p];
+        x = (x & ~31u) | (uint32_t)lane_of(b);
+        x |= (uint32_t)(a % apl) << 10;
+        x |= pc[p] == 1 ? 1u << 12 : 0u;
+        x |= pc[p] == 2 ? 1u << 13 : 0u;
+        nrs = pn[p];
+      }
+      if (c < delta && B(v, c) >= 0) {
+        const int p = B(v, c), a = act[p], b = a == pi[p] ? pj[p] : pi[p];
+        x = (x & ~(31u << 5)) | ((uint32_t)lane_of(a) << 5);
+        x |= (uint32_t)(b % apl) << 11;
+      }
+      x |= step_bits;
+      table[((size_t)c * V + v) * 2] = x;
+      memcpy(&table[((size_t)c * V + v) * 2 + 1], &nrs, 4);
+    }
+  }
+}
 
 dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
   if (!L) return set_error(DSDP_ERR_INVALID_ARG, "ligand is NULL");
@@ -262,17 +412,19 @@ dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
     out.hb_begin = out.hyd_begin + (int)by_class[1].size();
   }
   const int P = (int)out.pairs.size();
-  out.csr_start.assign(n + 1, 0);
-  out.csr.clear();
-  for (int a = 0; a < n; ++a) {
-    out.csr_start[a] = (uint16_t)out.csr.size();
+  {
+    static const double radius[8] = {1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0};
+    std::vector<int> pi(P), pj(P), pc(P);
+    std::vector<float> pn(P);
     for (int p = 0; p < P; ++p) {
-      const int i = out.pairs[p] & 0xff, j = (out.pairs[p] >> 8) & 0xff;
-      if (i == a) out.csr.push_back((uint32_t)p | ((uint32_t)j << 16));
-      else if (j == a) out.csr.push_back((uint32_t)p | 0x8000u | ((uint32_t)i << 16));
+      pi[p] = out.pairs[p] & 0xff;
+      pj[p] = (out.pairs[p] >> 8) & 0xff;
+      pc[p] = p < out.hyd_begin ? 0 : (p < out.hb_begin ? 1 : 2);
+      const int tp = out.pairs[p] >> 16;
+      pn[p] = (float)-(radius[tp / DSDP_NUM_MAP_TYPES] + radius[tp % DSDP_NUM_MAP_TYPES]);
     }
+    build_pair_steps(n, pi, pj, pc, pn, out.steps, out.n_steps);
   }
-  out.csr_start[n] = (uint16_t)out.csr.size();
   double s2 = 0.0;
   for (int i = 0; i < n; ++i)
     for (int a = 0; a < 3; ++a) {
@@ -309,15 +461,13 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   off = align16(off + 4 * (size_t)p.n);
   h.off_body = (uint32_t)off;
   off = align16(off + sizeof(BodyRec) * (size_t)p.B);
-  h.off_pairs = (uint32_t)off;
-  off = align16(off + 8 * (size_t)pair_slots(p.P));
-  h.off_csr_start = (uint32_t)off;
-  off = align16(off + 2 * (size_t)(p.n + 1));
-  h.off_csr = (uint32_t)off;
-  off = align16(off + 4 * (size_t)p.csr.size());
   h.off_torsion_body = (uint32_t)off;
   off = align16(off + 4 * (size_t)p.T);
+  h.off_steps = (uint32_t)off;
+  off = align16(off + 8 * 32 * (size_t)p.n_steps);
   h.stage_bytes = (uint32_t)off;  // the chain kernels stage only this prefix
+  h.off_pairs = (uint32_t)off;
+  off = align16(off + 8 * (size_t)p.P);
   h.off_atom64 = (uint32_t)off;
   off = align16(off + 8 * 3 * (size_t)p.n);
   h.off_body64 = (uint32_t)off;
@@ -328,6 +478,7 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   h.n_torsions = p.T;
   h.n_bodies = p.B;
   h.n_pairs = p.P;
+  h.n_steps = p.n_steps;
   h.pair_hyd_begin = p.hyd_begin;
   h.pair_hb_begin = p.hb_begin;
   h.rounds = p.rounds;
@@ -355,20 +506,14 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
     // Vina XS radii of the 8 ligand map types
     static const double radius[8] = {1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0};
     uint32_t* rec = (uint32_t*)(b + h.off_pairs);
-    for (int k = 0; k < pair_slots(p.P); ++k) {
-      if (k < p.P) {
-        const uint32_t pr = p.pairs[k], i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
-        const float nrs = (float)-(radius[tp / DSDP_NUM_MAP_TYPES] + radius[tp % DSDP_NUM_MAP_TYPES]);
-        rec[2 * k] = (i << 4) | (j << 20);
-        memcpy(&rec[2 * k + 1], &nrs, 4);
-      } else {
-        rec[2 * k] = (uint32_t)p.n << 4;  // far sentinel slot with atom 0: beyond the cutoff
-        rec[2 * k + 1] = 0u;
-      }
+    for (int k = 0; k < p.P; ++k) {
+      const uint32_t pr = p.pairs[k], i = pr & 0xff, j = (pr >> 8) & 0xff, tp = pr >> 16;
+      const float nrs = (float)-(radius[tp / DSDP_NUM_MAP_TYPES] + radius[tp % DSDP_NUM_MAP_TYPES]);
+      rec[2 * k] = (i << 4) | (j << 20);
+      memcpy(&rec[2 * k + 1], &nrs, 4);
     }
   }
-  memcpy(b + h.off_csr_start, p.csr_start.data(), 2 * (size_t)(p.n + 1));
-  if (!p.csr.empty()) memcpy(b + h.off_csr, p.csr.data(), 4 * p.csr.size());
+  if (p.n_steps) memcpy(b + h.off_steps, p.steps.data(), 4 * p.steps.size());
   if (p.T) memcpy(b + h.off_torsion_body, p.torsion_body.data(), 4 * (size_t)p.T);
   memcpy(b + h.off_atom64, p.local64.data(), 8 * 3 * (size_t)p.n);
   memcpy(b + h.off_body64, p.body64.data(), 8 * 6 * (size_t)p.B);

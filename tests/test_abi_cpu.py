@@ -35,39 +35,95 @@ def test_status_strings_and_version():
 
 
 def _parse_blob(blob):
-    hdr = struct.unpack_from("<2I5if3fi9IiIi", blob, 0)
+    hdr = struct.unpack_from("<2I5if3fi5Ii3IiIi", blob, 0)
     keys = ["magic", "bytes", "n_atoms", "T", "n_bodies", "n_pairs", "rounds", "gyr", "rx", "ry", "rz", "root_atom",
-            "off_atom", "off_user", "off_body", "off_pairs", "off_csr_start", "off_csr", "off_tb", "off_a64", "off_b64",
+            "off_atom", "off_user", "off_body", "off_pairs", "off_steps", "n_steps", "off_tb", "off_a64", "off_b64",
             "hyd_begin", "stage_bytes", "hb_begin"]
     h = dict(zip(keys, hdr))
     n, P = h["n_atoms"], h["n_pairs"]
     user = np.frombuffer(blob, dtype=np.int32, count=n, offset=h["off_user"])
     atom = np.frombuffer(blob, dtype=np.float32, count=4 * n, offset=h["off_atom"]).reshape(n, 4)
     body = atom[:, 3].copy().view(np.int32) >> 8
-    slots = (P + 63) // 64 * 64
-    rec = np.frombuffer(blob, dtype=np.uint32, count=2 * slots, offset=h["off_pairs"]).reshape(slots, 2)
-    h["pad_records"] = rec[P:]
-    h["nrs"] = rec[:P, 1].copy().view(np.float32)
+    rec = np.frombuffer(blob, dtype=np.uint32, count=2 * P, offset=h["off_pairs"]).reshape(P, 2)
+    h["nrs"] = rec[:, 1].copy().view(np.float32)
     h["types"] = atom[:, 3].copy().view(np.int32) & 0xFF
     # the records hold byte offsets (16 B per atom slot); give back i | j << 8 for the checks below
-    pairs = ((rec[:P, 0] & 0xFFFF) >> 4) | ((rec[:P, 0] >> 20) << 8)
-    csr_start = np.frombuffer(blob, dtype=np.uint16, count=n + 1, offset=h["off_csr_start"])
-    csr = np.frombuffer(blob, dtype=np.uint32, count=2 * P, offset=h["off_csr"])
+    pairs = ((rec[:, 0] & 0xFFFF) >> 4) | ((rec[:, 0] >> 20) << 8)
+    steps = np.frombuffer(blob, dtype=np.uint32, count=2 * 32 * h["n_steps"], offset=h["off_steps"]).reshape(
+        h["n_steps"], 32, 2)
     brec = np.frombuffer(blob, dtype=np.int32, count=12 * h["n_bodies"], offset=h["off_body"]).reshape(-1, 12)
-    return h, user, body, pairs, csr_start, csr, brec
+    return h, user, body, pairs, steps, brec
 
 
-@pytest.mark.parametrize("n,t,seed", [(8, 2, 0), (20, 4, 1), (30, 8, 2), (45, 12, 3), (60, 15, 4), (10, 0, 5)])
+RADIUS = np.array([1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0])
+XS_BITS = np.array([1, 0, 0, 2, 4, 4, 6, 0])
+
+
+def _pair_class(ti, tj):
+    hyd = (XS_BITS[ti] & XS_BITS[tj] & 1) > 0
+    hb = ((XS_BITS[ti] & 2) & ((XS_BITS[tj] & 4) >> 1)) | ((XS_BITS[ti] & 4) >> 1 & (XS_BITS[tj] & 2))
+    return np.where(hyd, 1, np.where(hb > 0, 2, 0))
+
+
+def _check_steps(h, pairs, steps):
+    """The intra-pair step table: every pair computed exactly once, no lane active
+    or passive twice in a step, reaction forces routed back to the right lane."""
+    n, P = h["n_atoms"], h["n_pairs"]
+    apl = 1 if n <= 32 else 2
+    assert h["n_steps"] % 2 == 0
+    want = {(int(p & 0xFF), int((p >> 8) & 0xFF)): k for k, p in enumerate(pairs)}
+    cls = _pair_class(h["types"][pairs & 0xFF], h["types"][(pairs >> 8) & 0xFF])
+    seen = set()
+    for st in steps:
+        x, nrs = st[:, 0], st[:, 1].copy().view(np.float32)
+        partner, pred = x & 31, (x >> 5) & 31
+        act_slot, pas_slot = (x >> 10) & 1, (x >> 11) & 1
+        active = nrs != np.float32(1.0e4)
+        passive_of = {}
+        step_cls = 0
+        for lane in np.nonzero(active)[0]:
+            a = int(lane) * apl + int(act_slot[lane])
+            pl = int(partner[lane])
+            b = pl * apl + int(pas_slot[pl])
+            assert a < n and b < n and a != b
+            assert pl not in passive_of, "lane passive twice in one step"
+            passive_of[pl] = int(lane)
+            assert int(pred[pl]) == lane, "reaction force not routed to the passive lane"
+            key = (min(a, b), max(a, b))
+            assert key in want and key not in seen
+            seen.add(key)
+            k = want[key]
+            assert nrs[lane] == h["nrs"][k]
+            assert bool(x[lane] >> 12 & 1) == (cls[k] == 1) and bool(x[lane] >> 13 & 1) == (cls[k] == 2)
+            step_cls |= 1 << (int(cls[k]) + 13) if cls[k] else 0
+        for lane in range(32):
+            if lane not in passive_of:  # takes its (zero) reaction force from an idle lane
+                assert not active[pred[lane]]
+            if not active[lane]:
+                assert partner[lane] == lane and not (x[lane] >> 12 & 3)
+        assert np.all((x >> 14 & 3) == step_cls >> 14)
+    assert len(seen) == P
+    # the schedule is as short as the busiest lane allows (balanced orientation)
+    deg = np.zeros(32, int)
+    for p in pairs:
+        deg[(p & 0xFF) // apl] += 1
+        deg[((p >> 8) & 0xFF) // apl] += 1
+    assert h["n_steps"] <= int(np.max((deg + 1) // 2)) + 2
+
+
+@pytest.mark.parametrize("n,t,seed", [(8, 2, 0), (20, 4, 1), (30, 8, 2), (45, 12, 3), (60, 15, 4), (10, 0, 5),
+                                      (64, 15, 6), (33, 6, 7)])
 def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
     lig = synth.ligand(n, t, seed)
     blob = dsdp.dsdp_ligand_pack(lig)
-    h, user, body, pairs, csr_start, csr, brec = _parse_blob(bytes(blob))
+    h, user, body, pairs, steps, brec = _parse_blob(bytes(blob))
     ol = oracle.Ligand(lig.xyz.astype(np.float64), lig.xs_type, lig.bonds, lig.rotatable)
     assert h["magic"] == 0x50445344 and h["bytes"] == len(blob) and h["bytes"] % 16 == 0
-    # the FP32 kernels stage a prefix holding every table they read; the FP64 geometry follows it
-    assert h["stage_bytes"] % 16 == 0 and h["stage_bytes"] <= h["off_a64"] < h["off_b64"] < h["bytes"]
-    assert max(h["off_atom"], h["off_user"], h["off_body"], h["off_pairs"], h["off_csr_start"], h["off_csr"],
-               h["off_tb"] + 4 * h["T"]) <= h["stage_bytes"]
+    # the FP32 kernels stage a prefix holding every table they read; the pair list
+    # (FP64 rescoring) and the FP64 geometry follow it
+    assert h["stage_bytes"] % 16 == 0 and h["stage_bytes"] <= h["off_pairs"] <= h["off_a64"] < h["off_b64"] < h["bytes"]
+    assert max(h["off_atom"], h["off_user"], h["off_body"], h["off_tb"] + 4 * h["T"],
+               h["off_steps"] + 256 * h["n_steps"]) <= h["stage_bytes"]
     assert (h["n_atoms"], h["T"], h["n_bodies"], h["n_pairs"]) == (ol.n_atoms, ol.T, ol.n_bodies, ol.n_pairs)
     assert h["root_atom"] == ol.root_atom
     assert h["gyr"] == pytest.approx(ol.gyration_radius, rel=1e-6)
@@ -76,28 +132,13 @@ def test_ligand_pack_agrees_with_the_oracle_topology(n, t, seed):
     got = {tuple(sorted((int(user[p & 0xFF]), int(user[(p >> 8) & 0xFF])))) for p in pairs}
     assert got == {tuple(p) for p in ol.pairs()}
     # per pair -(R_i + R_j); term classes in three contiguous groups (none, hydrophobic, H-bond)
-    radius = np.array([1.9, 1.9, 1.8, 1.8, 1.8, 1.7, 1.7, 2.0])
-    xs_bits = np.array([1, 0, 0, 2, 4, 4, 6, 0])
     ti, tj = h["types"][pairs & 0xFF], h["types"][(pairs >> 8) & 0xFF]
-    assert np.array_equal(h["nrs"], (-(radius[ti] + radius[tj])).astype(np.float32))
-    hyd = (xs_bits[ti] & xs_bits[tj] & 1) > 0
-    hb = ((xs_bits[ti] & 2) & ((xs_bits[tj] & 4) >> 1)) | ((xs_bits[ti] & 4) >> 1 & (xs_bits[tj] & 2))
-    cls = np.where(hyd, 1, np.where(hb > 0, 2, 0))
+    assert np.array_equal(h["nrs"], (-(RADIUS[ti] + RADIUS[tj])).astype(np.float32))
+    cls = _pair_class(ti, tj)
     P = h["n_pairs"]
     assert 0 <= h["hyd_begin"] <= h["hb_begin"] <= P
     assert np.array_equal(cls, np.repeat([0, 1, 2], [h["hyd_begin"], h["hb_begin"] - h["hyd_begin"], P - h["hb_begin"]]))
-    # padding slots pair the far sentinel slot (index n_atoms) with atom 0
-    assert np.all(h["pad_records"][:, 0] == n << 4) and np.all(h["pad_records"][:, 1] == 0)
-    # every atom's pair index lists each of its pairs once
-    for a in range(n):
-        entries = csr[csr_start[a]:csr_start[a + 1]]
-        mine = {int(e & 0x7FFF) for e in entries}
-        for e in entries:  # sign bit: set when the atom is the pair's second atom
-            p = pairs[e & 0x7FFF]
-            assert bool(e & 0x8000) == (((p >> 8) & 0xFF) == a)
-            assert (e >> 16) == ((p >> 8) & 0xFF if (p & 0xFF) == a else p & 0xFF)
-        expect = {k for k, p in enumerate(pairs) if (p & 0xFF) == a or ((p >> 8) & 0xFF) == a}
-        assert mine == expect
+    _check_steps(h, pairs, steps)
     # bodies: depth-first order, subtree atom ranges contiguous and nested
     parent = brec[:, 3]
     begin, end = brec[:, 8], brec[:, 9]
