@@ -66,17 +66,23 @@ struct Conf {
 // Per-warp shared scratch (layout in scratch_layout).
 struct WarpScratch {
   float4* pre;     // [kMaxAtoms][2] inclusive prefix sums of (g, (r - p) x g): (gx, gy, gz, cx), (cy, cz, -, -)
-  float* H;        // [kMaxDim][kMaxDim] BFGS inverse Hessian, row j owned by lane j
-  float* cur;      // [7 + kMaxDim] current conformation
-  float* best;     // [7 + kMaxDim] best conformation
+  float* H;        // [6 + T][kHStride] BFGS inverse Hessian, row j owned by lane j
+  float* vec;      // [3][kHStride] vectors broadcast to the H rows: g', s, u (BFGS update)
+  float* x;        // [7 + kMaxDim] local optimiser: current iterate (BFGS) / best iterate (BB)
+  float* cur;      // [7 + kMaxDim] current conformation of the chain
+  float* best;     // [7 + kMaxDim] best conformation of the chain
 };
 
 constexpr int kConfFloats = 7 + kMaxDim;
+// Row stride of H (floats): >= kMaxDim rounded up to float4, and 7 float4 per row
+// so that rows j = 0..7 fall on distinct 16-byte bank groups (float4 row reads
+// by the lanes need the minimum number of shared-memory wavefronts).
+constexpr int kHStride = 28;
+static_assert(kHStride >= ((kMaxDim + 3) & ~3) && (kHStride / 4) % 2 == 1, "H row stride");
 __host__ __device__ constexpr int align16i(int x) { return (x + 15) & ~15; }
-// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions); H rows
-// keep the stride kMaxDim (odd: lanes hit distinct banks).
+// Per-warp scratch sized for a group's largest ligand (n_atoms, torsions).
 struct ScratchLayout {
-  int pre, H, cur, best, bytes;
+  int pre, H, vec, x, cur, best, bytes;
 };
 __host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsions, int n_pairs, int apl) {
   (void)n_pairs;
@@ -85,7 +91,9 @@ __host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsi
   const int D = 6 + n_torsions;
   l.pre = 0;
   l.H = l.pre + align16i(32 * n_atoms);
-  l.cur = l.H + align16i(4 * kMaxDim * D);
+  l.vec = l.H + align16i(4 * kHStride * D);
+  l.x = l.vec + align16i(4 * 3 * kHStride);
+  l.cur = l.x + align16i(4 * kConfFloats);
   l.best = l.cur + align16i(4 * kConfFloats);
   l.bytes = l.best + align16i(4 * kConfFloats);
   return l;
@@ -94,6 +102,8 @@ __device__ __forceinline__ WarpScratch warp_scratch_at(uint8_t* base, const Scra
   WarpScratch W;
   W.pre = reinterpret_cast<float4*>(base + l.pre);
   W.H = reinterpret_cast<float*>(base + l.H);
+  W.vec = reinterpret_cast<float*>(base + l.vec);
+  W.x = reinterpret_cast<float*>(base + l.x);
   W.cur = reinterpret_cast<float*>(base + l.cur);
   W.best = reinterpret_cast<float*>(base + l.best);
   return W;
@@ -340,11 +350,6 @@ __device__ __forceinline__ Conf apply_step(const Conf& c, float s, int T) {
   return o;
 }
 
-struct OptOut {
-  float e;
-  uint32_t evals;
-};
-
 // Four warp sums at once (one butterfly, independent chains in flight).
 __device__ __forceinline__ void warp_sum4(float& a, float& b, float& c, float& d) {
 #pragma unroll
@@ -356,106 +361,72 @@ __device__ __forceinline__ void warp_sum4(float& a, float& b, float& c, float& d
   }
 }
 
-// BFGS with Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1,
-// inverse-Hessian update Eq. 6.17).  Row j of H lives in shared memory and is
-// owned by lane j; vectors are held one component per lane.
-// One matrix-vector product per iteration: with d = -H g and y = g' - g,
-// H y = H g' + d, and the next direction -H' g' follows from H g' and the dot
-// products s.g', (Hy).g' without forming H' g' separately:
+// BFGS inverse-Hessian step after an accepted line search (Nocedal & Wright
+// Eq. 6.17), lane j holding row j of H and component j of the vectors.  With
+// d = -H g and y = g' - g, H y = H g' + d, so one product H g' gives both the
+// update and the next direction:
 //   H' g' = H g' - rho (s (Hy.g') + Hy (s.g')) + (rho^2 y.Hy + rho) s (s.g').
-template <int APL, int FMT>
-__device__ __forceinline__ OptOut bfgs_warp(const MapView& M, const LigView& L, const LaneLig<APL>& R,
-                                            const WarpScratch& W, Conf& x, int max_iters) {
+// H is updated in place as H_jk += s_j u_k - rho Hy_j s_k, u = (rho^2 y.Hy + rho) s
+// - rho Hy.  Returns the new direction -H' g' (0 beyond D).
+__device__ __forceinline__ float bfgs_update(const WarpScratch& W, int D, float s, float y, float gn, float d) {
   const int lane = threadIdx.x & 31;
-  const int D = 6 + L.T;
-  float* Hrow = W.H + kMaxDim * (lane < kMaxDim ? lane : 0);
-  float g;
-  float e = eval_conf<APL, FMT>(M, L, R, W, x, g, DSDP_TERM_ALL);
-  uint32_t evals = 1;
-  if (lane < D)
-    for (int k = 0; k < D; ++k) Hrow[k] = (k == lane) ? 1.f : 0.f;
-  float d = -g;  // H0 = I
-  float gd = -warp_sum(g * g);
-  for (int it = 0; it < max_iters; ++it) {
-    float alpha = 1.f, et = 0.f, gt = 0.f;
-    Conf xt;
-    bool ok = false;
-    for (int trial = 0; trial < kMaxTrials; ++trial) {
-      xt = apply_step(x, alpha * d, L.T);
-      et = eval_conf<APL, FMT>(M, L, R, W, xt, gt, DSDP_TERM_ALL);
-      ++evals;
-      if (et <= e + kArmijoC1 * alpha * gd) {
-        ok = true;
-        break;
-      }
-      alpha *= kShrink;
-    }
-    if (!ok) break;
-    const float s = alpha * d, y = gt - g;
-    x = xt;
-    g = gt;
-    e = et;
-    if (it + 1 == max_iters) break;  // no further direction needed
-    float hg = 0.f;  // (H g')_lane
-    for (int k = 0; k < D; ++k) {
-      const float gk = __shfl_sync(kFull, gt, k);
-      if (lane < D) hg += Hrow[k] * gk;
-    }
-    const float hy = lane < D ? hg + d : 0.f;
-    float sy = s * y, yhy = y * hy, hyg = hy * gt, sg = s * gt;
-    warp_sum4(sy, yhy, hyg, sg);
-    if (sy > kMinCurvature) {
-      const float rho = 1.f / sy;
-      const float coef = rho * rho * yhy + rho;
-      for (int k = 0; k < D; ++k) {
-        const float sk = __shfl_sync(kFull, s, k), hk = __shfl_sync(kFull, hy, k);
-        if (lane < D) Hrow[k] += coef * s * sk - rho * (s * hk + hy * sk);
-      }
-      d = -(hg - rho * (s * hyg + hy * sg) + coef * s * sg);
-    } else {
-      d = -hg;
-    }
-    if (lane >= D) d = 0.f;
-    gd = warp_sum(g * d);  // computed directly: the sufficient-decrease test must see the true slope
-  }
-  return OptOut{e, evals};
-}
-
-// Barzilai-Borwein (the paper's second modification, Sec. 2 / ref. 37): BB1
-// step s.s / s.y without line search, clamped; returns the best iterate.
-template <int APL, int FMT>
-__device__ __forceinline__ OptOut bb_warp(const MapView& M, const LigView& L, const LaneLig<APL>& R,
-                                          const WarpScratch& W, Conf& x, int max_iters) {
-  float g;
-  float e = eval_conf<APL, FMT>(M, L, R, W, x, g, DSDP_TERM_ALL);
-  uint32_t evals = 1;
-  Conf best = x;
-  float ebest = e;
-  float alpha = kBBAlpha0;
-  for (int it = 0; it < max_iters; ++it) {
-    const float s = -alpha * g;
-    x = apply_step(x, s, L.T);
-    float gn;
-    e = eval_conf<APL, FMT>(M, L, R, W, x, gn, DSDP_TERM_ALL);
-    ++evals;
-    const float sy = warp_sum(s * (gn - g));
-    const float ss = warp_sum(s * s);
-    alpha = sy > 0.f ? fminf(fmaxf(ss / sy, kBBAlphaMin), kBBAlphaMax) : kBBAlphaMax;
-    g = gn;
-    if (e < ebest) {
-      ebest = e;
-      best = x;
+  const int D4 = (D + 3) & ~3;
+  float* vg = W.vec;
+  float* vs = W.vec + kHStride;
+  float* vu = W.vec + 2 * kHStride;
+  const float4* Hrow = reinterpret_cast<const float4*>(W.H + kHStride * (lane < D ? lane : 0));
+  if (lane < D4) vg[lane] = lane < D ? gn : 0.f;
+  __syncwarp();
+  float hg = 0.f;  // (H g')_lane
+  if (lane < D) {
+    for (int k = 0; k < D4; k += 4) {
+      const float4 h = Hrow[k >> 2], v = *reinterpret_cast<const float4*>(vg + k);
+      hg = fmaf(h.x, v.x, fmaf(h.y, v.y, fmaf(h.z, v.z, fmaf(h.w, v.w, hg))));
     }
   }
-  x = best;
-  return OptOut{ebest, evals};
+  const float hy = lane < D ? hg + d : 0.f;
+  float sy = s * y, yhy = y * hy, hyg = hy * gn, sg = s * gn;
+  warp_sum4(sy, yhy, hyg, sg);
+  float dn;
+  if (sy > kMinCurvature) {
+    const float rho = 1.f / sy;
+    const float coef = rho * rho * yhy + rho;
+    if (lane < D4) {
+      vs[lane] = lane < D ? s : 0.f;
+      vu[lane] = lane < D ? coef * s - rho * hy : 0.f;
+    }
+    __syncwarp();
+    if (lane < D) {
+      float4* Hw = reinterpret_cast<float4*>(W.H + kHStride * lane);
+      const float a = -rho * hy;
+      for (int k = 0; k < D4; k += 4) {
+        float4 h = Hw[k >> 2];
+        const float4 u = *reinterpret_cast<const float4*>(vu + k), v = *reinterpret_cast<const float4*>(vs + k);
+        h.x = fmaf(s, u.x, fmaf(a, v.x, h.x));
+        h.y = fmaf(s, u.y, fmaf(a, v.y, h.y));
+        h.z = fmaf(s, u.z, fmaf(a, v.z, h.z));
+        h.w = fmaf(s, u.w, fmaf(a, v.w, h.w));
+        Hw[k >> 2] = h;
+      }
+    }
+    dn = -(hg - rho * (s * hyg + hy * sg) + coef * s * sg);
+  } else {
+    dn = -hg;
+  }
+  __syncwarp();  // vec is rewritten by the next update
+  return lane < D ? dn : 0.f;
 }
 
-template <int APL, int FMT>
-__device__ __forceinline__ OptOut local_opt(const MapView& M, const LigView& L, const LaneLig<APL>& R,
-                                            const WarpScratch& W, Conf& x, int optimizer, int iters) {
-  return optimizer == DSDP_OPT_BB ? bb_warp<APL, FMT>(M, L, R, W, x, iters)
-                                  : bfgs_warp<APL, FMT>(M, L, R, W, x, iters);
+// H = I (rows 0..D-1, columns up to D rounded to float4).
+__device__ __forceinline__ void bfgs_reset(const WarpScratch& W, int D) {
+  const int lane = threadIdx.x & 31;
+  const int D4 = (D + 3) & ~3;
+  if (lane < D) {
+    float4* Hw = reinterpret_cast<float4*>(W.H + kHStride * lane);
+    for (int k = 0; k < D4; k += 4)
+      Hw[k >> 2] = make_float4(k == lane ? 1.f : 0.f, k + 1 == lane ? 1.f : 0.f, k + 2 == lane ? 1.f : 0.f,
+                               k + 3 == lane ? 1.f : 0.f);
+  }
 }
 
 // Write conf (7 + T floats) from lane layout: lanes 0..2 p, 3..6 q, 7 + k theta_k.
@@ -487,91 +458,186 @@ __device__ __forceinline__ Conf load_conf(const float* in, int T) {
 }
 
 // One Monte Carlo chain (Sec. 2: one of many short independent copies; Vina's
-// mutation and Metropolis rules).  The current and best conformations wait in
-// shared memory; only the candidate being optimised is held in registers.
+// mutation and Metropolis rules) with its local optimisations -- BFGS with
+// Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1) or
+// Barzilai-Borwein (the paper's second modification, Sec. 2 / ref. 37: BB1 step
+// s.s / s.y, clamped, no line search, best iterate returned).
+//
+// The whole chain is one loop around a single score + gradient evaluation: a
+// small state machine decides, from each evaluation, the next conformation to
+// evaluate.  The optimiser's iterate and the chain's current and best
+// conformations wait in shared memory; only the conformation under evaluation
+// and a few scalars stay in registers.
 template <int APL, int FMT>
 __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& W, int chain) {
+  enum : int { kStart = 0, kTrial = 1, kBB = 2 };
   const int lane = threadIdx.x & 31;
   const MapView M = make_map_view(J);
   LaneLig<APL> R;
   load_lane_lig<APL>(L, R);
-  const int T = L.T, nx = 7 + T;
+  const int T = L.T, nx = 7 + T, D = 6 + T;
+  const bool bb = J.optimizer == DSDP_OPT_BB;
+  const int max_iters = J.n_opt_iters;
   const ChainStream rs{J.seed_lo, J.seed_hi, (uint32_t)chain};
   // initial conformation: uniform word n of step 0 is word n % 4 of block n / 4
-  Conf cand;
+  Conf xt;
   {
     const uint4 b0 = rs.block(0, 0), b1 = rs.block(0, 1);
-    cand.p = make_float3(J.box_lo[0] + J.box_size[0] * ChainStream::to_uniform(b0.x),
-                         J.box_lo[1] + J.box_size[1] * ChainStream::to_uniform(b0.y),
-                         J.box_lo[2] + J.box_size[2] * ChainStream::to_uniform(b0.z));
+    xt.p = make_float3(J.box_lo[0] + J.box_size[0] * ChainStream::to_uniform(b0.x),
+                       J.box_lo[1] + J.box_size[1] * ChainStream::to_uniform(b0.y),
+                       J.box_lo[2] + J.box_size[2] * ChainStream::to_uniform(b0.z));
     const float u1 = ChainStream::to_uniform(b0.w), u2 = ChainStream::to_uniform(b1.x),
                 u3 = ChainStream::to_uniform(b1.y);
     float s2, c2, s3, c3;
     sincosf(kTwoPiF * u2, &s2, &c2);
     sincosf(kTwoPiF * u3, &s3, &c3);
     const float a = sqrtf(1.f - u1), b = sqrtf(u1);
-    cand.q = Quat{b * c3, a * s2, a * c2, b * s3};
+    xt.q = Quat{b * c3, a * s2, a * c2, b * s3};
     float th = 0.f;
     if (lane >= 6 && lane < 6 + T) {
       const uint4 bk = rs.block(0, (uint32_t)(lane >> 2));
       th = kPiF - kTwoPiF * ChainStream::to_uniform(pick(bk, lane & 3));
     }
-    cand.th = th;
+    xt.th = th;
   }
-  OptOut o = local_opt<APL, FMT>(M, L, R, W, cand, J.optimizer, J.n_opt_iters);
-  float e_cur = o.e, e_best = o.e;
-  uint32_t evals = o.evals;
-  store_conf(W.cur, cand, T);
-  store_conf(W.best, cand, T);
   const size_t trace_stride = (size_t)nx + 4;
   float* trace = J.trace ? J.trace + (size_t)chain * (J.n_steps + 1) * trace_stride : nullptr;
-  if (trace) {
-    store_conf(trace, cand, T);
-    if (lane == 0) {
-      trace[nx + 0] = e_cur;
-      trace[nx + 1] = e_cur;
-      trace[nx + 2] = -1.f;
-      trace[nx + 3] = 1.f;
-    }
-  }
-  __syncwarp();
   const float inv_gyr = 1.f / L.h->gyration_radius;
-  for (int step = 1; step <= J.n_steps; ++step) {
-    const uint4 w0 = rs.block((uint32_t)step, 0);
-    const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
-    cand = load_conf(W.cur, T);
-    if (mode == 0) {
-      const float3 b = unit_ball(rs, (uint32_t)step);
-      cand.p = cand.p + kMutationAmplitude * b;
-    } else if (mode == 1) {
-      const float3 b = unit_ball(rs, (uint32_t)step);
-      const float k = kMutationAmplitude * inv_gyr;
-      cand.q = qnormalize(qmul(quat_from_rotvec(k * b.x, k * b.y, k * b.z), cand.q));
-    } else if (lane == 6 + (mode - 2)) {
-      cand.th = kPiF - kTwoPiF * ChainStream::to_uniform(w0.z);
+  // optimiser state (warp-uniform except g and dir: component `lane`)
+  int phase = kStart, it = 0, trial = 0;
+  float e = 0.f, gd = 0.f, alpha = 1.f, g = 0.f, dir = 0.f, e_opt_best = 0.f;
+  // chain state
+  int step = 0;
+  float e_cur = 0.f, e_best = 0.f;
+  uint32_t evals = 0;
+  for (;;) {
+    float gn;
+    const float en = eval_conf<APL, FMT>(M, L, R, W, xt, gn, DSDP_TERM_ALL);
+    ++evals;
+    bool done = false;
+    if (phase == kStart) {  // first evaluation of a local optimisation
+      e = en;
+      g = gn;
+      store_conf(W.x, xt, T);
+      if (max_iters == 0) {
+        done = true;
+      } else if (!bb) {
+        bfgs_reset(W, D);
+        dir = -g;  // H0 = I
+        gd = -warp_sum(g * g);
+        it = trial = 0;
+        alpha = 1.f;
+        xt = apply_step(xt, dir, T);
+        phase = kTrial;
+      } else {
+        e_opt_best = e;
+        alpha = kBBAlpha0;
+        it = 0;
+        dir = -alpha * g;
+        xt = apply_step(xt, dir, T);
+        phase = kBB;
+      }
+    } else if (phase == kTrial) {  // BFGS: Armijo test of the trial point x + alpha d
+      if (en <= e + kArmijoC1 * alpha * gd) {
+        const float s = alpha * dir, y = gn - g;
+        g = gn;
+        e = en;
+        store_conf(W.x, xt, T);
+        if (++it == max_iters) {
+          done = true;
+        } else {
+          dir = bfgs_update(W, D, s, y, gn, dir);
+          gd = warp_sum(g * dir);  // computed directly: the sufficient-decrease test must see the true slope
+          alpha = 1.f;
+          trial = 0;
+          xt = apply_step(xt, dir, T);
+        }
+      } else {
+        alpha *= kShrink;
+        if (++trial == kMaxTrials) {
+          done = true;  // no acceptable step: the optimisation ends at the current iterate
+        } else {
+          __syncwarp();
+          xt = apply_step(load_conf(W.x, T), alpha * dir, T);
+        }
+      }
+    } else {  // BB: x_{k+1} = x_k + s_k evaluated; next step length from s.s / s.y
+      const float sy = warp_sum(dir * (gn - g));
+      const float ss = warp_sum(dir * dir);
+      alpha = sy > 0.f ? fminf(fmaxf(ss / sy, kBBAlphaMin), kBBAlphaMax) : kBBAlphaMax;
+      g = gn;
+      if (en < e_opt_best) {
+        e_opt_best = en;
+        store_conf(W.x, xt, T);
+      }
+      if (++it == max_iters) {
+        done = true;
+      } else {
+        dir = -alpha * g;
+        xt = apply_step(xt, dir, T);
+      }
     }
-    o = local_opt<APL, FMT>(M, L, R, W, cand, J.optimizer, J.n_opt_iters);
-    evals += o.evals;
-    const float u = ChainStream::to_uniform(w0.y);
-    const bool accept = (o.e < e_cur) || (u < expf(-(o.e - e_cur) / J.temperature));
-    if (accept) {
-      e_cur = o.e;
-      store_conf(W.cur, cand, T);
-      if (o.e < e_best) {
-        e_best = o.e;
-        store_conf(W.best, cand, T);
+    if (!done) continue;
+    // ---- local optimisation finished: its result is W.x with energy eo
+    const float eo = (bb && max_iters > 0) ? e_opt_best : e;
+    __syncwarp();
+    if (step == 0) {
+      e_cur = e_best = eo;
+      if (lane < nx) {
+        W.cur[lane] = W.x[lane];
+        W.best[lane] = W.x[lane];
+      }
+      if (trace) {
+        if (lane < nx) trace[lane] = W.x[lane];
+        if (lane == 0) {
+          trace[nx + 0] = e_cur;
+          trace[nx + 1] = e_cur;
+          trace[nx + 2] = -1.f;
+          trace[nx + 3] = 1.f;
+        }
+      }
+    } else {
+      const uint4 w0 = rs.block((uint32_t)step, 0);
+      const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
+      const float u = ChainStream::to_uniform(w0.y);
+      const bool accept = (eo < e_cur) || (u < expf(-(eo - e_cur) / J.temperature));
+      if (accept) {
+        e_cur = eo;
+        if (lane < nx) W.cur[lane] = W.x[lane];
+        if (eo < e_best) {
+          e_best = eo;
+          if (lane < nx) W.best[lane] = W.x[lane];
+        }
+      }
+      if (trace) {
+        float* t = trace + (size_t)step * trace_stride;
+        if (lane < nx) t[lane] = W.cur[lane];
+        if (lane == 0) {
+          t[nx + 0] = eo;
+          t[nx + 1] = e_cur;
+          t[nx + 2] = (float)mode;
+          t[nx + 3] = accept ? 1.f : 0.f;
+        }
       }
     }
     __syncwarp();
-    if (trace) {
-      float* t = trace + (size_t)step * trace_stride;
-      if (lane < nx) t[lane] = W.cur[lane];
-      if (lane == 0) {
-        t[nx + 0] = o.e;
-        t[nx + 1] = e_cur;
-        t[nx + 2] = (float)mode;
-        t[nx + 3] = accept ? 1.f : 0.f;
+    if (++step > J.n_steps) break;
+    // ---- mutation of the current conformation (the next local optimisation's start)
+    {
+      const uint4 w0 = rs.block((uint32_t)step, 0);
+      const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
+      xt = load_conf(W.cur, T);
+      if (mode == 0) {
+        const float3 b = unit_ball(rs, (uint32_t)step);
+        xt.p = xt.p + kMutationAmplitude * b;
+      } else if (mode == 1) {
+        const float3 b = unit_ball(rs, (uint32_t)step);
+        const float k = kMutationAmplitude * inv_gyr;
+        xt.q = qnormalize(qmul(quat_from_rotvec(k * b.x, k * b.y, k * b.z), xt.q));
+      } else if (lane == 6 + (mode - 2)) {
+        xt.th = kPiF - kTwoPiF * ChainStream::to_uniform(w0.z);
       }
+      phase = kStart;
     }
   }
   if (lane < nx) J.chain_best_conf[(size_t)chain * nx + lane] = W.best[lane];
