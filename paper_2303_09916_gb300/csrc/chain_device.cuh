@@ -175,14 +175,10 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     const float3 Ob = shfl3(O, b);
     pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
   }
-  // ---- inter, part 1: locate each atom's cell and ask L2 for its 8 corners now,
-  //      so that the pair terms below overlap the gather latency
+  // ---- inter, part 1: locate each atom's cell
   MapCell cell[APL];
 #pragma unroll
-  for (int s = 0; s < APL; ++s) {
-    cell[s] = map_cell(M, pos[s]);
-    if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) map_prefetch<FMT>(M, type[s], cell[s]);
-  }
+  for (int s = 0; s < APL; ++s) cell[s] = map_cell(M, pos[s]);
   float e_lane = 0.f;
   float3 g[APL];
 #pragma unroll
@@ -194,41 +190,60 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   if (flags & DSDP_TERM_INTRA) {
     float2 e_pair = make_float2(0.f, 0.f);
     const uint2* tab = L.steps + lane;
+    if (APL == 1) {
+      // packed accumulators: component .x collects the even steps, .y the odd ones
+      const float2 px = splat2(pos[0].x), py = splat2(pos[0].y), pz = splat2(pos[0].z);
+      float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
 #pragma unroll 1
-    for (int st = 0; st < L.n_steps; st += 2) {
-      const uint2 t0 = tab[st * 32], t1 = tab[st * 32 + 32];
-      const int pa0 = t0.x & 31, pa1 = t1.x & 31;
-      const int pr0 = (t0.x >> 5) & 31, pr1 = (t1.x >> 5) & 31;
-      float3 a0 = pos[0], a1 = pos[0], s0 = pos[0], s1 = pos[0];
-      if (APL == 2) {
-        if (t0.x & (1u << 10)) a0 = pos[APL - 1];
-        if (t1.x & (1u << 10)) a1 = pos[APL - 1];
-        if (t0.x & (1u << 11)) s0 = pos[APL - 1];
-        if (t1.x & (1u << 11)) s1 = pos[APL - 1];
+      for (int st = 0; st < L.n_steps; st += 2) {
+        const uint2 t0 = tab[st * 32], t1 = tab[st * 32 + 32];
+        // shfl.idx reads the source lane from bits 0-4 only: the entry's partner field
+        const float3 b0 = shfl3(pos[0], (int)t0.x), b1 = shfl3(pos[0], (int)t1.x);
+        const float2 dx = __ffma2_rn(make_float2(b0.x, b1.x), splat2(-1.f), px);
+        const float2 dy = __ffma2_rn(make_float2(b0.y, b1.y), splat2(-1.f), py);
+        const float2 dz = __ffma2_rn(make_float2(b0.z, b1.z), splat2(-1.f), pz);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const uint32_t both = t0.x | t1.x;  // bits 14 / 15: warp-uniform
+        const float2 wh = make_float2((t0.x & (1u << 12)) ? kWHydrophobic : 0.f, (t1.x & (1u << 12)) ? kWHydrophobic : 0.f);
+        const float2 wb = make_float2((t0.x & (1u << 13)) ? kWHBond : 0.f, (t1.x & (1u << 13)) ? kWHBond : 0.f);
+        float2 e, sp;
+        vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), wh, wb, (both >> 14) & 1,
+                     (both >> 15) & 1, e, sp);
+        e_pair = __fadd2_rn(e_pair, e);
+        const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
+        // reaction forces of the pairs this lane is passive in (source lane: bits 5-9)
+        const float3 c0 = shfl3(make_float3(fx.x, fy.x, fz.x), (int)(t0.x >> 5));
+        const float3 c1 = shfl3(make_float3(fx.y, fy.y, fz.y), (int)(t1.x >> 5));
+        ax = __ffma2_rn(make_float2(c0.x, c1.x), splat2(-1.f), __fadd2_rn(ax, fx));
+        ay = __ffma2_rn(make_float2(c0.y, c1.y), splat2(-1.f), __fadd2_rn(ay, fy));
+        az = __ffma2_rn(make_float2(c0.z, c1.z), splat2(-1.f), __fadd2_rn(az, fz));
       }
-      const float3 b0 = shfl3(s0, pa0), b1 = shfl3(s1, pa1);
-      const float2 dx = make_float2(a0.x - b0.x, a1.x - b1.x);
-      const float2 dy = make_float2(a0.y - b0.y, a1.y - b1.y);
-      const float2 dz = make_float2(a0.z - b0.z, a1.z - b1.z);
-      const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-      const uint32_t both = t0.x | t1.x;  // bits 14 / 15: warp-uniform
-      const float2 wh = make_float2((t0.x & (1u << 12)) ? kWHydrophobic : 0.f, (t1.x & (1u << 12)) ? kWHydrophobic : 0.f);
-      const float2 wb = make_float2((t0.x & (1u << 13)) ? kWHBond : 0.f, (t1.x & (1u << 13)) ? kWHBond : 0.f);
-      float2 e, sp;
-      vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), wh, wb, (both >> 14) & 1,
-                   (both >> 15) & 1, e, sp);
-      e_pair = __fadd2_rn(e_pair, e);
-      const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
-      // reaction forces of the pairs this lane is passive in
-      const float3 c0 = shfl3(make_float3(fx.x, fy.x, fz.x), pr0);
-      const float3 c1 = shfl3(make_float3(fx.y, fy.y, fz.y), pr1);
-      if (APL == 1) {
-        g[0].x += (fx.x + fx.y) - (c0.x + c1.x);
-        g[0].y += (fy.x + fy.y) - (c0.y + c1.y);
-        g[0].z += (fz.x + fz.y) - (c0.z + c1.z);
-      } else {
+      g[0].x += ax.x + ax.y;
+      g[0].y += ay.x + ay.y;
+      g[0].z += az.x + az.y;
+    } else {
+#pragma unroll 1
+      for (int st = 0; st < L.n_steps; st += 2) {
+        const uint2 t0 = tab[st * 32], t1 = tab[st * 32 + 32];
         const bool ac0 = t0.x & (1u << 10), ac1 = t1.x & (1u << 10);
         const bool pc0 = t0.x & (1u << 11), pc1 = t1.x & (1u << 11);
+        const float3 a0 = ac0 ? pos[APL - 1] : pos[0], a1 = ac1 ? pos[APL - 1] : pos[0];
+        const float3 s0 = pc0 ? pos[APL - 1] : pos[0], s1 = pc1 ? pos[APL - 1] : pos[0];
+        const float3 b0 = shfl3(s0, (int)t0.x), b1 = shfl3(s1, (int)t1.x);
+        const float2 dx = make_float2(a0.x - b0.x, a1.x - b1.x);
+        const float2 dy = make_float2(a0.y - b0.y, a1.y - b1.y);
+        const float2 dz = make_float2(a0.z - b0.z, a1.z - b1.z);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const uint32_t both = t0.x | t1.x;
+        const float2 wh = make_float2((t0.x & (1u << 12)) ? kWHydrophobic : 0.f, (t1.x & (1u << 12)) ? kWHydrophobic : 0.f);
+        const float2 wb = make_float2((t0.x & (1u << 13)) ? kWHBond : 0.f, (t1.x & (1u << 13)) ? kWHBond : 0.f);
+        float2 e, sp;
+        vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), wh, wb, (both >> 14) & 1,
+                     (both >> 15) & 1, e, sp);
+        e_pair = __fadd2_rn(e_pair, e);
+        const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
+        const float3 c0 = shfl3(make_float3(fx.x, fy.x, fz.x), (int)(t0.x >> 5));
+        const float3 c1 = shfl3(make_float3(fx.y, fy.y, fz.y), (int)(t1.x >> 5));
         g[0].x += (ac0 ? 0.f : fx.x) + (ac1 ? 0.f : fx.y) - (pc0 ? 0.f : c0.x) - (pc1 ? 0.f : c1.x);
         g[0].y += (ac0 ? 0.f : fy.x) + (ac1 ? 0.f : fy.y) - (pc0 ? 0.f : c0.y) - (pc1 ? 0.f : c1.y);
         g[0].z += (ac0 ? 0.f : fz.x) + (ac1 ? 0.f : fz.y) - (pc0 ? 0.f : c0.z) - (pc1 ? 0.f : c1.z);
@@ -377,12 +392,17 @@ __device__ __forceinline__ float bfgs_update(const WarpScratch& W, int D, float 
   const float4* Hrow = reinterpret_cast<const float4*>(W.H + kHStride * (lane < D ? lane : 0));
   if (lane < D4) vg[lane] = lane < D ? gn : 0.f;
   __syncwarp();
-  float hg = 0.f;  // (H g')_lane
+  float hg = 0.f;  // (H g')_lane: four independent partial sums
   if (lane < D) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = 0; k < D4; k += 4) {
       const float4 h = Hrow[k >> 2], v = *reinterpret_cast<const float4*>(vg + k);
-      hg = fmaf(h.x, v.x, fmaf(h.y, v.y, fmaf(h.z, v.z, fmaf(h.w, v.w, hg))));
+      acc.x = fmaf(h.x, v.x, acc.x);
+      acc.y = fmaf(h.y, v.y, acc.y);
+      acc.z = fmaf(h.z, v.z, acc.z);
+      acc.w = fmaf(h.w, v.w, acc.w);
     }
+    hg = (acc.x + acc.y) + (acc.z + acc.w);
   }
   const float hy = lane < D ? hg + d : 0.f;
   float sy = s * y, yhy = y * hy, hyg = hy * gn, sg = s * gn;

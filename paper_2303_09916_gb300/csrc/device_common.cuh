@@ -203,7 +203,10 @@ __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 // the term.
 __device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, float2 wb, bool use_hyd, bool use_hb,
                                              float2& e, float2& s) {
-  const float2 ir = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+  // 1e-30 keeps an idle slot's r2 = 0 finite (r2 ir = 0 there); real pairs are
+  // Angstroms apart, where it changes nothing
+  const float2 rp = __fadd2_rn(r2, splat2(1e-30f));
+  const float2 ir = make_float2(rsqrtf(rp.x), rsqrtf(rp.y));
   float2 d = __ffma2_rn(r2, ir, nrs);
   d.x = r2.x < kCutoff * kCutoff ? d.x : kFarD;
   d.y = r2.y < kCutoff * kCutoff ? d.y : kFarD;
@@ -326,26 +329,6 @@ __device__ __forceinline__ MapCell map_cell(const MapView& M, float3 r) {
   c.ey = (uy - cy) * M.h;
   c.ez = (uz - cz) * M.h;
   return c;
-}
-
-// Ask L2 to fetch the 8 corners of a cell for map type t (no registers held;
-// the loads of map_interp later find them there).
-template <int FMT>
-__device__ __forceinline__ void map_prefetch(const MapView& M, int t, const MapCell& c) {
-  const unsigned sxy = (unsigned)M.nx * (unsigned)M.ny;
-  const unsigned b = (unsigned)t * sxy * (unsigned)M.nz + c.base;
-  const unsigned nb = (unsigned)(fmt_channels(FMT) * fmt_elem_bytes(FMT));
-  const char* p = reinterpret_cast<const char*>(M.maps);
-  const unsigned off[4] = {b, b + M.nx, b + sxy, b + sxy + M.nx};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    // corners x and x + 1 are adjacent: one prefetch per 128-byte line they touch
-    const char* a0 = p + (size_t)off[k] * nb;
-    const char* a1 = a0 + 2 * nb - 1;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a0));
-    if ((reinterpret_cast<uintptr_t>(a0) >> 7) != (reinterpret_cast<uintptr_t>(a1) >> 7))
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(a1));
-  }
 }
 
 // Trilinear score (Eq. 2) and gradient (Eq. 4 from the gradient maps, or

@@ -124,12 +124,29 @@ void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>&
     u = lane_of(a);
     v = lane_of(b);
   };
-  for (int p = 0; p < P; ++p) {
+  // Pairs with a hydrophobic or H-bond term ("ramp" pairs) are coloured first,
+  // from the top of the palette, the others from the bottom: the ramp pairs then
+  // gather in a few steps, and the kernels skip those terms in the other steps.
+  std::vector<int> order;
+  for (int p = 0; p < P; ++p)
+    if (pc[p] != 0) order.push_back(p);
+  const size_t n_ramp = order.size();
+  for (int p = 0; p < P; ++p)
+    if (pc[p] == 0) order.push_back(p);
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    const int p = order[oi];
     int u, v;
     ends(p, u, v);
-    int c1 = 0, c2 = 0;
-    while (A(u, c1) >= 0) ++c1;
-    while (B(v, c2) >= 0) ++c2;
+    int c1, c2;
+    if (oi < n_ramp) {
+      c1 = c2 = delta - 1;
+      while (A(u, c1) >= 0) --c1;
+      while (B(v, c2) >= 0) --c2;
+    } else {
+      c1 = c2 = 0;
+      while (A(u, c1) >= 0) ++c1;
+      while (B(v, c2) >= 0) ++c2;
+    }
     if (B(v, c1) >= 0) {
       // swap c1 / c2 along the path from v (passive side) that starts with colour c1
       std::vector<int> path;
@@ -163,10 +180,18 @@ void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>&
     A(u, c1) = p;
     B(v, c1) = p;
   }
-  // ---- table
+  // ---- table: steps holding ramp pairs first (they are processed two at a time)
+  std::vector<int> col_order;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c = delta - 1; c >= 0; --c) {
+      bool ramp = false;
+      for (int v = 0; v < V; ++v) ramp |= A(v, c) >= 0 && pc[A(v, c)] != 0;
+      if (ramp == (pass == 0)) col_order.push_back(c);
+    }
   n_steps = (delta + 1) & ~1;
   table.assign((size_t)n_steps * V * 2, 0u);
-  for (int c = 0; c < n_steps; ++c) {
+  for (int st = 0; st < n_steps; ++st) {
+    const int c = st < delta ? col_order[st] : delta;  // delta: the empty padding step
     uint32_t step_bits = 0;
     int idle = -1;
     for (int v = 0; v < V && c < delta; ++v) {
@@ -190,8 +215,8 @@ void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>&
         x |= (uint32_t)(b % apl) << 11;
       }
       x |= step_bits;
-      table[((size_t)c * V + v) * 2] = x;
-      memcpy(&table[((size_t)c * V + v) * 2 + 1], &nrs, 4);
+      table[((size_t)st * V + v) * 2] = x;
+      memcpy(&table[((size_t)st * V + v) * 2 + 1], &nrs, 4);
     }
   }
 }
