@@ -175,10 +175,6 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     const float3 Ob = shfl3(O, b);
     pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
   }
-  // ---- inter, part 1: locate each atom's cell
-  MapCell cell[APL];
-#pragma unroll
-  for (int s = 0; s < APL; ++s) cell[s] = map_cell(M, pos[s]);
   float e_lane = 0.f;
   float3 g[APL];
 #pragma unroll
@@ -254,12 +250,14 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     }
     e_lane += e_pair.x + e_pair.y;
   }
-  // ---- inter, part 2: trilinear score and gradient (Eq. 2, Eq. 4 / Eq. 3)
+  // ---- inter: trilinear score and gradient (Eq. 2, Eq. 4 / Eq. 3)
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
     if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) {
       float3 gi;
-      e_lane += map_interp<FMT>(M, type[s], cell[s], gi);
+      // the cell is located here, where it is used: holding it across the intra
+      // block miscompiled the two-atoms-per-lane kernels (gradient x channel lost)
+      e_lane += map_interp<FMT>(M, type[s], map_cell(M, pos[s]), gi);
       g[s] = g[s] + gi;
     }
   }

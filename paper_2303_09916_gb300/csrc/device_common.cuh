@@ -190,17 +190,33 @@ constexpr float kFarD = 100.f;                     // surface distance where eve
 
 __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 
-// Two intra-ligand pairs per lane in packed FP32x2 arithmetic (fma / mul / add
-// .f32x2 of sm_100+): the terms of vina_pair without per-lane branches, with
-// d = r2 / r + nrs, nrs = -(R_i + R_j), returning e and (de/dd) / r.
-// hydrophobic = min(max(1.5 - d, 0), 1) and H-bond = min(max(-d / 0.7, 0), 1)
-// equal the piecewise forms; their slopes are taken on the half-open intervals
-// [0.5, 1.5) and [-0.7, 0), as in vina_pair.  Pairs at or beyond the cutoff
-// take d = kFarD, and idle slots get a surface distance at least kStepIdleNrs:
-// there every term and slope is exactly zero.  wh / wb: weight of the
-// hydrophobic / H-bond term of each pair (0 where the pair does not carry it);
-// use_hyd / use_hb: warp-uniform, false when no pair of the two steps carries
-// the term.
+// gauss1 + gauss2 + repulsion of two surface distances in packed FP32x2
+// arithmetic (fma / mul / add .f32x2 of sm_100+): returns e and de/dd of each.
+__device__ __forceinline__ void steric_x2(float2 d, float2& e, float2& de) {
+  const float2 u1 = __fmul2_rn(__fmul2_rn(d, d), splat2(-4.f * kLog2E));  // -(d / 0.5)^2 / ln 2
+  const float2 b = __ffma2_rn(d, splat2(0.5f), splat2(-1.5f));             // (d - 3) / 2
+  const float2 u2 = __fmul2_rn(__fmul2_rn(b, b), splat2(-kLog2E));        // -b^2 / ln 2
+  const float2 g1 = make_float2(ex2_approx(u1.x), ex2_approx(u1.y));
+  const float2 g2 = make_float2(ex2_approx(u2.x), ex2_approx(u2.y));
+  const float2 m = make_float2(fminf(d.x, 0.f), fminf(d.y, 0.f));
+  float2 ee = __fmul2_rn(g1, splat2(kWGauss1));
+  ee = __ffma2_rn(g2, splat2(kWGauss2), ee);
+  e = __ffma2_rn(__fmul2_rn(m, m), splat2(kWRepulsion), ee);
+  float2 dd = __fmul2_rn(g1, __fmul2_rn(d, splat2(-8.f * kWGauss1)));
+  dd = __ffma2_rn(g2, __fmul2_rn(b, splat2(-kWGauss2)), dd);
+  de = __ffma2_rn(m, splat2(2.f * kWRepulsion), dd);
+}
+
+// Two intra-ligand pairs per lane in packed FP32x2 arithmetic: the terms of
+// vina_pair without per-lane branches, with d = r2 / r + nrs, nrs = -(R_i + R_j),
+// returning e and (de/dd) / r.  hydrophobic = min(max(1.5 - d, 0), 1) and
+// H-bond = min(max(-d / 0.7, 0), 1) equal the piecewise forms; their slopes are
+// taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in vina_pair.
+// Pairs at or beyond the cutoff take d = kFarD, and idle slots get a surface
+// distance at least kStepIdleNrs: there every term and slope is exactly zero.
+// wh / wb: weight of the hydrophobic / H-bond term of each pair (0 where the
+// pair does not carry it); use_hyd / use_hb: warp-uniform, false when no pair of
+// the two steps carries the term.
 __device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, float2 wb, bool use_hyd, bool use_hb,
                                              float2& e, float2& s) {
   // 1e-30 keeps an idle slot's r2 = 0 finite (r2 ir = 0 there); real pairs are
@@ -210,18 +226,8 @@ __device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, f
   float2 d = __ffma2_rn(r2, ir, nrs);
   d.x = r2.x < kCutoff * kCutoff ? d.x : kFarD;
   d.y = r2.y < kCutoff * kCutoff ? d.y : kFarD;
-  const float2 u1 = __fmul2_rn(__fmul2_rn(d, d), splat2(-4.f * kLog2E));  // -(d / 0.5)^2 / ln 2
-  const float2 b = __ffma2_rn(d, splat2(0.5f), splat2(-1.5f));             // (d - 3) / 2
-  const float2 u2 = __fmul2_rn(__fmul2_rn(b, b), splat2(-kLog2E));        // -b^2 / ln 2
-  const float2 g1 = make_float2(ex2_approx(u1.x), ex2_approx(u1.y));
-  const float2 g2 = make_float2(ex2_approx(u2.x), ex2_approx(u2.y));
-  const float2 m = make_float2(fminf(d.x, 0.f), fminf(d.y, 0.f));
-  float2 ee = __fmul2_rn(g1, splat2(kWGauss1));
-  ee = __ffma2_rn(g2, splat2(kWGauss2), ee);
-  ee = __ffma2_rn(__fmul2_rn(m, m), splat2(kWRepulsion), ee);
-  float2 de = __fmul2_rn(g1, __fmul2_rn(d, splat2(-8.f * kWGauss1)));
-  de = __ffma2_rn(g2, __fmul2_rn(b, splat2(-kWGauss2)), de);
-  de = __ffma2_rn(m, splat2(2.f * kWRepulsion), de);
+  float2 ee, de;
+  steric_x2(d, ee, de);
   if (use_hyd) {  // min(max(1.5 - d, 0), 1), slope on [0.5, 1.5)
     const float2 t = __ffma2_rn(d, splat2(-1.f), splat2(1.5f));
     ee = __ffma2_rn(wh, make_float2(__saturatef(t.x), __saturatef(t.y)), ee);

@@ -5,8 +5,11 @@
 // index order, keeps those within the cutoff of the brick's bounding box
 // (ballot compaction into shared memory, order preserved, so the sums are
 // deterministic), then every thread sums the pair score and its gradient
-// for all 8 ligand types at its vertex.  The 8 types share 4 atomic radii, so
-// each pair costs 4 x 2 exponentials instead of 8 x 2.
+// for all 8 ligand types at its vertex.  The 8 types share 4 atomic radii:
+// the gauss / repulsion terms are summed once per radius (packed FP32x2, two
+// radii per operation), and the hydrophobic and H-bond terms, which only some
+// receptor atoms carry and only at short range, in five sums of their own;
+// each type's map is its radius sum plus its own term at the end.
 #include "launch.h"
 
 namespace dsdp {
@@ -15,19 +18,8 @@ namespace {
 constexpr int kBX = 8, kBY = 8, kBZ = 4, kThreads = kBX * kBY * kBZ;
 constexpr int kChunk = 1536;
 
-// gauss1 + gauss2 + repulsion of surface distance d: e and de/dd
-__device__ __forceinline__ void steric(float d, float& e, float& de) {
-  const float a = 2.f * d;
-  const float g1 = __expf(-a * a);
-  const float b = 0.5f * (d - 3.f);
-  const float g2 = __expf(-b * b);
-  e = kWGauss1 * g1 + kWGauss2 * g2;
-  de = kWGauss1 * g1 * (-8.f * d) + kWGauss2 * g2 * (-b);
-  if (d < 0.f) {
-    e += kWRepulsion * d * d;
-    de += 2.f * kWRepulsion * d;
-  }
-}
+// hydrophobic term of surface distance d (1 below 0.5, linear to 0 at 1.5),
+// added to e and de/dd
 __device__ __forceinline__ void hydrophobic(float d, float& e, float& de) {
   if (d < 0.5f) {
     e += kWHydrophobic;
@@ -36,6 +28,7 @@ __device__ __forceinline__ void hydrophobic(float d, float& e, float& de) {
     de -= kWHydrophobic;
   }
 }
+// H-bond term (1 below -0.7, linear to 0 at 0)
 __device__ __forceinline__ void hbond(float d, float& e, float& de) {
   if (d < -0.7f) {
     e += kWHBond;
@@ -43,6 +36,14 @@ __device__ __forceinline__ void hbond(float d, float& e, float& de) {
     e += kWHBond * (-d * (1.0f / 0.7f));
     de -= kWHBond * (1.0f / 0.7f);
   }
+}
+
+// a (e, de/dd) pair term projected on the unit vector u, added to (E, G)
+__device__ __forceinline__ void add_term(float4& acc, float e, float de, float ux, float uy, float uz) {
+  acc.x += e;
+  acc.y = fmaf(de, ux, acc.y);
+  acc.z = fmaf(de, uy, acc.z);
+  acc.w = fmaf(de, uz, acc.w);
 }
 
 template <int FMT>
@@ -86,9 +87,11 @@ __global__ void __launch_bounds__(kThreads) grid_build_kernel(int n_rec, const f
   const float hix = ox + h * (float)min(bx0 + kBX - 1, nx - 1), hiy = oy + h * (float)min(by0 + kBY - 1, ny - 1),
               hiz = oz + h * (float)min(bz0 + kBZ - 1, nz - 1);
   const float reach2 = (kCutoff + 0.01f) * (kCutoff + 0.01f);
-  float E[8], GX[8], GY[8], GZ[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) E[t] = GX[t] = GY[t] = GZ[t] = 0.f;
+  // gauss / repulsion sums per radius, packed (1.9, 1.8) and (1.7, 2.0): energy and gradient
+  float2 Ea = make_float2(0.f, 0.f), Eb = Ea, Xa = Ea, Xb = Ea, Ya = Ea, Yb = Ea, Za = Ea, Zb = Ea;
+  // hydrophobic term of C_H; H-bond terms of N_D (with receptor acceptors), N_A
+  // and O_A (with receptor donors), O_DA (with donors or acceptors): (e, gx, gy, gz)
+  float4 Hch = make_float4(0.f, 0.f, 0.f, 0.f), Hnd = Hch, Hna = Hch, Hoa = Hch, Hoda = Hch;
   int base = 0;
   while (base < n_rec) {
     int count = 0;
@@ -127,38 +130,48 @@ __global__ void __launch_bounds__(kThreads) grid_build_kernel(int n_rec, const f
         const float dx = mx - a.x, dy = my - a.y, dz = mz - a.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < kCutoff * kCutoff)) continue;
-        const float r = sqrtf(r2);
-        const float inv_r = r > 0.f ? 1.f / r : 0.f;
+        // a vertex on an atom (r = 0) takes no gradient from it: ir is finite there and d* = 0
+        const float ir = rsqrtf(fmaxf(r2, 1e-30f));
+        const float r = r2 * ir;
         const int tj = min(__float_as_int(a.w), 8);
         const float Rj = c_xs_radius[tj];
-        const int bj = c_xs_bits[tj];
-        float e19, d19, e18, d18, e17, d17, e20, d20;
-        const float s19 = r - (1.9f + Rj), s18 = r - (1.8f + Rj), s17 = r - (1.7f + Rj), s20 = r - (2.0f + Rj);
-        steric(s19, e19, d19);
-        steric(s18, e18, d18);
-        steric(s17, e17, d17);
-        steric(s20, e20, d20);
-        float te[8], td[8];
-        te[0] = e19, td[0] = d19;  // C_H
-        if (bj & 1) hydrophobic(s19, te[0], td[0]);
-        te[1] = e19, td[1] = d19;  // C_P
-        te[2] = e18, td[2] = d18;  // N_P
-        te[3] = e18, td[3] = d18;  // N_D: H-bond with an acceptor
-        if (bj & 4) hbond(s18, te[3], td[3]);
-        te[4] = e18, td[4] = d18;  // N_A: H-bond with a donor
-        if (bj & 2) hbond(s18, te[4], td[4]);
-        te[5] = e17, td[5] = d17;  // O_A
-        if (bj & 2) hbond(s17, te[5], td[5]);
-        te[6] = e17, td[6] = d17;  // O_DA
-        if (bj & 6) hbond(s17, te[6], td[6]);
-        te[7] = e20, td[7] = d20;  // S_P
-        const float ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          E[t] += te[t];
-          GX[t] += td[t] * ux;
-          GY[t] += td[t] * uy;
-          GZ[t] += td[t] * uz;
+        const int bj = c_xs_bits[tj];  // the same for every thread: the branches below do not diverge on it
+        const float2 sa = make_float2(r - (1.9f + Rj), r - (1.8f + Rj));
+        const float2 sb = make_float2(r - (1.7f + Rj), r - (2.0f + Rj));
+        float2 ea, da, eb, db;
+        steric_x2(sa, ea, da);
+        steric_x2(sb, eb, db);
+        const float ux = dx * ir, uy = dy * ir, uz = dz * ir;
+        Ea = __fadd2_rn(Ea, ea);
+        Eb = __fadd2_rn(Eb, eb);
+        Xa = __ffma2_rn(da, splat2(ux), Xa);
+        Xb = __ffma2_rn(db, splat2(ux), Xb);
+        Ya = __ffma2_rn(da, splat2(uy), Ya);
+        Yb = __ffma2_rn(db, splat2(uy), Yb);
+        Za = __ffma2_rn(da, splat2(uz), Za);
+        Zb = __ffma2_rn(db, splat2(uz), Zb);
+        if ((bj & 1) && sa.x < 1.5f) {  // hydrophobic receptor atom: C_H (radius 1.9)
+          float e = 0.f, de = 0.f;
+          hydrophobic(sa.x, e, de);
+          add_term(Hch, e, de, ux, uy, uz);
+        }
+        if ((bj & 6) && sa.y < 0.f) {  // donor and/or acceptor within H-bond range (d of radius 1.8 < 0)
+          if (bj & 4) {  // receptor acceptor: N_D (1.8)
+            float e = 0.f, de = 0.f;
+            hbond(sa.y, e, de);
+            add_term(Hnd, e, de, ux, uy, uz);
+          }
+          if (bj & 2) {  // receptor donor: N_A (1.8), O_A (1.7)
+            float e = 0.f, de = 0.f;
+            hbond(sa.y, e, de);
+            add_term(Hna, e, de, ux, uy, uz);
+            e = de = 0.f;
+            hbond(sb.x, e, de);
+            add_term(Hoa, e, de, ux, uy, uz);
+          }
+          float e = 0.f, de = 0.f;  // O_DA (1.7) with either
+          hbond(sb.x, e, de);
+          add_term(Hoda, e, de, ux, uy, uz);
         }
       }
     }
@@ -167,8 +180,14 @@ __global__ void __launch_bounds__(kThreads) grid_build_kernel(int n_rec, const f
   if (!active) return;
   const size_t nxyz = (size_t)nx * ny * nz;
   const size_t v = ((size_t)iz * ny + iy) * nx + ix;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) store_node<FMT>(maps, (size_t)t * nxyz + v, E[t], GX[t], GY[t], GZ[t]);
+  store_node<FMT>(maps, 0 * nxyz + v, Ea.x + Hch.x, Xa.x + Hch.y, Ya.x + Hch.z, Za.x + Hch.w);     // C_H
+  store_node<FMT>(maps, 1 * nxyz + v, Ea.x, Xa.x, Ya.x, Za.x);                                     // C_P
+  store_node<FMT>(maps, 2 * nxyz + v, Ea.y, Xa.y, Ya.y, Za.y);                                     // N_P
+  store_node<FMT>(maps, 3 * nxyz + v, Ea.y + Hnd.x, Xa.y + Hnd.y, Ya.y + Hnd.z, Za.y + Hnd.w);     // N_D
+  store_node<FMT>(maps, 4 * nxyz + v, Ea.y + Hna.x, Xa.y + Hna.y, Ya.y + Hna.z, Za.y + Hna.w);     // N_A
+  store_node<FMT>(maps, 5 * nxyz + v, Eb.x + Hoa.x, Xb.x + Hoa.y, Yb.x + Hoa.z, Zb.x + Hoa.w);     // O_A
+  store_node<FMT>(maps, 6 * nxyz + v, Eb.x + Hoda.x, Xb.x + Hoda.y, Yb.x + Hoda.z, Zb.x + Hoda.w); // O_DA
+  store_node<FMT>(maps, 7 * nxyz + v, Eb.y, Xb.y, Yb.y, Zb.y);                                     // S_P
 }
 
 template <int FMT>
