@@ -95,6 +95,7 @@ enum {
 #define DSDP_MAX_TORSIONS 15
 #define DSDP_MAX_CHAINS 8192
 #define DSDP_MAX_TOP_K 64
+#define DSDP_MAX_SITE_POINTS 256
 
 typedef enum { DSDP_MAP_F32 = 0, DSDP_MAP_BF16 = 1, DSDP_MAP_F16 = 2 } dsdp_map_dtype;
 typedef enum { DSDP_GRID_EQ4 = 0, DSDP_GRID_EQ3 = 1 } dsdp_grid_mode;
@@ -138,7 +139,23 @@ typedef struct {
   int32_t top_k;        /* poses returned after FP64 rescoring [9], <= DSDP_MAX_TOP_K */
   double rmsd_dedup;    /* poses closer than this heavy-atom RMSD to a better kept pose are dropped [1.0] */
   int32_t trace;        /* 1: keep per-step chain traces (tests; costs memory) */
-  int32_t reserved[7];
+  /* Adaptive search space (Sec. 2, third modification; Fig. 3): with
+   * n_site_points > 0 each chain's initial position is drawn uniformly from the
+   * box intersected with the union of balls of radius site_radius around the
+   * predicted binding-site points, instead of from the whole box.  The points
+   * come from the caller (the paper's binding-site network is not part of this
+   * library).  Rejection sampling: attempt a draws a uniform point of the box
+   * from the chain's Philox stream (step 0, block 0 for a = 0, block 64 + a
+   * after), accepted when it lies within site_radius of some point; the test
+   * runs in FP32 with a fixed operation order (the same on every device); after
+   * 64 rejected attempts the first site point is the start.  The MC steps are
+   * not restrained beyond the box's wall. */
+  float site_radius;    /* Angstrom [7.0] */
+  int32_t n_site_points; /* 0 = the whole box, else 1 .. DSDP_MAX_SITE_POINTS */
+  int32_t reserved0;
+  const float* site_points; /* [n_site_points][3] Angstrom: host memory in dsdp_dock_submit (copied);
+                               unused by the device-resident API (see dsdp_job_device) */
+  int32_t reserved[2];
 } dsdp_dock_params;
 
 /* Result buffers of a finished job (caller-allocated host memory).  Set
@@ -308,6 +325,7 @@ typedef struct {
   double* d_out_intra;      /* [top_k] */
   double* d_out_conf;       /* [top_k][7 + T] */
   float* d_out_coords;      /* [top_k][n_atoms][3] input atom order */
+  const float* d_site_points; /* device [params.n_site_points][3] when params.n_site_points > 0 */
 } dsdp_job_device;
 
 typedef struct dsdp_plan dsdp_plan;

@@ -279,8 +279,12 @@ class Ligand:
         return c, out[0], int(out[1]), int(out[2])
 
 
-def dock_params_array(n_mc_steps, optimizer, temperature, box_lo, box_size):
-    return np.array([n_mc_steps, optimizer, temperature, *box_lo, *box_size], dtype=np.float64)
+def dock_params_array(n_mc_steps, optimizer, temperature, box_lo, box_size, sites=None, site_radius=7.0):
+    """[n_mc_steps, optimizer, temperature, box_lo, box_size, site_radius, n_sites, sites...]; sites ([n][3],
+    FP32-representable) select the adaptive search space for the initial positions."""
+    pts = np.zeros((0, 3)) if sites is None else np.asarray(sites, dtype=np.float32).astype(np.float64).reshape(-1, 3)
+    return np.array([n_mc_steps, optimizer, temperature, *box_lo, *box_size, float(np.float32(site_radius)),
+                     len(pts), *pts.ravel()], dtype=np.float64)
 
 
 def chain_init(lig: Ligand, dock_params, seed, chain, opt=None):

@@ -852,6 +852,11 @@ struct DockSettings {
   int optimizer = 0;  // 0 BFGS, 1 BB
   double temperature = 1.2;
   double box_lo[3], box_size[3];
+  // adaptive search space: n_sites predicted binding-site points [3 n_sites]
+  // (values representable in FP32) and the ball radius; n_sites = 0: the box
+  int n_sites = 0;
+  const double* sites = nullptr;
+  double site_radius = 7.0;
   OptSettings opt;
 };
 
@@ -867,9 +872,52 @@ OptResult local_opt(DockObjective& obj, double* x, const DockSettings& ds) {
   return ds.optimizer == 0 ? bfgs(obj, x, ds.opt) : barzilai_borwein(obj, x, ds.opt);
 }
 
+// Adaptive search space (Sec. 2, third modification; Fig. 3): the search
+// region is the box intersected with the union of balls of radius R around the
+// predicted binding-site points, and the initial positions are drawn uniformly
+// from it.  Reading: rejection from the box -- attempt a uses the uniforms of
+// block 0 (a = 0) or block 64 + a (a >= 1) of step 0, words 0-2; the candidate
+// is lo + size u and it is accepted when its squared distance to some point is
+// at most R^2; after 64 rejections the first point is taken.  The accept
+// decision is made in FP32 (candidate by one fused multiply-add per axis,
+// distance ((dx dx + dy dy) + dz dz) with every operation rounded), as the GPU
+// makes it, so both take the same branch; the accepted position itself is
+// lo + size u in FP64.  Parity: pinned by the tests (every start inside the
+// region, the box case unchanged when the balls cover the box, uniformity in a
+// ball).
+bool site_accepts_f32(const DockSettings& ds, const double* u) {
+  float c[3];
+  for (int a = 0; a < 3; ++a) c[a] = std::fmaf((float)ds.box_size[a], (float)u[a], (float)ds.box_lo[a]);
+  const float r2 = (float)ds.site_radius * (float)ds.site_radius;
+  for (int k = 0; k < ds.n_sites; ++k) {
+    const float dx = c[0] - (float)ds.sites[3 * k], dy = c[1] - (float)ds.sites[3 * k + 1],
+                dz = c[2] - (float)ds.sites[3 * k + 2];
+    const float d2 = (dx * dx + dy * dy) + dz * dz;
+    if (d2 <= r2) return true;
+  }
+  return false;
+}
+
+void initial_position(const ChainRng& rng, const DockSettings& ds, double* c) {
+  double u[3] = {rng.uniform(0, 0, 0), rng.uniform(0, 0, 1), rng.uniform(0, 0, 2)};
+  if (ds.n_sites > 0) {
+    bool found = false;
+    for (int a = 0; a < 64 && !found; ++a) {
+      if (a > 0)
+        for (int w = 0; w < 3; ++w) u[w] = rng.uniform(0, 64 + a, w);
+      found = site_accepts_f32(ds, u);
+    }
+    if (!found) {
+      for (int a = 0; a < 3; ++a) c[a] = (double)(float)ds.sites[a];
+      return;
+    }
+  }
+  for (int a = 0; a < 3; ++a) c[a] = ds.box_lo[a] + ds.box_size[a] * u[a];
+}
+
 void chain_init(const Ligand& L, const ChainRng& rng, const DockSettings& ds, double* c) {
   auto U = [&](int n) { return rng.uniform(0, n / 4, n % 4); };
-  for (int a = 0; a < 3; ++a) c[a] = ds.box_lo[a] + ds.box_size[a] * U(a);
+  initial_position(rng, ds, c);
   const double u1 = U(3), u2 = U(4), u3 = U(5);
   c[3] = std::sqrt(u1) * std::cos(2 * kPi * u3);
   c[4] = std::sqrt(1 - u1) * std::sin(2 * kPi * u2);
@@ -1156,13 +1204,17 @@ void orc_unit_ball(uint64_t seed, uint32_t chain, uint32_t step, double* out) {
   out[0] = b.x, out[1] = b.y, out[2] = b.z;
 }
 
-// dock_params: [n_mc_steps, optimizer, temperature, box_lo x3, box_size x3]
+// dock_params: [n_mc_steps, optimizer, temperature, box_lo x3, box_size x3,
+//               site_radius, n_sites, sites x 3 n_sites]
 static DockSettings dock_from(const double* dp, const double* op) {
   DockSettings ds;
   ds.n_mc_steps = (int)dp[0];
   ds.optimizer = (int)dp[1];
   ds.temperature = dp[2];
   for (int a = 0; a < 3; ++a) ds.box_lo[a] = dp[3 + a], ds.box_size[a] = dp[6 + a];
+  ds.site_radius = dp[9];
+  ds.n_sites = (int)dp[10];
+  ds.sites = ds.n_sites > 0 ? dp + 11 : nullptr;
   ds.opt = opt_from(op);
   return ds;
 }

@@ -50,7 +50,8 @@ struct Job {
   dsdp_status err = DSDP_OK;
   std::string msg;
   const dsdp_grid* grid = nullptr;
-  std::vector<uint8_t> blob;
+  std::vector<uint8_t> blob;  // packed ligand, then (16-byte aligned) the site points, uploaded together
+  size_t sites_off = 0;       // offset of the site points in blob (n_site_points > 0)
   dsdp_dock_params params{};
   int n_atoms = 0, T = 0;
   // device memory: [blob | results]; results copied back with one D2H
@@ -290,6 +291,7 @@ bool job_prepare(dsdp_ctx* ctx, Job* j, int stream) {
   jd.h_blob = j->blob.data();
   jd.d_blob = dm;
   jd.params = j->params;
+  if (j->params.n_site_points > 0) jd.d_site_points = (const float*)(dm + j->sites_off);
   jd.d_chain_best_conf = (float*)(res + j->o_cbc);
   jd.d_chain_best_e = (float*)(res + j->o_cbe);
   jd.d_chain_evals = (uint32_t*)(res + j->o_evals);
@@ -858,6 +860,22 @@ extern "C" dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, co
   }
   int32_t P, B;
   dsdp_ligand_blob_info(j->blob.data(), &j->n_atoms, &j->T, &P, &B);
+  if (j->params.n_site_points > 0) {
+    // the caller's points are borrowed for this call: keep a copy behind the blob
+    if (!params->site_points) {
+      delete j;
+      return set_error(DSDP_ERR_INVALID_ARG, "n_site_points > 0 but site_points is NULL");
+    }
+    for (int i = 0; i < 3 * j->params.n_site_points; ++i)
+      if (!isfinite(params->site_points[i])) {
+        delete j;
+        return set_error(DSDP_ERR_INVALID_ARG, "site point coordinate %d not finite", i);
+      }
+    j->sites_off = (j->blob.size() + 15) & ~(size_t)15;
+    j->blob.resize(j->sites_off + sizeof(float) * 3 * j->params.n_site_points);
+    memcpy(j->blob.data() + j->sites_off, params->site_points, sizeof(float) * 3 * j->params.n_site_points);
+  }
+  j->params.site_points = nullptr;
   j->grid = grid;
   layout_results(j);
   const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);

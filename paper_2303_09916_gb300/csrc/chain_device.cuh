@@ -200,11 +200,9 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
         const float2 dz = __ffma2_rn(make_float2(b0.z, b1.z), splat2(-1.f), pz);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const uint32_t both = t0.x | t1.x;  // bits 14 / 15: warp-uniform
-        const float2 wh = make_float2((t0.x & (1u << 12)) ? kWHydrophobic : 0.f, (t1.x & (1u << 12)) ? kWHydrophobic : 0.f);
-        const float2 wb = make_float2((t0.x & (1u << 13)) ? kWHBond : 0.f, (t1.x & (1u << 13)) ? kWHBond : 0.f);
         float2 e, sp;
-        vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), wh, wb, (both >> 14) & 1,
-                     (both >> 15) & 1, e, sp);
+        vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), t0.x >> 12, t1.x >> 12,
+                     (both >> 14) & 1, (both >> 15) & 1, e, sp);
         e_pair = __fadd2_rn(e_pair, e);
         const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
         // reaction forces of the pairs this lane is passive in (source lane: bits 5-9)
@@ -231,11 +229,9 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
         const float2 dz = make_float2(a0.z - b0.z, a1.z - b1.z);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const uint32_t both = t0.x | t1.x;
-        const float2 wh = make_float2((t0.x & (1u << 12)) ? kWHydrophobic : 0.f, (t1.x & (1u << 12)) ? kWHydrophobic : 0.f);
-        const float2 wb = make_float2((t0.x & (1u << 13)) ? kWHBond : 0.f, (t1.x & (1u << 13)) ? kWHBond : 0.f);
         float2 e, sp;
-        vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), wh, wb, (both >> 14) & 1,
-                     (both >> 15) & 1, e, sp);
+        vina_pair_x2(r2, make_float2(__uint_as_float(t0.y), __uint_as_float(t1.y)), t0.x >> 12, t1.x >> 12,
+                     (both >> 14) & 1, (both >> 15) & 1, e, sp);
         e_pair = __fadd2_rn(e_pair, e);
         const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
         const float3 c0 = shfl3(make_float3(fx.x, fy.x, fz.x), (int)(t0.x >> 5));
@@ -475,6 +471,37 @@ __device__ __forceinline__ Conf load_conf(const float* in, int T) {
   return c;
 }
 
+// Adaptive search space (Sec. 2, third modification; Fig. 3): a start position
+// uniform in the box intersected with the union of balls of radius R around the
+// predicted binding-site points, by rejection.  Attempt 0 is the box draw p0
+// (block 0 of step 0), attempt a >= 1 takes words 0-2 of block 64 + a; a
+// candidate is accepted when some point lies within R of it.  The candidate
+// (one fused multiply-add per axis) and the squared distances ((dx dx + dy dy)
+// + dz dz, no contraction) are FP32 with a fixed operation order, so every
+// device and the oracle take the same decisions; the lanes share the points.
+// After 64 rejected attempts the start is the first point.
+__device__ __forceinline__ float3 site_start(const DevJob& J, const ChainStream& rs, float3 p0) {
+  const int lane = threadIdx.x & 31;
+  for (int a = 0; a < 64; ++a) {
+    float3 c = p0;
+    if (a > 0) {
+      const uint4 b = rs.block(0, 64u + (uint32_t)a);
+      c = make_float3(__fmaf_rn(J.box_size[0], ChainStream::to_uniform(b.x), J.box_lo[0]),
+                      __fmaf_rn(J.box_size[1], ChainStream::to_uniform(b.y), J.box_lo[1]),
+                      __fmaf_rn(J.box_size[2], ChainStream::to_uniform(b.z), J.box_lo[2]));
+    }
+    bool inside = false;
+    for (int k = lane; k < J.n_sites; k += 32) {
+      const float dx = __fsub_rn(c.x, __ldg(J.sites + 3 * k)), dy = __fsub_rn(c.y, __ldg(J.sites + 3 * k + 1)),
+                  dz = __fsub_rn(c.z, __ldg(J.sites + 3 * k + 2));
+      const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      inside |= d2 <= J.site_r2;
+    }
+    if (__any_sync(kFull, inside)) return c;
+  }
+  return make_float3(__ldg(J.sites), __ldg(J.sites + 1), __ldg(J.sites + 2));
+}
+
 // One Monte Carlo chain (Sec. 2: one of many short independent copies; Vina's
 // mutation and Metropolis rules) with its local optimisations -- BFGS with
 // Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1) or
@@ -501,9 +528,10 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
   Conf xt;
   {
     const uint4 b0 = rs.block(0, 0), b1 = rs.block(0, 1);
-    xt.p = make_float3(J.box_lo[0] + J.box_size[0] * ChainStream::to_uniform(b0.x),
-                       J.box_lo[1] + J.box_size[1] * ChainStream::to_uniform(b0.y),
-                       J.box_lo[2] + J.box_size[2] * ChainStream::to_uniform(b0.z));
+    xt.p = make_float3(__fmaf_rn(J.box_size[0], ChainStream::to_uniform(b0.x), J.box_lo[0]),
+                       __fmaf_rn(J.box_size[1], ChainStream::to_uniform(b0.y), J.box_lo[1]),
+                       __fmaf_rn(J.box_size[2], ChainStream::to_uniform(b0.z), J.box_lo[2]));
+    if (J.n_sites > 0) xt.p = site_start(J, rs, xt.p);
     const float u1 = ChainStream::to_uniform(b0.w), u2 = ChainStream::to_uniform(b1.x),
                 u3 = ChainStream::to_uniform(b1.y);
     float s2, c2, s3, c3;

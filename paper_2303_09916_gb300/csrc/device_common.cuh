@@ -214,11 +214,10 @@ __device__ __forceinline__ void steric_x2(float2 d, float2& e, float2& de) {
 // taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in vina_pair.
 // Pairs at or beyond the cutoff take d = kFarD, and idle slots get a surface
 // distance at least kStepIdleNrs: there every term and slope is exactly zero.
-// wh / wb: weight of the hydrophobic / H-bond term of each pair (0 where the
-// pair does not carry it); use_hyd / use_hb: warp-uniform, false when no pair of
-// the two steps carries the term.
-__device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, float2 wb, bool use_hyd, bool use_hb,
-                                             float2& e, float2& s) {
+// cls0 / cls1: terms the two pairs carry (1 hydrophobic, 2 H-bond); use_hyd /
+// use_hb: warp-uniform, false when no pair of the two steps carries the term.
+__device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, uint32_t cls0, uint32_t cls1, bool use_hyd,
+                                             bool use_hb, float2& e, float2& s) {
   // 1e-30 keeps an idle slot's r2 = 0 finite (r2 ir = 0 there); real pairs are
   // Angstroms apart, where it changes nothing
   const float2 rp = __fadd2_rn(r2, splat2(1e-30f));
@@ -229,12 +228,14 @@ __device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, float2 wh, f
   float2 ee, de;
   steric_x2(d, ee, de);
   if (use_hyd) {  // min(max(1.5 - d, 0), 1), slope on [0.5, 1.5)
+    const float2 wh = make_float2((cls0 & 1u) ? kWHydrophobic : 0.f, (cls1 & 1u) ? kWHydrophobic : 0.f);
     const float2 t = __ffma2_rn(d, splat2(-1.f), splat2(1.5f));
     ee = __ffma2_rn(wh, make_float2(__saturatef(t.x), __saturatef(t.y)), ee);
     if (d.x >= 0.5f && d.x < 1.5f) de.x -= wh.x;
     if (d.y >= 0.5f && d.y < 1.5f) de.y -= wh.y;
   }
   if (use_hb) {  // min(max(-d / 0.7, 0), 1), slope on [-0.7, 0)
+    const float2 wb = make_float2((cls0 & 2u) ? kWHBond : 0.f, (cls1 & 2u) ? kWHBond : 0.f);
     const float2 t = __fmul2_rn(d, splat2(-1.f / 0.7f));
     ee = __ffma2_rn(wb, make_float2(__saturatef(t.x), __saturatef(t.y)), ee);
     if (d.x >= -0.7f && d.x < 0.f) de.x -= wb.x * (1.f / 0.7f);

@@ -91,6 +91,9 @@ struct DevJob {
   uint32_t seed_lo, seed_hi;
   float box_lo[3];
   float box_size[3];
+  const float* sites;  // adaptive search space: [n_sites][3] predicted binding-site points
+  int32_t n_sites;     // 0: initial positions uniform in the box
+  float site_r2;       // site radius squared (FP32)
   float* chain_best_conf;
   float* chain_best_e;
   uint32_t* chain_evals;

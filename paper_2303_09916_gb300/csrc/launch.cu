@@ -43,6 +43,7 @@ dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) 
   if (out->temperature == 0.0) out->temperature = 1.2;
   if (out->top_k == 0) out->top_k = 9;
   if (out->rmsd_dedup == 0.0) out->rmsd_dedup = 1.0;
+  if (out->site_radius == 0.f) out->site_radius = 7.0f;
   if (out->n_chains < 1 || out->n_chains > DSDP_MAX_CHAINS)
     return set_error(DSDP_ERR_INVALID_ARG, "n_chains %d outside 1..%d", out->n_chains, DSDP_MAX_CHAINS);
   if (out->n_mc_steps < 0 || out->n_mc_steps > 100000) return set_error(DSDP_ERR_INVALID_ARG, "n_mc_steps out of range");
@@ -54,6 +55,11 @@ dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) 
   if (out->top_k < 1 || out->top_k > DSDP_MAX_TOP_K)
     return set_error(DSDP_ERR_INVALID_ARG, "top_k %d outside 1..%d", out->top_k, DSDP_MAX_TOP_K);
   if (!(out->rmsd_dedup >= 0.0)) return set_error(DSDP_ERR_INVALID_ARG, "rmsd_dedup must be >= 0");
+  if (out->n_site_points < 0 || out->n_site_points > DSDP_MAX_SITE_POINTS)
+    return set_error(DSDP_ERR_INVALID_ARG, "n_site_points %d outside 0..%d", out->n_site_points,
+                     DSDP_MAX_SITE_POINTS);
+  if (!(out->site_radius > 0.f) || !isfinite(out->site_radius))
+    return set_error(DSDP_ERR_INVALID_ARG, "site_radius must be positive");
   return DSDP_OK;
 }
 
@@ -188,6 +194,8 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
       if (!(J.box_size[a] >= 0.0) || !isfinite(J.box_lo[a]))
         return set_error(DSDP_ERR_INVALID_ARG, "job %d: search box invalid", j);
     if (p.trace && !J.d_trace) return set_error(DSDP_ERR_INVALID_ARG, "job %d: trace requested without d_trace", j);
+    if (p.n_site_points > 0 && !J.d_site_points)
+      return set_error(DSDP_ERR_INVALID_ARG, "job %d: n_site_points > 0 without d_site_points", j);
     fmt[j] = map_fmt(J.grid.dtype, J.grid.mode);
     apl[j] = atoms[j] <= 32 ? 1 : 2;
     blob_bytes[j] = (int)((const BlobHeader*)J.h_blob)->stage_bytes;
@@ -223,6 +231,9 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
     d.chain_best_e = J.d_chain_best_e;
     d.chain_evals = J.d_chain_evals;
     d.trace = p.trace ? J.d_trace : nullptr;
+    d.sites = p.n_site_points > 0 ? J.d_site_points : nullptr;
+    d.n_sites = p.n_site_points;
+    d.site_r2 = p.site_radius * p.site_radius;
     d.n_rec = J.receptor.n;
     d.rec_xyz = J.receptor.xyz;
     d.rec_type = J.receptor.xs_type;

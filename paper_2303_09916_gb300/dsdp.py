@@ -59,7 +59,9 @@ class dsdp_ligand(C.Structure):
 class dsdp_dock_params(C.Structure):
     _fields_ = [("n_chains", C.c_int32), ("n_mc_steps", C.c_int32), ("n_opt_iters", C.c_int32),
                 ("optimizer", C.c_int32), ("temperature", C.c_double), ("seed", C.c_uint64), ("top_k", C.c_int32),
-                ("rmsd_dedup", C.c_double), ("trace", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("rmsd_dedup", C.c_double), ("trace", C.c_int32), ("site_radius", C.c_float),
+                ("n_site_points", C.c_int32), ("reserved0", C.c_int32), ("site_points", C.c_void_p),
+                ("reserved", C.c_int32 * 2)]
 
 
 class dsdp_dock_result(C.Structure):
@@ -96,7 +98,8 @@ class dsdp_job_device(C.Structure):
                 ("box_size", C.c_double * 3), ("d_chain_best_conf", C.c_void_p), ("d_chain_best_e", C.c_void_p),
                 ("d_chain_evals", C.c_void_p), ("d_trace", C.c_void_p), ("d_out_n", C.c_void_p),
                 ("d_out_chain", C.c_void_p), ("d_out_score", C.c_void_p), ("d_out_inter", C.c_void_p),
-                ("d_out_intra", C.c_void_p), ("d_out_conf", C.c_void_p), ("d_out_coords", C.c_void_p)]
+                ("d_out_intra", C.c_void_p), ("d_out_conf", C.c_void_p), ("d_out_coords", C.c_void_p),
+                ("d_site_points", C.c_void_p)]
 
 
 P = C.POINTER
@@ -205,9 +208,16 @@ def make_ligand(lig):
 
 
 def make_params(n_chains=0, n_mc_steps=0, n_opt_iters=0, optimizer=DSDP_OPT_BFGS, temperature=0.0, seed=0,
-                top_k=0, rmsd_dedup=0.0, trace=0) -> dsdp_dock_params:
-    return dsdp_dock_params(int(n_chains), int(n_mc_steps), int(n_opt_iters), int(optimizer), float(temperature),
-                            int(seed), int(top_k), float(rmsd_dedup), int(trace))
+                top_k=0, rmsd_dedup=0.0, trace=0, site_points=None, site_radius=0.0) -> dsdp_dock_params:
+    """Dock parameters; site_points ([n][3] float32, host) selects the adaptive search space."""
+    p = dsdp_dock_params(int(n_chains), int(n_mc_steps), int(n_opt_iters), int(optimizer), float(temperature),
+                         int(seed), int(top_k), float(rmsd_dedup), int(trace), float(site_radius))
+    if site_points is not None and len(site_points):
+        pts = np.ascontiguousarray(site_points, dtype=np.float32).reshape(-1, 3)
+        p.n_site_points = len(pts)
+        p.site_points = pts.ctypes.data
+        p._keep_sites = pts  # alive as long as the params
+    return p
 
 
 # ------------------------------------------------------------------ context / grids

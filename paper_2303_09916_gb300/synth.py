@@ -238,6 +238,14 @@ def ligand(n_atoms: int, n_torsions: int, seed: int = 0, center=None) -> Ligand:
     return Ligand(xyz.astype(np.float32), types, bonds, rot, int(T))
 
 
+def site_points(rec: Receptor, n_points: int = 100, seed: int = 0, spread: float = POCKET_RADIUS) -> np.ndarray:
+    """Stand-in for the binding-site network's output (its top-scored voxel
+    centres): n_points uniform in a ball of radius `spread` around the
+    receptor's pocket centre, float32 [n_points][3]."""
+    rng = _rng(seed, "SITE")
+    return (rec.pocket_center + _ball(rng, n_points, spread)).astype(np.float32)
+
+
 def box_around(center, size, spacing=0.375) -> Box:
     s = np.array(size if np.ndim(size) else [size] * 3, dtype=np.float64)
     return Box(np.asarray(center, dtype=np.float64), s, float(spacing))

@@ -331,6 +331,64 @@ def test_replay_one_step_transitions(ctx, chain_complex):
     assert n_match >= n_base - 0.1 * n_steps
 
 
+def test_adaptive_search_space_starts_match_the_oracle(ctx, chain_complex):
+    """Adaptive search space (Sec. 2, third modification): with binding-site
+    points the chains start in the box intersected with the union of 7 A balls.
+    The first line search of every chain (one BFGS iteration) ends where the
+    oracle's does from its own start -- so the GPU drew the same starts (the
+    inside / outside decisions are FP32 on both sides).  The device-resident
+    plan with d_site_points gives bitwise the handle API's chains."""
+    cx = chain_complex
+    og = cx.oracle_grid()
+    sites = synth.site_points(cx.rec, 60, seed=4, spread=4.0)
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
+                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    nc, nx = 32, 7 + cx.T
+    dp = oracle.dock_params_array(1, 0, 1.2, cx.box_lo(), cx.size, sites, 7.0)
+    starts = np.array([oracle.chain_init(cx.olig, dp, 7, c) for c in range(nc)])
+    d = np.linalg.norm(starts[:, None, :3] - sites[None].astype(np.float64), axis=2).min(1)
+    assert np.all(d <= 7.0 + 1e-5)
+    box_starts = np.array([oracle.chain_init(cx.olig, oracle.dock_params_array(1, 0, 1.2, cx.box_lo(), cx.size), 7, c)
+                           for c in range(nc)])
+    assert not np.array_equal(starts[:, :3], box_starts[:, :3])  # the region does restrict these starts
+    try:
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=2, n_opt_iters=1, seed=7, trace=1, top_k=1,
+                       site_points=sites)
+        for c in range(nc):
+            _, e_ref, _, _ = cx.olig.local_opt(og, 0, 0, starts[c], opt=dict(max_iters=1))
+            pose = res["trace"][c, 0, :nx].astype(np.float64)
+            tol = E_REL * max(cx.abs_terms(og, 0, pose), 1.0)
+            assert abs(float(res["trace"][c, 0, nx + 1]) - e_ref) <= tol, c
+        # the same jobs through the device-resident plan
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.current_stream().cuda_stream
+        info = dsdp.dsdp_grid_info(grid)
+        maps = torch.from_numpy(og.maps.astype(np.float32).ravel().copy()).to(dev)
+        blob = dsdp.dsdp_ligand_pack(cx.lig)
+        dblob = torch.from_numpy(blob.copy()).to(dev)
+        dsites = torch.from_numpy(sites.copy()).to(dev)
+        conf = torch.zeros((nc, nx), dtype=torch.float32, device=dev)
+        e = torch.zeros(nc, dtype=torch.float32, device=dev)
+        j = dsdp.dsdp_job_device()
+        j.grid = dsdp.grid_view(maps.data_ptr(), info["n"], info["origin"], cx.spacing, dsdp.DSDP_MAP_F32)
+        j.h_blob, j.d_blob = blob.ctypes.data, dblob.data_ptr()
+        j.params = dsdp.make_params(n_chains=nc, n_mc_steps=2, n_opt_iters=1, seed=7, top_k=1, site_points=sites)
+        j.d_site_points = dsites.data_ptr()
+        for a in range(3):
+            j.box_lo[a], j.box_size[a] = cx.box_lo()[a], cx.size[a]
+        j.d_chain_best_conf, j.d_chain_best_e = conf.data_ptr(), e.data_ptr()
+        plan = dsdp.dsdp_plan_create(None, [j], dsdp.DSDP_PLAN_NO_RESCORE, 1)
+        try:
+            dsdp.dsdp_plan_launch(plan, stream)
+            torch.cuda.synchronize()
+        finally:
+            dsdp.dsdp_plan_destroy(None, plan)
+        assert np.array_equal(e.cpu().numpy(), res["chain_best_e"])
+        assert np.array_equal(conf.cpu().numpy(), res["chain_best_conf"])
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+
+
 def test_rescore_topk_matches_oracle(ctx):
     cx = Complex(2000, 16.0, 20, 4, seed=9)
     grid = dsdp.dsdp_grid_build(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx))
