@@ -319,12 +319,14 @@ def run_device(args, rank, world, dev, dist):
 
 # ---------------------------------------------------------------- other forms of the same work
 def make_device_job(dsdp, torch, dev, rec, lig, seed, box_size, spacing, dtype, n_chains, n_steps, n_iters, top_k,
-                    grid=None):
-    """Device buffers and a dsdp_job_device for one docking job (caller-owned memory)."""
+                    grid=None, sites=None, mode=0):
+    """Device buffers and a dsdp_job_device for one docking job (caller-owned memory);
+    sites: binding-site points of the adaptive search space (None: the whole box);
+    mode: DSDP_GRID_EQ4 (score + gradient maps) or DSDP_GRID_EQ3 (score maps)."""
     box = dsdp.make_box(rec.pocket_center, box_size, spacing)
     if grid is None:
-        nbytes = dsdp.dsdp_grid_map_bytes(box, dtype, dsdp.DSDP_GRID_EQ4)
-        grid = dict(box=box, maps=torch.empty(nbytes, dtype=torch.uint8, device=dev),
+        nbytes = dsdp.dsdp_grid_map_bytes(box, dtype, mode)
+        grid = dict(box=box, mode=mode, maps=torch.empty(nbytes, dtype=torch.uint8, device=dev),
                     xyz=torch.from_numpy(rec.xyz.copy()).to(dev), type=torch.from_numpy(rec.xs_type.copy()).to(dev))
     blob = dsdp.dsdp_ligand_pack(lig)
     info = dsdp.dsdp_ligand_blob_info(blob)
@@ -340,11 +342,15 @@ def make_device_job(dsdp, torch, dev, rec, lig, seed, box_size, spacing, dtype, 
     j = dsdp.dsdp_job_device()
     j.grid = dsdp.grid_view(grid["maps"].data_ptr(), n,
                             [rec.pocket_center[a] - (n[a] - 1) * spacing / 2 for a in range(3)], spacing, dtype,
-                            dsdp.DSDP_GRID_EQ4)
+                            grid.get("mode", 0))
     j.receptor = dsdp.dsdp_receptor(len(rec.xs_type), grid["xyz"].data_ptr(), grid["type"].data_ptr())
     j.h_blob = blob.ctypes.data
     j.d_blob = keep["d_blob"].data_ptr()
-    j.params = dsdp.make_params(n_chains=n_chains, n_mc_steps=n_steps, n_opt_iters=n_iters, seed=seed, top_k=top_k)
+    j.params = dsdp.make_params(n_chains=n_chains, n_mc_steps=n_steps, n_opt_iters=n_iters, seed=seed, top_k=top_k,
+                                site_points=sites)
+    if sites is not None:
+        keep["sites"] = torch.from_numpy(np.ascontiguousarray(sites, dtype=np.float32)).to(dev)
+        j.d_site_points = keep["sites"].data_ptr()
     for a in range(3):
         j.box_lo[a] = rec.pocket_center[a] - box_size / 2
         j.box_size[a] = box_size
@@ -356,7 +362,7 @@ def make_device_job(dsdp, torch, dev, rec, lig, seed, box_size, spacing, dtype, 
 
 def build_grid(dsdp, grid, dtype, sptr):
     dsdp.dsdp_grid_build_device(len(grid["type"]), grid["xyz"].data_ptr(), grid["type"].data_ptr(), grid["box"],
-                                dtype, dsdp.DSDP_GRID_EQ4, grid["maps"].data_ptr(), grid["maps"].numel(), sptr)
+                                dtype, grid.get("mode", 0), grid["maps"].data_ptr(), grid["maps"].numel(), sptr)
 
 
 def run_one_job_per_launch(args, rank, dev, steps):
@@ -396,6 +402,52 @@ def run_one_job_per_launch(args, rank, dev, steps):
         dsdp.dsdp_plan_destroy(None, plan)
     return dict(systems_per_s=steps * len(items) / (t0.elapsed_time(t1) * 1e-3),
                 latency_p50_ms=float(np.percentile(ms, 50)), latency_p99_ms=float(np.percentile(ms, 99)))
+
+
+def run_variants(args, rank, dev, steps=2):
+    """The typical-4k batch docked in variants of the method, each reporting the
+    systems/s of the chain + rescoring stages and the mean top-1 FP64 score
+    (lower is better):
+      search_region: initial positions from the whole 30 A box (cube) or from
+        the box intersected with 7 A balls around 100 synthetic binding-site
+        points in the pocket (shape; Sec. 2 third modification);
+      grid_mode: score + gradient maps interpolated (Eq. 4, 128 B gathered per
+        atom) or score maps only with the gradient of the interpolant (Eq. 3,
+        32 B per atom)."""
+    import torch
+    from paper_2303_09916_gb300 import dsdp, synth
+
+    sptr = torch.cuda.current_stream().cuda_stream
+    dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
+    variants = [("search_region", "cube", False, dsdp.DSDP_GRID_EQ4), ("search_region", "shape", True, dsdp.DSDP_GRID_EQ4),
+                ("grid_mode", "eq4", False, dsdp.DSDP_GRID_EQ4), ("grid_mode", "eq3", False, dsdp.DSDP_GRID_EQ3)]
+    out = {"search_region": {"site_points": "100 per system, uniform within 6 A of the pocket centre; 7 A balls"},
+           "grid_mode": {}}
+    for group, name, use_sites, mode in variants:
+        jobs, keeps = [], []
+        for seed, rec, lig in systems(rank, args.batch):
+            sites = synth.site_points(rec, 100, seed) if use_sites else None
+            j, keep = make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dtype, N_CHAINS, N_STEPS,
+                                      N_ITERS, TOP_K, sites=sites, mode=mode)
+            build_grid(dsdp, keep["grid"], dtype, sptr)
+            jobs.append(j)
+            keeps.append(keep)
+        plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
+        dsdp.dsdp_plan_launch(plan, sptr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(steps):
+            dsdp.dsdp_plan_launch(plan, sptr)
+        b.record()
+        torch.cuda.synchronize()
+        dsdp.dsdp_plan_destroy(None, plan)
+        top1 = [float(k["score"][0].item()) for k in keeps]
+        evals = sum(int(k["evals"].sum().item()) for k in keeps)
+        sec = a.elapsed_time(b) * 1e-3 / steps
+        out[group][name] = dict(systems_per_s=len(jobs) / sec, evals_per_s=evals / sec,
+                                evals_per_system=evals / len(jobs), mean_top1_score=float(np.mean(top1)))
+    return out
 
 
 def run_uneven_graph(args, dev, steps=3):
@@ -660,6 +712,7 @@ def main():
     e2e = run_e2e(args, rank, local) if args.e2e_steps > 0 else None
     single = run_one_job_per_launch(args, rank, local, 2) if args.forms else None
     uneven = run_uneven_graph(args, local) if args.forms and rank == 0 else None
+    variants = run_variants(args, rank, local) if args.forms and rank == 0 else None
     if dist:
         t = torch.tensor([e2e["value"] if e2e else 0.0], dtype=torch.float64, device=local)
         dist.all_reduce(t)
@@ -712,6 +765,8 @@ def main():
                                              "latency_p99_ms": e2e["p99_ms"] if e2e else None}}
     if uneven:
         line["uneven_5k_batch"] = uneven
+    if variants:
+        line.update(variants)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
