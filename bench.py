@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--serve-streams", type=int, default=8, help="batches in flight (one per stream)")
     p.add_argument("--no-forms", dest="forms", action="store_false",
                    help="skip the one-job-per-launch and uneven-batch (CUDA graph) measurements")
+    p.add_argument("--sweep", action="store_true",
+                   help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
     p.add_argument("--tile-config", type=int, default=-1,
                    help="chain kernel launch configuration: -1 autotune (default), 1/2 fixed register budget")
     return p.parse_args()
@@ -494,6 +496,60 @@ def run_uneven_graph(args, dev, steps=3):
                 results_ok=ok)
 
 
+# ---------------------------------------------------------------- copies x steps sweep
+SWEEP = [(128, 20), (384, 40), (512, 40), (512, 200), (1024, 200), (2048, 200)]
+
+
+def run_sweep(args, dev=0):
+    """Typical-4k systems docked with the copies x MC-steps combinations of the
+    paper's Table 1 (128 x 20 ... 2048 x 200): one system per launch (grid build,
+    chains, rescoring: its latency) and `--batch` systems per launch (throughput)."""
+    import torch
+    from paper_2303_09916_gb300 import dsdp
+
+    torch.cuda.set_device(dev)
+    sptr = torch.cuda.current_stream().cuda_stream
+    sysl = systems(0, args.batch)
+    rows = []
+    for chains, steps in SWEEP:
+        items = [make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dsdp.DSDP_MAP_F32, chains, steps,
+                                 N_ITERS, TOP_K) for seed, rec, lig in sysl]
+        for _, keep in items:
+            build_grid(dsdp, keep["grid"], dsdp.DSDP_MAP_F32, sptr)
+        # one system per launch: grid build + chains + rescoring, CUDA events
+        j0, k0 = items[0]
+        plan = dsdp.dsdp_plan_create(None, [j0], 0, 0)
+        lat = []
+        for r in range(3):
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            build_grid(dsdp, k0["grid"], dsdp.DSDP_MAP_F32, sptr)
+            dsdp.dsdp_plan_launch(plan, sptr)
+            b.record()
+            torch.cuda.synchronize()
+            if r:
+                lat.append(a.elapsed_time(b))
+        dsdp.dsdp_plan_destroy(None, plan)
+        # the batch in one launch
+        plan = dsdp.dsdp_plan_create(None, [j for j, _ in items], 0, 0)
+        dsdp.dsdp_plan_launch(plan, sptr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _, keep in items:
+            build_grid(dsdp, keep["grid"], dsdp.DSDP_MAP_F32, sptr)
+        dsdp.dsdp_plan_launch(plan, sptr)
+        b.record()
+        torch.cuda.synchronize()
+        dsdp.dsdp_plan_destroy(None, plan)
+        evals = sum(int(k["evals"].sum().item()) for _, k in items)
+        rows.append(dict(copies=chains, steps=steps, one_system_ms=float(np.mean(lat)),
+                         batch_systems_per_s=len(items) / (a.elapsed_time(b) * 1e-3),
+                         evals_per_system=evals / len(items),
+                         mean_top1_score=float(np.mean([float(k["score"][0].item()) for _, k in items]))))
+    return rows
+
+
 # ---------------------------------------------------------------- serving (continuous batching)
 def run_serving(args):
     """Poisson arrivals of docking requests over 8 resident receptors (2,000-8,000
@@ -574,6 +630,7 @@ def run_e2e(args, rank, dev):
     dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
     opt = dsdp.DSDP_OPT_BFGS if args.optimizer == "bfgs" else dsdp.DSDP_OPT_BB
     sysl = systems(rank, args.batch)
+    blob_bytes = {seed: len(dsdp.dsdp_ligand_pack(lig)) for seed, rec, lig in sysl}  # counted, not timed
     ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, args.batch))
     h2d = d2h = 0
     latencies = []
@@ -592,7 +649,7 @@ def run_e2e(args, rank, dev):
                 grids.append(g)
                 bufs.append(dsdp.result_buffers(lig.n_atoms, lig.n_torsions, params))
                 if count:
-                    h2d += rec.xyz.nbytes + rec.xs_type.nbytes + len(dsdp.dsdp_ligand_pack(lig))
+                    h2d += rec.xyz.nbytes + rec.xs_type.nbytes + blob_bytes[seed]
             for (seed, *_), j, b in zip(sysl, jids, bufs):
                 r = dsdp.dsdp_dock_poll(ctx, j, b, wait_ms=-1)
                 if count:
@@ -678,6 +735,16 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        rows = run_sweep(args)
+        print(json.dumps({"metric": "typical-4k docking time vs copies x MC steps (paper Table 1 grid)", "n_gpus": 1,
+                          "unit": "ms per system (one per launch) / systems/s (batched)",
+                          "systems_per_batch": args.batch, "dtype": "f32", "data": "synthetic", "sweep": rows}),
+              flush=True)
         return
     if args.serve:
         import __graft_entry__

@@ -217,7 +217,11 @@ dsdp_status dsdp_destroy(dsdp_ctx* ctx);
  * E_t(m) = sum_j f(t, t_j, |m - r_j|) over receptor atoms within 8 A and its
  * gradient with respect to m.  Receptor arrays are host memory.  The grid
  * (and a device copy of the receptor, used for FP64 rescoring) stays resident
- * until dsdp_grid_free.  Returns after the maps are built. */
+ * until dsdp_grid_free.  Returns once the receptor has been copied and the
+ * build is queued on the device: jobs, scoring and downloads that use the grid
+ * are ordered after the build there, so a host thread can submit the next
+ * request while the GPU is busy.  An error of the build kernel itself is
+ * reported by the first call that waits for it. */
 dsdp_status dsdp_grid_build(dsdp_ctx* ctx, const dsdp_receptor* receptor, const dsdp_box* box,
                             dsdp_map_dtype dtype, dsdp_grid_mode mode, dsdp_grid** out);
 /* Make a grid from maps computed elsewhere (host, FP32, layout above, C = 4

@@ -38,6 +38,7 @@ struct dsdp_grid {
   uint8_t* d_rec_type = nullptr;
   uint64_t rec_bytes = 0;
   std::atomic<int> users{0};  // jobs referencing the grid
+  cudaEvent_t ready = nullptr;  // recorded after the maps are written; jobs wait on it on the device
 };
 
 namespace {
@@ -89,8 +90,10 @@ struct dsdp_ctx {
   int max_inflight = 16;
   int max_batch_chains = 0;            // chains per batch: 4 x the resident chain slots
   std::vector<cudaStream_t> streams;   // one batch in flight per stream
-  cudaStream_t sync_stream = nullptr;   // synchronous calls
+  cudaStream_t sync_stream = nullptr;   // synchronous calls and grid builds
+  cudaStream_t upload_stream = nullptr; // receptor uploads of grid builds (copy engines only)
   cudaStream_t alloc_stream = nullptr;  // allocations done outside a job stream
+  cudaMemPool_t pool = nullptr;         // the context's own stream-ordered pool (no caller allocator)
   int next_stream = 0;
   dsdp_alloc_fn alloc = nullptr;
   dsdp_free_fn free_fn = nullptr;
@@ -129,7 +132,8 @@ void* ctx_alloc(dsdp_ctx* ctx, size_t bytes, void* stream) {
     return p;
   }
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->alloc_stream;
-  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+  const cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(&p, bytes, ctx->pool, st) : cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -325,6 +329,8 @@ Batch* batch_launch(dsdp_ctx* ctx, const std::vector<Job*>& jobs, int stream) {
   b->jobs = jobs;
   b->stream = stream;
   dsdp_status s = dsdp_plan_create(ctx, (int32_t)jd.size(), jd.data(), 0, 0, &b->plan);
+  for (size_t i = 0; s == DSDP_OK && i < jobs.size(); ++i)  // the maps may still be in the making
+    if (jobs[i]->grid->ready) s = check_cuda(cudaStreamWaitEvent(st, jobs[i]->grid->ready, 0), "grid wait");
   if (s == DSDP_OK) {
     cudaEventCreateWithFlags(&b->ev_start, cudaEventDefault);
     cudaEventCreateWithFlags(&b->ev_done, cudaEventDefault);
@@ -498,10 +504,34 @@ extern "C" dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** 
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     ctx->streams.push_back(s);
   }
-  cudaStreamCreateWithFlags(&ctx->sync_stream, cudaStreamNonBlocking);
-  cudaStreamCreateWithFlags(&ctx->alloc_stream, cudaStreamNonBlocking);
+  // Synchronous calls (grid builds, scoring) run at the highest stream priority:
+  // their CTAs are scheduled ahead of the job streams' pending chain CTAs, so a
+  // grid build does not wait for the docking kernels already on the GPU.
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  cudaStreamCreateWithPriority(&ctx->sync_stream, cudaStreamNonBlocking, prio_greatest);
+  cudaStreamCreateWithPriority(&ctx->alloc_stream, cudaStreamNonBlocking, prio_greatest);
+  cudaStreamCreateWithPriority(&ctx->upload_stream, cudaStreamNonBlocking, prio_greatest);
   ctx->alloc = p.alloc;
   ctx->free_fn = p.free;
+  if (!ctx->alloc) {
+    // A pool of the context's own that keeps freed memory (up to the budget)
+    // instead of returning it to the driver at each synchronisation: grids and
+    // jobs come and go at serving rates, and re-mapping tens of MB per grid
+    // costs milliseconds.
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) == cudaSuccess) {
+      uint64_t keep = ctx->budget;
+      cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      ctx->pool = nullptr;
+    }
+  }
   ctx->alloc_user = p.alloc_user;
   if (!ctx->alloc) {
     cudaMemPool_t pool;
@@ -547,7 +577,10 @@ extern "C" dsdp_status dsdp_destroy(dsdp_ctx* ctx) {
   for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s), cudaStreamDestroy(s);
   cudaStreamSynchronize(ctx->alloc_stream);
   cudaStreamDestroy(ctx->alloc_stream);
+  cudaStreamSynchronize(ctx->upload_stream);
+  cudaStreamDestroy(ctx->upload_stream);
   cudaStreamDestroy(ctx->sync_stream);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return DSDP_OK;
 }
@@ -612,13 +645,20 @@ static dsdp_status grid_alloc(dsdp_ctx* ctx, const dsdp_receptor* receptor, cons
     dsdp_grid_free(ctx, g);
     return set_error(DSDP_ERR_OUT_OF_MEMORY, "grid device allocation failed");
   }
-  if (receptor) {
-    cudaError_t e = cudaMemcpy(g->d_rec_xyz, receptor->xyz, (size_t)receptor->n * 12, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_rec_type, receptor->xs_type, receptor->n, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      dsdp_grid_free(ctx, g);
-      return check_cuda(e, "receptor upload");
-    }
+  cudaError_t e = cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming);
+  if (e == cudaSuccess && receptor) {
+    // pageable sources: each copy returns once the caller's array has been read;
+    // the upload stream holds only such copies, so it never waits for kernels
+    e = cudaMemcpyAsync(g->d_rec_xyz, receptor->xyz, (size_t)receptor->n * 12, cudaMemcpyHostToDevice,
+                        ctx->upload_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->d_rec_type, receptor->xs_type, receptor->n, cudaMemcpyHostToDevice, ctx->upload_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ready, ctx->upload_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->sync_stream, g->ready, 0);
+  }
+  if (e != cudaSuccess) {
+    dsdp_grid_free(ctx, g);
+    return check_cuda(e, "receptor upload");
   }
   *out = g;
   return DSDP_OK;
@@ -636,7 +676,8 @@ extern "C" dsdp_status dsdp_grid_build(dsdp_ctx* ctx, const dsdp_receptor* recep
   if (s != DSDP_OK) return s;
   dsdp_receptor dr{g->n_rec, g->d_rec_xyz, g->d_rec_type};
   s = dsdp_grid_build_device(&dr, box, dtype, mode, g->d_maps, g->map_bytes, (void*)ctx->sync_stream);
-  if (s == DSDP_OK) s = check_cuda(cudaStreamSynchronize(ctx->sync_stream), "grid build");
+  // no host wait: jobs on this grid wait for `ready` on the device
+  if (s == DSDP_OK) s = check_cuda(cudaEventRecord(g->ready, ctx->sync_stream), "grid build event");
   if (s != DSDP_OK) {
     dsdp_grid_free(ctx, g);
     return s;
@@ -734,7 +775,8 @@ extern "C" dsdp_status dsdp_grid_download(dsdp_ctx* ctx, const dsdp_grid* g, flo
   const size_t count = (size_t)DSDP_NUM_MAP_TYPES * g->n[0] * g->n[1] * g->n[2] * (g->mode == DSDP_GRID_EQ4 ? 4 : 1);
   if (capacity_floats < count) return set_error(DSDP_ERR_INVALID_ARG, "capacity %zu < %zu floats", capacity_floats, count);
   cudaSetDevice(ctx->device);
-  cudaError_t e;
+  cudaError_t e = g->ready ? cudaEventSynchronize(g->ready) : cudaSuccess;  // the build may still run
+  if (e != cudaSuccess) return check_cuda(e, "grid build");
   if (g->dtype == DSDP_MAP_F32) {
     e = cudaMemcpy(maps, g->d_maps, count * 4, cudaMemcpyDeviceToHost);
   } else {
@@ -762,9 +804,11 @@ extern "C" dsdp_status dsdp_grid_free(dsdp_ctx* ctx, dsdp_grid* g) {
   if (!ctx) ctx = g->ctx;
   if (g->users.load() > 0) return set_error(DSDP_ERR_INVALID_ARG, "grid still used by %d job(s)", g->users.load());
   cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->upload_stream);
   cudaStreamSynchronize(ctx->sync_stream);
   ctx_free(ctx, g->d_maps, g->map_bytes, nullptr);
   ctx_free(ctx, g->d_rec_xyz, g->rec_bytes, nullptr);
+  if (g->ready) cudaEventDestroy(g->ready);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->in_use -= g->map_bytes + g->rec_bytes;
