@@ -236,12 +236,15 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
         const float2 fx = __fmul2_rn(sp, dx), fy = __fmul2_rn(sp, dy), fz = __fmul2_rn(sp, dz);
         const float3 c0 = shfl3(make_float3(fx.x, fy.x, fz.x), (int)(t0.x >> 5));
         const float3 c1 = shfl3(make_float3(fx.y, fy.y, fz.y), (int)(t1.x >> 5));
-        g[0].x += (ac0 ? 0.f : fx.x) + (ac1 ? 0.f : fx.y) - (pc0 ? 0.f : c0.x) - (pc1 ? 0.f : c1.x);
-        g[0].y += (ac0 ? 0.f : fy.x) + (ac1 ? 0.f : fy.y) - (pc0 ? 0.f : c0.y) - (pc1 ? 0.f : c1.y);
-        g[0].z += (ac0 ? 0.f : fz.x) + (ac1 ? 0.f : fz.y) - (pc0 ? 0.f : c0.z) - (pc1 ? 0.f : c1.z);
-        g[APL - 1].x += (ac0 ? fx.x : 0.f) + (ac1 ? fx.y : 0.f) - (pc0 ? c0.x : 0.f) - (pc1 ? c1.x : 0.f);
-        g[APL - 1].y += (ac0 ? fy.x : 0.f) + (ac1 ? fy.y : 0.f) - (pc0 ? c0.y : 0.f) - (pc1 ? c1.y : 0.f);
-        g[APL - 1].z += (ac0 ? fz.x : 0.f) + (ac1 ? fz.y : 0.f) - (pc0 ? c0.z : 0.f) - (pc1 ? c1.z : 0.f);
+        // each force goes to the slot its bit names (per-lane predication, no selects)
+        if (ac0) g[APL - 1].x += fx.x, g[APL - 1].y += fy.x, g[APL - 1].z += fz.x;
+        else g[0].x += fx.x, g[0].y += fy.x, g[0].z += fz.x;
+        if (ac1) g[APL - 1].x += fx.y, g[APL - 1].y += fy.y, g[APL - 1].z += fz.y;
+        else g[0].x += fx.y, g[0].y += fy.y, g[0].z += fz.y;
+        if (pc0) g[APL - 1].x -= c0.x, g[APL - 1].y -= c0.y, g[APL - 1].z -= c0.z;
+        else g[0].x -= c0.x, g[0].y -= c0.y, g[0].z -= c0.z;
+        if (pc1) g[APL - 1].x -= c1.x, g[APL - 1].y -= c1.y, g[APL - 1].z -= c1.z;
+        else g[0].x -= c1.x, g[0].y -= c1.y, g[0].z -= c1.z;
       }
     }
     e_lane += e_pair.x + e_pair.y;
