@@ -149,9 +149,10 @@ CHAIN_SOURCES = ["chain_device.cuh", "device_common.cuh", "dock_kernels.cuh", "d
                  "launch.h", "ligand_pack.cpp"]
 
 
-def chain_kernel_traffic(batch, map_dtype):
-    """DRAM bytes per chain-kernel launch from the committed ncu capture, or None
-    when the kernel sources changed since it was taken or the workload differs."""
+def chain_kernel_capture(batch, map_dtype):
+    """The committed ncu figures of the chain kernel (DRAM bytes per launch of the
+    16-system workload, warp instructions per evaluation), or None when the kernel
+    sources changed since they were taken or the workload differs."""
     import hashlib
 
     try:
@@ -165,7 +166,12 @@ def chain_kernel_traffic(batch, map_dtype):
             h.update(f.read())
     if h.hexdigest() != rec.get("sources_sha256") or batch != 16 or map_dtype != "f32":
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return rec
+
+
+def issue_peak_per_s(sm_mhz):
+    # 152 SMs x 4 schedulers x one warp instruction per cycle
+    return 152 * 4 * sm_mhz * 1e6
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -795,6 +801,7 @@ def main():
     achieved_tflops = r["flops"] / per_launch_s / 1e12
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = fp32_peak_tflops(sm_mhz)
+    capture = chain_kernel_capture(args.batch, args.map_dtype)
     line = {
         "metric": "docked systems/s (typical-4k: 4k-atom receptor, 80^3 maps, 30-atom ligand, 384x40 MC+BFGS)",
         "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -810,12 +817,18 @@ def main():
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
         "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": chain_kernel_traffic(args.batch, args.map_dtype),
+                     "traffic": capture["dram_bytes_per_launch"] if capture else None,
                      "traffic_unit": "DRAM bytes per launch (ncu)",
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
                                     f"(clock from MEASURED_PEAKS.json, {peaks_src})"},
         "l2_gather": {"achieved_gbs": r["gather_bytes"] / per_launch_s / 1e9, "microbench_gbs": r["gather_gbs"],
                       "frac": (r["gather_bytes"] / per_launch_s / 1e9) / r["gather_gbs"]},
+        "issue": None if not capture else {
+            "warp_instructions_per_eval": capture["warp_instructions_per_eval"],
+            "achieved_per_s": capture["warp_instructions_per_eval"] * r["total_evals"] / per_launch_s,
+            "peak_per_s": issue_peak_per_s(sm_mhz),
+            "frac": capture["warp_instructions_per_eval"] * r["total_evals"] / per_launch_s / issue_peak_per_s(sm_mhz),
+            "note": "instructions per evaluation from the committed ncu capture; evaluations and time measured here"},
         "gpu_launches": r["launches_per_step"] * args.steps,
         "clocks": r["clocks"],
         "results_ok": r["results_ok"],
