@@ -60,12 +60,43 @@ def parse():
     return p.parse_args()
 
 
+def replica_seeds(rank, batch):
+    """Seeds of the systems rank `rank` docks: the replicas share no system."""
+    return [1000 * rank + b for b in range(batch)]
+
+
+def max_over_ranks(dist, value, device):
+    """The slowest rank's time (every rank gets it)."""
+    import torch
+
+    if not dist:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device):
+    """A per-rank rate summed over the ranks (every rank gets it)."""
+    import torch
+
+    if not dist:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+def job_throughput(world, systems_per_rank_step, steps, slowest_ms):
+    """Whole-job systems/s: every rank's systems over the slowest rank's time."""
+    return world * systems_per_rank_step * steps / (slowest_ms * 1e-3)
+
+
 def systems(rank, batch):
     from paper_2303_09916_gb300 import synth
 
     out = []
-    for b in range(batch):
-        seed = 1000 * rank + b
+    for seed in replica_seeds(rank, batch):
         rec = synth.receptor(N_REC, seed)
         lig = synth.ligand(N_LIG, T_LIG, seed, center=rec.pocket_center)
         out.append((seed, rec, lig))
@@ -286,11 +317,7 @@ def run_device(args, rank, world, dev, dist):
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    if dist:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), dev)
     grid_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     chain_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     rescore_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
@@ -786,17 +813,15 @@ def main():
     single = run_one_job_per_launch(args, rank, local, 2) if args.forms else None
     uneven = run_uneven_graph(args, local) if args.forms and rank == 0 else None
     variants = run_variants(args, rank, local) if args.forms and rank == 0 else None
-    if dist:
-        t = torch.tensor([e2e["value"] if e2e else 0.0], dtype=torch.float64, device=local)
-        dist.all_reduce(t)
-        if e2e:
-            e2e["value"] = float(t.item())
+    e2e_total = sum_over_ranks(dist, e2e["value"] if e2e else 0.0, local)
+    if e2e:
+        e2e["value"] = e2e_total
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     peaks, peaks_src = measured_peaks()
-    value = world * args.batch * args.steps / (r["elapsed_ms"] * 1e-3)
+    value = job_throughput(world, args.batch, args.steps, r["elapsed_ms"])
     per_launch_s = r["chain_ms"] * 1e-3
     achieved_tflops = r["flops"] / per_launch_s / 1e12
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)

@@ -1,0 +1,54 @@
+"""The multi-GPU bench path (independent replicas, one per GPU: the docking
+jobs shard with no exchange step) on two CPU ranks over gloo: replicas dock
+disjoint systems, the timing is the slowest rank's, rates add up."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        elapsed = [120.0, 95.5][rank]  # ms: rank 0 is the slower one
+        e2e = [10.0, 12.5][rank]  # systems/s
+        slowest = bench.max_over_ranks(dist, elapsed, "cpu")
+        total = bench.sum_over_ranks(dist, e2e, "cpu")
+        out[rank] = (slowest, total, bench.replica_seeds(rank, 16),
+                     bench.job_throughput(world, 16, 10, slowest))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_combine_like_the_bench():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        slowest, total, seeds, value = res[r]
+        assert slowest == 120.0  # max over ranks, on every rank
+        assert total == 22.5  # e2e rates add up
+        assert value == pytest.approx(2 * 16 * 10 / 0.120)  # all ranks' systems over the slowest time
+    assert not set(res[0][2]) & set(res[1][2])  # replicas dock disjoint systems
+    assert len(set(res[0][2])) == 16
+
+
+def test_single_process_is_the_identity():
+    assert bench.max_over_ranks(None, 7.0, "cpu") == 7.0
+    assert bench.sum_over_ranks(None, 3.0, "cpu") == 3.0
+    assert bench.job_throughput(1, 16, 10, 500.0) == pytest.approx(320.0)
