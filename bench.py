@@ -56,7 +56,8 @@ def parse():
     p.add_argument("--sweep", action="store_true",
                    help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
     p.add_argument("--tile-config", type=int, default=-1,
-                   help="chain kernel launch configuration: -1 autotune (default), 1/2 fixed register budget")
+                   help="chain kernel launch configuration: -1 autotune (default); 1..6 fixed: register budget "
+                        "128 (odd) or 96 (even), 1 (1, 2), 2 (3, 4) or 4 (5, 6) chains per CTA")
     return p.parse_args()
 
 
@@ -101,6 +102,15 @@ def systems(rank, batch):
         lig = synth.ligand(N_LIG, T_LIG, seed, center=rec.pocket_center)
         out.append((seed, rec, lig))
     return out
+
+
+def describe_tile_config(chosen):
+    """The autotuner's choice (1 + variant + 2 persistent + 4 log2 W) in words."""
+    if not 1 <= chosen <= 12:
+        return "?"
+    c = chosen - 1
+    regs, queue, warps = (128, 96)[c % 2], (c // 2) % 2, 1 << (c // 4)
+    return f"{regs} regs, {warps} chain{'s' if warps > 1 else ''}/CTA" + (", work queue" if queue else "")
 
 
 def flops_per_eval(n_atoms, n_pairs, n_bodies):
@@ -280,7 +290,8 @@ def run_device(args, rank, world, dev, dist):
     else:
         dsdp.dsdp_plan_destroy(None, plan)
         plan = dsdp.dsdp_plan_create(None, jobs, 0, args.tile_config)
-        tile_config = args.tile_config
+        # fixed configuration 1..6 (variant, chains per CTA) in the autotuner's numbering
+        tile_config = 1 + (args.tile_config - 1) % 2 + 4 * ((args.tile_config - 1) // 2)
     n_plan_kernels = dsdp.dsdp_plan_kernel_count(plan)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -524,8 +535,7 @@ def run_uneven_graph(args, dev, steps=3):
     atoms = [lig.n_atoms for lig in cfg.ligands]
     return dict(ligands_per_s=len(jobs) / (ms * 1e-3), ms_per_launch=ms, evals_per_s=evals / (ms * 1e-3),
                 ligand_atoms=f"{min(atoms)}-{max(atoms)}", chains_per_ligand=cfg.n_chains,
-                chain_kernel={1: "128 regs", 2: "96 regs", 3: "128 regs, work queue",
-                              4: "96 regs, work queue"}.get(chosen, "?"), launch="captured CUDA graph",
+                chain_kernel=describe_tile_config(chosen), launch="captured CUDA graph",
                 results_ok=ok)
 
 
@@ -836,8 +846,7 @@ def main():
                    "grid": "80^3 x 8", "map_dtype": args.map_dtype, "ligand": f"{N_LIG} atoms / {T_LIG} torsions",
                    "chains": N_CHAINS, "mc_steps": N_STEPS, "opt_iters": N_ITERS, "optimizer": args.optimizer,
                    "top_k": TOP_K, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
-                   "chain_kernel": {1: "128 regs", 2: "96 regs", 3: "128 regs, work queue",
-                                    4: "96 regs, work queue"}.get(r["tile_config"], "?")},
+                   "chain_kernel": describe_tile_config(r["tile_config"])},
         "evals_per_s": world * r["total_evals"] * args.steps / (r["elapsed_ms"] * 1e-3),
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
         "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,

@@ -339,18 +339,22 @@ enum {
 };
 /* Prepare a launch of n_jobs jobs (uneven ligands allowed): uploads job and
  * tile tables, sizes scratch (allocated with the ctx allocator; ctx may be NULL
- * for plain cudaMalloc).  One warp runs one chain, one chain per CTA.
+ * for plain cudaMalloc).  One warp runs one chain; a CTA runs a tile of W
+ * chains of one job (W = 1, 2 or 4) and stages that job's ligand once.
  * tile_config: 0 = automatic (the choice dsdp_plan_autotune recorded for a plan
  * of the same shape -- map formats, atoms per lane, chain count rounded up to
- * a power of two -- else the 128-register kernel), 1 = chain kernel limited to
- * 128 registers (16 warps per SM), 2 = limited to 96 registers (20 warps per
- * SM). */
+ * a power of two -- else the 128-register kernel with W = 1); 1 .. 6 = a fixed
+ * choice: register budget 128 (odd values; 16 warps per SM) or 96 (even; 20
+ * warps per SM) and W = 1 (1, 2), 2 (3, 4) or 4 (5, 6).  Results do not depend
+ * on the configuration. */
 dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
                              int32_t tile_config, dsdp_plan** out);
 /* Autotuner: runs the plan's chain stage `repeats` times for each register
- * budget, with and without the persistent work queue, keeps the fastest for
- * this plan and records it for later plans of the same shape (process-wide).
- * *chosen = 1 + variant + 2 * persistent.  Synchronises the stream. */
+ * budget, each tile of W = 1, 2, 4 chains per CTA, with and without the
+ * persistent work queue, keeps the fastest for this plan and records it for
+ * later plans of the same shape (process-wide).  *chosen = 1 + variant
+ * + 2 * persistent + 4 * log2(W) (variant 0: 128 registers, 1: 96).
+ * Synchronises the stream. */
 dsdp_status dsdp_plan_autotune(dsdp_plan* plan, void* stream, int32_t repeats, int32_t* chosen);
 /* Enqueue the plan's kernels on `stream` (chains, then FP64 rescoring and
  * top-k).  No allocation and no host synchronisation: a launch can be

@@ -8,16 +8,18 @@ namespace dsdp {
 
 // Register budgets of the chain kernel: variant 0 caps at 128 registers (16
 // warps per SM, no spills), variant 1 at 96 (20 warps, a few spills); the
-// autotuner picks per plan by measurement.
+// autotuner picks per plan by measurement.  The bounds are stated for CTAs of
+// up to 4 warps (chains); CTAs of 1 or 2 warps get the same register cap.
+constexpr int kMaxChainWarps = 4;
 template <int VAR>
 struct ChainOcc;
 template <>
 struct ChainOcc<0> {
-  static constexpr int kMinBlocks = 16;  // with 32-thread CTAs: 65536 / (32 * 16) = 128 registers
+  static constexpr int kMinBlocks = 4;  // 65536 / (128 * 4) = 128 registers
 };
 template <>
 struct ChainOcc<1> {
-  static constexpr int kMinBlocks = 20;  // 102 -> 96 registers
+  static constexpr int kMinBlocks = 5;  // 102 -> 96 registers
 };
 
 // Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
@@ -28,7 +30,7 @@ struct ChainOcc<1> {
 // single-tile kernel keeps its register allocation to itself).
 // persistent != 0: CTAs pull tiles from *tile_counter until none are left.
 template <int FMT, int VAR, int APLS>
-__global__ void __launch_bounds__(32, ChainOcc<VAR>::kMinBlocks) dock_chains_kernel(const DevJob* __restrict__ jobs,
+__global__ void __launch_bounds__(32 * kMaxChainWarps, ChainOcc<VAR>::kMinBlocks) dock_chains_kernel(const DevJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles, int n_tiles,
                                                           int* tile_counter, int persistent, int blob_smem,
                                                           ScratchLayout lay) {
@@ -99,8 +101,8 @@ __global__ void __launch_bounds__(256) score_eval_kernel(MapView M, const uint8_
 
 template <int FMT, int VAR, int APLS>
 cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
-  const dim3 block(32);
-  const size_t smem = (size_t)a.blob_smem + (size_t)a.scratch.bytes;
+  const dim3 block(32 * a.warps_per_cta);
+  const size_t smem = (size_t)a.blob_smem + (size_t)a.warps_per_cta * a.scratch.bytes;
   auto k = dock_chains_kernel<FMT, VAR, APLS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -109,7 +111,7 @@ cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * a.warps_per_cta, smem);
     if (e != cudaSuccess) return e;
     grid = per_sm * sms < a.n_tiles ? per_sm * sms : a.n_tiles;
     if (grid < 1) grid = 1;
@@ -121,7 +123,7 @@ cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
 
 template <int FMT>
 cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
-  if (a.warps_per_cta != 1) return cudaErrorInvalidValue;  // one warp (one chain) per CTA
+  if (a.warps_per_cta != 1 && a.warps_per_cta != 2 && a.warps_per_cta != kMaxChainWarps) return cudaErrorInvalidValue;
   if (a.apl_mask == 1) return a.variant ? launch_chains_var<FMT, 1, 1>(a, st) : launch_chains_var<FMT, 0, 1>(a, st);
   if (a.apl_mask == 2) return a.variant ? launch_chains_var<FMT, 1, 2>(a, st) : launch_chains_var<FMT, 0, 2>(a, st);
   return launch_chains_var<FMT, 0, 3>(a, st);  // mixed tiles: the 128-register budget only

@@ -29,6 +29,7 @@ struct dsdp_plan {
   void* d_rtiles = nullptr;
   int* d_counters = nullptr;
   int n_rtiles = 0;
+  std::vector<int> job_fmt, job_chains;  // to lay chain tiles out again for another warps_per_cta
   int sms = 148;
 };
 
@@ -104,7 +105,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 // by plans created with tile_config 0.
 struct TuneEntry {
   uint64_t key;
-  int variant, persistent;
+  int variant, persistent, warps;
 };
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
@@ -115,26 +116,51 @@ static uint64_t tune_key(uint32_t fmt_mask, int apl, size_t chains) {
   return ((uint64_t)fmt_mask << 16) | ((uint64_t)apl << 8) | (uint64_t)lg;
 }
 
-static bool tune_lookup(uint64_t key, int* variant, int* persistent) {
+static bool tune_lookup(uint64_t key, int* variant, int* persistent, int* warps) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (const TuneEntry& t : g_tune)
     if (t.key == key) {
       *variant = t.variant;
       *persistent = t.persistent;
+      *warps = t.warps;
       return true;
     }
   return false;
 }
 
-static void tune_store(uint64_t key, int variant, int persistent) {
+static void tune_store(uint64_t key, int variant, int persistent, int warps) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (TuneEntry& t : g_tune)
     if (t.key == key) {
       t.variant = variant;
       t.persistent = persistent;
+      t.warps = warps;
       return;
     }
-  g_tune.push_back(TuneEntry{key, variant, persistent});
+  g_tune.push_back(TuneEntry{key, variant, persistent, warps});
+}
+
+// Chain tiles of W chains of one job, grouped by map format (one launch per
+// format present); fills each group's tile range.
+static void plan_tiles(dsdp_plan* P, int W, std::vector<Tile>& tiles) {
+  tiles.clear();
+  for (dsdp_plan::Group& g : P->groups) {
+    g.first_tile = (int)tiles.size();
+    for (int j = 0; j < P->n_jobs; ++j) {
+      if (P->job_fmt[j] != g.fmt) continue;
+      for (int c = 0; c < P->job_chains[j]; c += W)
+        tiles.push_back(Tile{j, c, std::min(W, P->job_chains[j] - c), 0});
+    }
+    g.n_tiles = (int)tiles.size() - g.first_tile;
+  }
+}
+
+static cudaError_t plan_use_warps(dsdp_plan* P, int W) {
+  std::vector<Tile> tiles;
+  plan_tiles(P, W, tiles);
+  P->warps_per_cta = W;
+  return tiles.empty() ? cudaSuccess
+                       : cudaMemcpy(P->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice);
 }
 
 }  // namespace dsdp
@@ -173,7 +199,7 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   if (!out) return set_error(DSDP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_jobs < 1 || !jobs) return set_error(DSDP_ERR_INVALID_ARG, "plan needs >= 1 job");
-  if (tile_config < 0 || tile_config > 2) return set_error(DSDP_ERR_INVALID_ARG, "tile_config outside 0..2");
+  if (tile_config < 0 || tile_config > 6) return set_error(DSDP_ERR_INVALID_ARG, "tile_config outside 0..6");
   std::vector<DevJob> dj(n_jobs);
   std::vector<int> fmt(n_jobs), apl(n_jobs), blob_bytes(n_jobs), pairs(n_jobs), atoms(n_jobs), tors(n_jobs);
   size_t scratch = 0;
@@ -253,30 +279,28 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   P->flags = flags;
   P->max_chains = max_chains;
   P->sms = ctx_sm_count(ctx);
-  // One warp (one chain) per CTA: each chain is scheduled on its own, so no CTA
-  // slot waits for the slowest chain of a tile; the ligand is staged per chain.
-  const int W = 1;
-  P->warps_per_cta = W;
-  // chain tiles grouped by map format (one launch per format present)
-  std::vector<Tile> tiles;
+  // Groups by map format (one launch per format present); a CTA runs a tile of
+  // W chains of one job (W = warps per CTA: 1, 2 or 4), staging the ligand once.
+  P->job_fmt = fmt;
+  P->job_chains.resize(n_jobs);
+  size_t total_chains = 0;
+  for (int j = 0; j < n_jobs; ++j) total_chains += (size_t)(P->job_chains[j] = dj[j].n_chains);
   for (int f = 0; f < 6; ++f) {
-    dsdp_plan::Group g{f, 1, (int)tiles.size(), 0, 0, 0, 0, 0, 0};
-    for (int j = 0; j < n_jobs; ++j)
-      if (fmt[j] == f) {
-        g.apl = std::max(g.apl, apl[j]);  // largest tile present: part of the autotuner key
-        g.apl_mask |= apl[j];             // each job runs at its own tile (see dock_chains_kernel)
-      }
+    dsdp_plan::Group g{f, 1, 0, 0, 0, 0, 0, 0, 0};
+    bool any = false;
     for (int j = 0; j < n_jobs; ++j) {
       if (fmt[j] != f) continue;
+      any = true;
+      g.apl = std::max(g.apl, apl[j]);  // largest tile present: part of the autotuner key
+      g.apl_mask |= apl[j];             // each job runs at its own tile (see dock_chains_kernel)
       g.blob_smem = std::max(g.blob_smem, blob_bytes[j]);
       g.max_atoms = std::max(g.max_atoms, atoms[j]);
       g.max_torsions = std::max(g.max_torsions, tors[j]);
       g.max_pairs = std::max(g.max_pairs, pairs[j]);
-      for (int c = 0; c < dj[j].n_chains; c += W) tiles.push_back(Tile{j, c, std::min(W, dj[j].n_chains - c), 0});
     }
-    g.n_tiles = (int)tiles.size() - g.first_tile;
-    if (g.n_tiles > 0) P->groups.push_back(g);
+    if (any) P->groups.push_back(g);
   }
+  int W = 1;
   {
     uint32_t fmt_mask = 0;
     int apl_max = 1;
@@ -284,21 +308,25 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
       fmt_mask |= 1u << g.fmt;
       apl_max = std::max(apl_max, g.apl);
     }
-    P->tune_key = tune_key(fmt_mask, apl_max, tiles.size());
+    P->tune_key = tune_key(fmt_mask, apl_max, total_chains);
     int var = 0, pers = (flags & DSDP_PLAN_PERSISTENT) ? 1 : 0;
     if (tile_config == 0) {
-      if (tune_lookup(P->tune_key, &var, &pers) && pers) P->flags |= DSDP_PLAN_PERSISTENT;
+      if (tune_lookup(P->tune_key, &var, &pers, &W) && pers) P->flags |= DSDP_PLAN_PERSISTENT;
     } else {
-      var = tile_config - 1;
+      var = (tile_config - 1) % 2;
+      W = 1 << ((tile_config - 1) / 2);
     }
     P->variant = var;
   }
+  std::vector<Tile> tiles;
+  plan_tiles(P, W, tiles);
+  P->warps_per_cta = W;
   std::vector<Tile> rtiles;
   const int rw = rescore_tile_chains();
   for (int j = 0; j < n_jobs; ++j)
     for (int c = 0; c < dj[j].n_chains; c += rw) rtiles.push_back(Tile{j, c, std::min(rw, dj[j].n_chains - c), 0});
   P->n_rtiles = (int)rtiles.size();
-  const size_t b_jobs = up256(sizeof(DevJob) * n_jobs), b_tiles = up256(sizeof(Tile) * tiles.size()),
+  const size_t b_jobs = up256(sizeof(DevJob) * n_jobs), b_tiles = up256(sizeof(Tile) * total_chains),
                b_rtiles = up256(sizeof(Tile) * rtiles.size()), b_cnt = up256(sizeof(int) * 8);
   P->arena_bytes = b_jobs + b_tiles + b_rtiles + b_cnt + scratch;
   P->arena = ctx_alloc(ctx, P->arena_bytes, nullptr);
@@ -399,8 +427,14 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
   if (e != cudaSuccess) return check_cuda(e, "autotune events");
   const uint32_t base_flags = P->flags & ~(uint32_t)DSDP_PLAN_PERSISTENT;
   float best = 1e30f;
-  int best_var = P->variant, best_pers = (P->flags & DSDP_PLAN_PERSISTENT) ? 1 : 0;
+  int best_var = P->variant, best_pers = (P->flags & DSDP_PLAN_PERSISTENT) ? 1 : 0, best_w = P->warps_per_cta;
   dsdp_status s = DSDP_OK;
+  for (int w = 1; w <= 4 && s == DSDP_OK; w *= 2) {
+    e = plan_use_warps(P, w);
+    if (e != cudaSuccess) {
+      s = check_cuda(e, "autotune tiles");
+      break;
+    }
   for (int var = 0; var < 2 && s == DSDP_OK; ++var)
     for (int pers = 0; pers < 2 && s == DSDP_OK; ++pers) {
       P->variant = var;
@@ -421,15 +455,18 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
         best = ms;
         best_var = var;
         best_pers = pers;
+        best_w = w;
       }
     }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   P->variant = best_var;
   P->flags = base_flags | (best_pers ? DSDP_PLAN_PERSISTENT : 0u);
+  if (s == DSDP_OK) s = check_cuda(plan_use_warps(P, best_w), "plan tiles");
   if (s != DSDP_OK) return s;
-  tune_store(P->tune_key, best_var, best_pers);
-  if (chosen) *chosen = 1 + best_var + 2 * best_pers;
+  tune_store(P->tune_key, best_var, best_pers, best_w);
+  if (chosen) *chosen = 1 + best_var + 2 * best_pers + 4 * (best_w == 4 ? 2 : best_w - 1);
   return DSDP_OK;
 }
 

@@ -439,8 +439,9 @@ def test_determinism_and_batch_independence(ctx):
 def test_plan_launch_configurations_agree(ctx):
     """One uneven batch (ligands of 10-60 atoms, 0-15 torsions, two map formats)
     through the device plan in every launch configuration the autotuner chooses
-    from -- 128- or 96-register chain kernel, with or without the persistent work
-    queue -- gives bitwise the same chains, and the autotuner returns one of them.
+    from -- 128- or 96-register chain kernel, 1, 2 or 4 chains per CTA, with or
+    without the persistent work queue -- gives bitwise the same chains, and the
+    autotuner returns one of them.
     Each job run alone in a plan of its own gives bitwise what it gave in the
     batch (the batch mixes one- and two-atoms-per-lane ligands on one map format)."""
     dev = torch.device("cuda", 0)
@@ -474,7 +475,7 @@ def test_plan_launch_configurations_agree(ctx):
         jobs.append(j)
         keep.append((maps, xyz, ty, blob, dblob, conf, e))
     results = []
-    for tile_config in (1, 2):
+    for tile_config in (1, 2, 3, 4, 5, 6):  # register budget x chains per CTA (1, 2, 4)
         for flags in (0, dsdp.DSDP_PLAN_PERSISTENT):
             plan = dsdp.dsdp_plan_create(None, jobs, flags | dsdp.DSDP_PLAN_NO_RESCORE, tile_config)
             try:
@@ -500,7 +501,7 @@ def test_plan_launch_configurations_agree(ctx):
         chosen = dsdp.dsdp_plan_autotune(plan, stream, 1)
     finally:
         dsdp.dsdp_plan_destroy(None, plan)
-    assert chosen in (1, 2, 3, 4)
+    assert 1 <= chosen <= 12
 
 
 def test_plan_replayed_from_a_cuda_graph_matches_the_eager_launch(ctx):
