@@ -286,7 +286,7 @@ def run_device(args, rank, world, dev, dist):
         dsdp.dsdp_grid_build_device(N_REC, d_xyz.data_ptr(), d_type.data_ptr(), box, dtype, dsdp.DSDP_GRID_EQ4,
                                     d_maps.data_ptr(), d_maps.numel(), sptr)
     if args.tile_config < 0:
-        tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 1)  # picks register budget and work queue by measurement
+        tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 2)  # register budget, chains per CTA, work queue
     else:
         dsdp.dsdp_plan_destroy(None, plan)
         plan = dsdp.dsdp_plan_create(None, jobs, 0, args.tile_config)
@@ -514,7 +514,7 @@ def run_uneven_graph(args, dev, steps=3):
         keeps.append(keep)
     build_grid(dsdp, grid, dsdp.DSDP_MAP_F32, sptr)
     plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
-    chosen = dsdp.dsdp_plan_autotune(plan, sptr, 1)
+    chosen = dsdp.dsdp_plan_autotune(plan, sptr, 2)
     cap = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
     torch.cuda.synchronize()

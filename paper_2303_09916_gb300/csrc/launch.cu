@@ -311,6 +311,9 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
     P->tune_key = tune_key(fmt_mask, apl_max, total_chains);
     int var = 0, pers = (flags & DSDP_PLAN_PERSISTENT) ? 1 : 0;
     if (tile_config == 0) {
+      // without a recorded choice: ligands above 32 atoms stage large blobs, which
+      // tiles of 4 chains share (measured faster on mixed batches); else 1 chain
+      W = apl_max == 2 ? 4 : 1;
       if (tune_lookup(P->tune_key, &var, &pers, &W) && pers) P->flags |= DSDP_PLAN_PERSISTENT;
     } else {
       var = (tile_config - 1) % 2;
