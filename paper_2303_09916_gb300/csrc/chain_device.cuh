@@ -332,24 +332,6 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   return E;
 }
 
-// Coordinates of this lane's atoms for a conformation (same kinematics as eval_conf).
-template <int APL>
-__device__ __forceinline__ void conf_coords(const LigView& L, const Conf& c, float3* pos) {
-  const int lane = threadIdx.x & 31;
-  Quat Q;
-  float3 O;
-  body_frames(L, c, Q, O);
-#pragma unroll
-  for (int s = 0; s < APL; ++s) {
-    const int i = lane * APL + s;
-    const float4 a = L.atom[i < L.n_atoms ? i : L.n_atoms - 1];
-    const int b = i < L.n_atoms ? (__float_as_int(a.w) >> 8) & 0xff : 0;
-    const Quat Qb = shflq(Q, b);
-    const float3 Ob = shfl3(O, b);
-    pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
-  }
-}
-
 // c (+) s for a step held in lane layout.
 __device__ __forceinline__ Conf apply_step(const Conf& c, float s, int T) {
   const int lane = threadIdx.x & 31;

@@ -145,38 +145,6 @@ __device__ __forceinline__ Quat shflq(const Quat& q, int src) {
 }
 
 // ------------------------------------------------------------------ pair score
-// Vina pair score of surface distance d (the scoring function DSDP keeps,
-// Sec. 2): weighted gauss1, gauss2, repulsion, hydrophobic and H-bond terms.
-// bits: 1 = hydrophobic pair, 2 = donor/acceptor pair.  Returns e and de/dd.
-__device__ __forceinline__ void vina_pair(float d, int bits, float& e, float& de) {
-  const float a = 2.f * d;  // d / 0.5
-  const float g1 = __expf(-a * a);
-  const float b = 0.5f * (d - 3.f);  // (d - 3) / 2
-  const float g2 = __expf(-b * b);
-  e = kWGauss1 * g1 + kWGauss2 * g2;
-  de = kWGauss1 * g1 * (-8.f * d) + kWGauss2 * g2 * (-b);
-  if (d < 0.f) {
-    e += kWRepulsion * d * d;
-    de += 2.f * kWRepulsion * d;
-  }
-  if (bits & 1) {
-    if (d < 0.5f) {
-      e += kWHydrophobic;
-    } else if (d < 1.5f) {
-      e += kWHydrophobic * (1.5f - d);
-      de -= kWHydrophobic;
-    }
-  }
-  if (bits & 2) {
-    if (d < -0.7f) {
-      e += kWHBond;
-    } else if (d < 0.f) {
-      e += kWHBond * (-d * (1.0f / 0.7f));
-      de -= kWHBond * (1.0f / 0.7f);
-    }
-  }
-}
-
 // 2^x by the ex2.approx instruction (PTX ISA: relative error about 2^-22,
 // subnormal results flushed to zero).  exp(x) = 2^(x / ln 2): callers fold the
 // 1 / ln 2 into their constants.
@@ -207,11 +175,14 @@ __device__ __forceinline__ void steric_x2(float2 d, float2& e, float2& de) {
   de = __ffma2_rn(m, splat2(2.f * kWRepulsion), dd);
 }
 
-// Two intra-ligand pairs per lane in packed FP32x2 arithmetic: the terms of
-// vina_pair without per-lane branches, with d = r2 / r + nrs, nrs = -(R_i + R_j),
-// returning e and (de/dd) / r.  hydrophobic = min(max(1.5 - d, 0), 1) and
-// H-bond = min(max(-d / 0.7, 0), 1) equal the piecewise forms; their slopes are
-// taken on the half-open intervals [0.5, 1.5) and [-0.7, 0), as in vina_pair.
+// Two intra-ligand pairs per lane in packed FP32x2 arithmetic: the Vina-form
+// pair score (the scoring function DSDP keeps, Sec. 2: weighted gauss1, gauss2,
+// repulsion, hydrophobic and H-bond terms of the surface distance d) without
+// per-lane branches, with d = r2 / r + nrs, nrs = -(R_i + R_j), returning e and
+// (de/dd) / r.  hydrophobic = min(max(1.5 - d, 0), 1) and H-bond =
+// min(max(-d / 0.7, 0), 1) equal the piecewise forms (1 below 0.5 / -0.7, 0 from
+// 1.5 / 0); their slopes are taken on the half-open intervals [0.5, 1.5) and
+// [-0.7, 0), the branch of the strict inequality at a breakpoint.
 // Pairs at or beyond the cutoff take d = kFarD, and idle slots get a surface
 // distance at least kStepIdleNrs: there every term and slope is exactly zero.
 // cls0 / cls1: terms the two pairs carry (1 hydrophobic, 2 H-bond); use_hyd /

@@ -10,7 +10,6 @@ constexpr uint32_t kBlobMagic = 0x50445344u;  // "DSDP"
 constexpr int kMaxAtoms = DSDP_MAX_LIGAND_ATOMS;
 constexpr int kMaxBodies = DSDP_MAX_TORSIONS + 1;
 constexpr int kMaxDim = 6 + DSDP_MAX_TORSIONS;  // gradient / step dimension
-constexpr int kMaxPairs = kMaxAtoms * (kMaxAtoms - 1) / 2;
 // Atoms per lane of a warp holding one conformation: internal atom i sits in
 // lane i / APL, slot i % APL.
 __host__ __device__ constexpr int atoms_per_lane(int n_atoms) { return n_atoms <= 32 ? 1 : 2; }
