@@ -343,14 +343,17 @@ enum {
  * chains of one job (W = 1, 2 or 4) and stages that job's ligand once.
  * tile_config: 0 = automatic (the choice dsdp_plan_autotune recorded for a plan
  * of the same shape -- map formats, atoms per lane, chain count rounded up to
- * a power of two -- else the 128-register kernel with W = 1); 1 .. 6 = a fixed
- * choice: register budget 128 (odd values; 16 warps per SM) or 96 (even; 20
- * warps per SM) and W = 1 (1, 2), 2 (3, 4) or 4 (5, 6).  Results do not depend
- * on the configuration. */
+ * a power of two -- else the 128-register kernel with W = 1, or W = 4 when a
+ * ligand has more than 32 atoms); 1 .. 6 = a fixed choice: register budget 128
+ * (odd values; 16 warps per SM) or 96 (even; 20 warps per SM) and W = 1 (1, 2),
+ * 2 (3, 4) or 4 (5, 6).  A map-format group that mixes ligands of up to 32 and
+ * of more than 32 atoms runs one kernel holding both tile sizes, compiled for
+ * 128 registers only.  Results do not depend on the configuration. */
 dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
                              int32_t tile_config, dsdp_plan** out);
 /* Autotuner: runs the plan's chain stage `repeats` times for each register
- * budget, each tile of W = 1, 2, 4 chains per CTA, with and without the
+ * budget (128 only when every group mixes tile sizes), each tile of
+ * W = 1, 2, 4 chains per CTA, with and without the
  * persistent work queue, keeps the fastest for this plan and records it for
  * later plans of the same shape (process-wide).  *chosen = 1 + variant
  * + 2 * persistent + 4 * log2(W) (variant 0: 128 registers, 1: 96).

@@ -152,8 +152,9 @@ __device__ __forceinline__ void body_frames(const LigView& L, const Conf& c, Qua
 }
 
 // Score and gradient of one conformation (all lanes return the same E;
-// lane j < 6 + T returns gradient component j, other lanes 0).
-template <int APL, int FMT>
+// lane j < 6 + T returns gradient component j, other lanes 0).  IU: how many
+// step pairs of the one-atom-per-lane intra loop are unrolled.
+template <int APL, int FMT, int IU = 2>
 __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, const LaneLig<APL>& R,
                                            const WarpScratch& W, const Conf& c, float& grad, uint32_t flags) {
   const int lane = threadIdx.x & 31;
@@ -190,7 +191,10 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       // packed accumulators: component .x collects the even steps, .y the odd ones
       const float2 px = splat2(pos[0].x), py = splat2(pos[0].y), pz = splat2(pos[0].z);
       float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
-#pragma unroll 1
+      // unrolled (IU = 2): the shuffles of one step pair overlap the arithmetic of
+      // the next; four measured slower, and the kernel that holds both tiles
+      // (more live registers) runs faster without unrolling
+#pragma unroll IU
       for (int st = 0; st < L.n_steps; st += 2) {
         const uint2 t0 = tab[st * 32], t1 = tab[st * 32 + 32];
         // shfl.idx reads the source lane from bits 0-4 only: the entry's partner field
@@ -344,15 +348,27 @@ __device__ __forceinline__ Conf apply_step(const Conf& c, float s, int T) {
   return o;
 }
 
-// Four warp sums at once (one butterfly, independent chains in flight).
+// Four warp sums at once, every lane getting all four.  Transposed butterfly:
+// the first two exchanges halve the values each lane carries (lanes with bit 4
+// clear keep a, b, the others c, d; then bit 3 picks one of the two), the last
+// three sum one value over a group of 8 lanes, and lanes 0, 8, 16, 24 hold a, b,
+// c, d: 10 shuffles and 6 adds instead of 20 and 20.
 __device__ __forceinline__ void warp_sum4(float& a, float& b, float& c, float& d) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(kFull, a, o);
-    b += __shfl_xor_sync(kFull, b, o);
-    c += __shfl_xor_sync(kFull, c, o);
-    d += __shfl_xor_sync(kFull, d, o);
-  }
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  float k0 = hi16 ? c : a, k1 = hi16 ? d : b;
+  const float s0 = hi16 ? a : c, s1 = hi16 ? b : d;
+  k0 += __shfl_xor_sync(kFull, s0, 16);
+  k1 += __shfl_xor_sync(kFull, s1, 16);
+  float k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(kFull, hi8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(kFull, k, 4);
+  k += __shfl_xor_sync(kFull, k, 2);
+  k += __shfl_xor_sync(kFull, k, 1);
+  a = __shfl_sync(kFull, k, 0);
+  b = __shfl_sync(kFull, k, 8);
+  c = __shfl_sync(kFull, k, 16);
+  d = __shfl_sync(kFull, k, 24);
 }
 
 // BFGS inverse-Hessian step after an accepted line search (Nocedal & Wright
@@ -498,7 +514,7 @@ __device__ __forceinline__ float3 site_start(const DevJob& J, const ChainStream&
 // evaluate.  The optimiser's iterate and the chain's current and best
 // conformations wait in shared memory; only the conformation under evaluation
 // and a few scalars stay in registers.
-template <int APL, int FMT>
+template <int APL, int FMT, int IU = 2>
 __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& W, int chain) {
   enum : int { kStart = 0, kTrial = 1, kBB = 2 };
   const int lane = threadIdx.x & 31;
@@ -543,7 +559,7 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
   uint32_t evals = 0;
   for (;;) {
     float gn;
-    const float en = eval_conf<APL, FMT>(M, L, R, W, xt, gn, DSDP_TERM_ALL);
+    const float en = eval_conf<APL, FMT, IU>(M, L, R, W, xt, gn, DSDP_TERM_ALL);
     ++evals;
     bool done = false;
     if (phase == kStart) {  // first evaluation of a local optimisation

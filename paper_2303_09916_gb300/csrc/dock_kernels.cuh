@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(32 * kMaxChainWarps, ChainOcc<VAR>::kMinBlocks
     }
     const LigView L = view_blob(smem);
     if (warp < tile.count) {
-      if (APLS == 1 || (APLS == 3 && L.n_atoms <= 32)) run_chain<1, FMT>(J, L, W, tile.chain0 + warp);
+      if (APLS == 1 || (APLS == 3 && L.n_atoms <= 32)) run_chain<1, FMT, APLS == 3 ? 1 : 2>(J, L, W, tile.chain0 + warp);
       else run_chain<2, FMT>(J, L, W, tile.chain0 + warp);
     }
     if (!persistent) break;

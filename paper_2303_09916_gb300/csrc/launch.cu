@@ -432,13 +432,18 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
   float best = 1e30f;
   int best_var = P->variant, best_pers = (P->flags & DSDP_PLAN_PERSISTENT) ? 1 : 0, best_w = P->warps_per_cta;
   dsdp_status s = DSDP_OK;
+  // the register budget is a choice only where a group runs one tile size: the
+  // kernel for mixed tiles is compiled once, at 128 registers
+  int n_var = 1;
+  for (const dsdp_plan::Group& g : P->groups)
+    if (g.apl_mask != 3) n_var = 2;
   for (int w = 1; w <= 4 && s == DSDP_OK; w *= 2) {
     e = plan_use_warps(P, w);
     if (e != cudaSuccess) {
       s = check_cuda(e, "autotune tiles");
       break;
     }
-  for (int var = 0; var < 2 && s == DSDP_OK; ++var)
+  for (int var = 0; var < n_var && s == DSDP_OK; ++var)
     for (int pers = 0; pers < 2 && s == DSDP_OK; ++pers) {
       P->variant = var;
       P->flags = base_flags | (pers ? DSDP_PLAN_PERSISTENT : 0u);
