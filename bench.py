@@ -56,8 +56,9 @@ def parse():
     p.add_argument("--sweep", action="store_true",
                    help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
     p.add_argument("--tile-config", type=int, default=-1,
-                   help="chain kernel launch configuration: -1 autotune (default); 1..6 fixed: register budget "
-                        "128 (odd) or 96 (even), 1 (1, 2), 2 (3, 4) or 4 (5, 6) chains per CTA")
+                   help="chain kernel launch configuration: -1 autotune (default); 1..12 fixed, numbered as the "
+                        "autotuner reports them: 1 + variant (0: 128 registers, 1: 96) + 2 work queue + 4 log2(chains "
+                        "per CTA)")
     return p.parse_args()
 
 
@@ -102,6 +103,17 @@ def systems(rank, batch):
         lig = synth.ligand(N_LIG, T_LIG, seed, center=rec.pocket_center)
         out.append((seed, rec, lig))
     return out
+
+
+def plan_tile_config(chosen):
+    """dsdp_plan_create's tile_config (1 + variant + 2 log2 W) of an autotuner choice."""
+    c = chosen - 1
+    return 1 + c % 2 + 2 * (c // 4)
+
+
+def plan_flags(dsdp, chosen):
+    """The plan flags of an autotuner choice: the persistent work queue or none."""
+    return dsdp.DSDP_PLAN_PERSISTENT if ((chosen - 1) // 2) % 2 else 0
 
 
 def describe_tile_config(chosen):
@@ -190,10 +202,12 @@ CHAIN_SOURCES = ["chain_device.cuh", "device_common.cuh", "dock_kernels.cuh", "d
                  "launch.h", "ligand_pack.cpp"]
 
 
-def chain_kernel_capture(batch, map_dtype):
+def chain_kernel_capture(batch, map_dtype, chain_kernel):
     """The committed ncu figures of the chain kernel (DRAM bytes per launch of the
     bench's workload, warp instructions per evaluation), or None when the kernel
-    sources changed since they were taken or the workload differs."""
+    sources changed since they were taken, the workload differs or this run's
+    launch configuration (register budget, chains per CTA, work queue) is not
+    the captured one."""
     import hashlib
 
     try:
@@ -207,7 +221,10 @@ def chain_kernel_capture(batch, map_dtype):
             h.update(f.read())
     if h.hexdigest() != rec.get("sources_sha256") or batch != rec.get("systems_per_launch") or map_dtype != "f32":
         return None
-    return rec
+    for cap in rec.get("captures", []):
+        if cap.get("chain_kernel") == chain_kernel:
+            return cap
+    return None
 
 
 def issue_peak_per_s(sm_mhz):
@@ -289,9 +306,8 @@ def run_device(args, rank, world, dev, dist):
         tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 2)  # register budget, chains per CTA, work queue
     else:
         dsdp.dsdp_plan_destroy(None, plan)
-        plan = dsdp.dsdp_plan_create(None, jobs, 0, args.tile_config)
-        # fixed configuration 1..6 (variant, chains per CTA) in the autotuner's numbering
-        tile_config = 1 + (args.tile_config - 1) % 2 + 4 * ((args.tile_config - 1) // 2)
+        plan = dsdp.dsdp_plan_create(None, jobs, plan_flags(dsdp, args.tile_config), plan_tile_config(args.tile_config))
+        tile_config = args.tile_config
     n_plan_kernels = dsdp.dsdp_plan_kernel_count(plan)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -836,7 +852,7 @@ def main():
     achieved_tflops = r["flops"] / per_launch_s / 1e12
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = fp32_peak_tflops(sm_mhz)
-    capture = chain_kernel_capture(args.batch, args.map_dtype)
+    capture = chain_kernel_capture(args.batch, args.map_dtype, describe_tile_config(r["tile_config"]))
     line = {
         "metric": "docked systems/s (typical-4k: 4k-atom receptor, 80^3 maps, 30-atom ligand, 384x40 MC+BFGS)",
         "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

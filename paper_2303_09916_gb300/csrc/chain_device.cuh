@@ -67,7 +67,8 @@ struct Conf {
 struct WarpScratch {
   float4* pre;     // [kMaxAtoms][2] inclusive prefix sums of (g, (r - p) x g): (gx, gy, gz, cx), (cy, cz, -, -)
   float* H;        // [6 + T][kHStride] BFGS inverse Hessian, row j owned by lane j
-  float* vec;      // [3][kHStride] vectors broadcast to the H rows: g', s, u (BFGS update)
+  float* vec;      // [5][kHStride] + 24: g', s, u broadcast to the H rows (BFGS update);
+                   // the chain's g and d; its ChainVars
   float* x;        // [7 + kMaxDim] local optimiser: current iterate (BFGS) / best iterate (BB)
   float* cur;      // [7 + kMaxDim] current conformation of the chain
   float* best;     // [7 + kMaxDim] best conformation of the chain
@@ -92,7 +93,7 @@ __host__ __device__ inline ScratchLayout scratch_layout(int n_atoms, int n_torsi
   l.pre = 0;
   l.H = l.pre + align16i(32 * n_atoms);
   l.vec = l.H + align16i(4 * kHStride * D);
-  l.x = l.vec + align16i(4 * 3 * kHStride);
+  l.x = l.vec + align16i(4 * (5 * kHStride + 24));
   l.cur = l.x + align16i(4 * kConfFloats);
   l.best = l.cur + align16i(4 * kConfFloats);
   l.bytes = l.best + align16i(4 * kConfFloats);
@@ -503,6 +504,23 @@ __device__ __forceinline__ float3 site_start(const DevJob& J, const ChainStream&
   return make_float3(__ldg(J.sites), __ldg(J.sites + 1), __ldg(J.sites + 2));
 }
 
+// Chain and optimiser variables that wait in shared memory while a
+// conformation is evaluated (read back through volatile loads, so that none of
+// them holds a register during the evaluation).
+struct ChainVars {
+  int phase, it, trial, step;
+  float e, gd, alpha, e_opt_best;
+  float e_cur, e_best;
+  uint32_t evals;
+  int T;
+  int bb, max_iters, n_steps;
+  float temperature;
+  float inv_gyr;
+  uint32_t seed_lo, seed_hi, chain;
+  float* trace;
+};
+static_assert(sizeof(ChainVars) <= 4 * 24, "ChainVars must fit its 24 words of the vec area");
+
 // One Monte Carlo chain (Sec. 2: one of many short independent copies; Vina's
 // mutation and Metropolis rules) with its local optimisations -- BFGS with
 // Armijo backtracking (Vina's optimiser; Nocedal & Wright Alg. 6.1) or
@@ -511,9 +529,9 @@ __device__ __forceinline__ float3 site_start(const DevJob& J, const ChainStream&
 //
 // The whole chain is one loop around a single score + gradient evaluation: a
 // small state machine decides, from each evaluation, the next conformation to
-// evaluate.  The optimiser's iterate and the chain's current and best
-// conformations wait in shared memory; only the conformation under evaluation
-// and a few scalars stay in registers.
+// evaluate.  Only the conformation under evaluation stays in registers across
+// an evaluation; the optimiser's vectors g and d, the chain's scalars and the
+// iterate / current / best conformations wait in shared memory.
 template <int APL, int FMT, int IU = 2>
 __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& W, int chain) {
   enum : int { kStart = 0, kTrial = 1, kBB = 2 };
@@ -521,13 +539,14 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
   const MapView M = make_map_view(J);
   LaneLig<APL> R;
   load_lane_lig<APL>(L, R);
-  const int T = L.T, nx = 7 + T, D = 6 + T;
-  const bool bb = J.optimizer == DSDP_OPT_BB;
-  const int max_iters = J.n_opt_iters;
-  const ChainStream rs{J.seed_lo, J.seed_hi, (uint32_t)chain};
-  // initial conformation: uniform word n of step 0 is word n % 4 of block n / 4
+  volatile float* const Vg = W.vec + 3 * kHStride;  // g, component `lane` (lane < kHStride)
+  volatile float* const Vd = W.vec + 4 * kHStride;  // search direction / step
+  volatile ChainVars& V = *reinterpret_cast<volatile ChainVars*>(W.vec + 5 * kHStride);
   Conf xt;
   {
+    const int T = L.T;
+    const ChainStream rs{J.seed_lo, J.seed_hi, (uint32_t)chain};
+    // initial conformation: uniform word n of step 0 is word n % 4 of block n / 4
     const uint4 b0 = rs.block(0, 0), b1 = rs.block(0, 1);
     xt.p = make_float3(__fmaf_rn(J.box_size[0], ChainStream::to_uniform(b0.x), J.box_lo[0]),
                        __fmaf_rn(J.box_size[1], ChainStream::to_uniform(b0.y), J.box_lo[1]),
@@ -546,21 +565,35 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
       th = kPiF - kTwoPiF * ChainStream::to_uniform(pick(bk, lane & 3));
     }
     xt.th = th;
+    // every lane writes the same values
+    V.phase = kStart;
+    V.it = V.trial = V.step = 0;
+    V.e = V.gd = V.e_opt_best = V.e_cur = V.e_best = 0.f;
+    V.alpha = 1.f;
+    V.evals = 0;
+    V.T = T;
+    V.bb = J.optimizer == DSDP_OPT_BB;
+    V.max_iters = J.n_opt_iters;
+    V.n_steps = J.n_steps;
+    V.temperature = J.temperature;
+    V.inv_gyr = 1.f / L.h->gyration_radius;
+    V.seed_lo = J.seed_lo;
+    V.seed_hi = J.seed_hi;
+    V.chain = (uint32_t)chain;
+    V.trace = J.trace ? J.trace + (size_t)chain * (J.n_steps + 1) * ((size_t)7 + T + 4) : nullptr;
+    if (lane < kHStride) Vg[lane] = Vd[lane] = 0.f;
+    __syncwarp();
   }
-  const size_t trace_stride = (size_t)nx + 4;
-  float* trace = J.trace ? J.trace + (size_t)chain * (J.n_steps + 1) * trace_stride : nullptr;
-  const float inv_gyr = 1.f / L.h->gyration_radius;
-  // optimiser state (warp-uniform except g and dir: component `lane`)
-  int phase = kStart, it = 0, trial = 0;
-  float e = 0.f, gd = 0.f, alpha = 1.f, g = 0.f, dir = 0.f, e_opt_best = 0.f;
-  // chain state
-  int step = 0;
-  float e_cur = 0.f, e_best = 0.f;
-  uint32_t evals = 0;
   for (;;) {
     float gn;
     const float en = eval_conf<APL, FMT, IU>(M, L, R, W, xt, gn, DSDP_TERM_ALL);
-    ++evals;
+    const int T = V.T, nx = 7 + T, D = 6 + T;
+    const bool bb = V.bb;
+    const int max_iters = V.max_iters;
+    int phase = V.phase, it = V.it, trial = V.trial;
+    float e = V.e, gd = V.gd, alpha = V.alpha, e_opt_best = V.e_opt_best;
+    float g = lane < kHStride ? Vg[lane] : 0.f, dir = lane < kHStride ? Vd[lane] : 0.f;
+    const uint32_t evals = V.evals + 1;
     bool done = false;
     if (phase == kStart) {  // first evaluation of a local optimisation
       e = en;
@@ -624,53 +657,65 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
         xt = apply_step(xt, dir, T);
       }
     }
-    if (!done) continue;
-    // ---- local optimisation finished: its result is W.x with energy eo
-    const float eo = (bb && max_iters > 0) ? e_opt_best : e;
-    __syncwarp();
-    if (step == 0) {
-      e_cur = e_best = eo;
-      if (lane < nx) {
-        W.cur[lane] = W.x[lane];
-        W.best[lane] = W.x[lane];
+    if (done) {
+      // ---- local optimisation finished: its result is W.x with energy eo
+      const float eo = (bb && max_iters > 0) ? e_opt_best : e;
+      const ChainStream rs{V.seed_lo, V.seed_hi, V.chain};
+      float* const trace = V.trace;
+      const size_t trace_stride = (size_t)nx + 4;
+      int step = V.step;
+      float e_cur = V.e_cur, e_best = V.e_best;
+      __syncwarp();
+      if (step == 0) {
+        e_cur = e_best = eo;
+        if (lane < nx) {
+          W.cur[lane] = W.x[lane];
+          W.best[lane] = W.x[lane];
+        }
+        if (trace) {
+          if (lane < nx) trace[lane] = W.x[lane];
+          if (lane == 0) {
+            trace[nx + 0] = e_cur;
+            trace[nx + 1] = e_cur;
+            trace[nx + 2] = -1.f;
+            trace[nx + 3] = 1.f;
+          }
+        }
+      } else {
+        const uint4 w0 = rs.block((uint32_t)step, 0);
+        const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
+        const float u = ChainStream::to_uniform(w0.y);
+        const bool accept = (eo < e_cur) || (u < expf(-(eo - e_cur) / V.temperature));
+        if (accept) {
+          e_cur = eo;
+          if (lane < nx) W.cur[lane] = W.x[lane];
+          if (eo < e_best) {
+            e_best = eo;
+            if (lane < nx) W.best[lane] = W.x[lane];
+          }
+        }
+        if (trace) {
+          float* t = trace + (size_t)step * trace_stride;
+          if (lane < nx) t[lane] = W.cur[lane];
+          if (lane == 0) {
+            t[nx + 0] = eo;
+            t[nx + 1] = e_cur;
+            t[nx + 2] = (float)mode;
+            t[nx + 3] = accept ? 1.f : 0.f;
+          }
+        }
       }
-      if (trace) {
-        if (lane < nx) trace[lane] = W.x[lane];
+      __syncwarp();
+      if (++step > V.n_steps) {
+        if (lane < nx) J.chain_best_conf[(size_t)chain * nx + lane] = W.best[lane];
         if (lane == 0) {
-          trace[nx + 0] = e_cur;
-          trace[nx + 1] = e_cur;
-          trace[nx + 2] = -1.f;
-          trace[nx + 3] = 1.f;
+          J.chain_best_e[chain] = e_best;
+          J.chain_evals[chain] = evals;
         }
+        __syncwarp();
+        return;
       }
-    } else {
-      const uint4 w0 = rs.block((uint32_t)step, 0);
-      const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
-      const float u = ChainStream::to_uniform(w0.y);
-      const bool accept = (eo < e_cur) || (u < expf(-(eo - e_cur) / J.temperature));
-      if (accept) {
-        e_cur = eo;
-        if (lane < nx) W.cur[lane] = W.x[lane];
-        if (eo < e_best) {
-          e_best = eo;
-          if (lane < nx) W.best[lane] = W.x[lane];
-        }
-      }
-      if (trace) {
-        float* t = trace + (size_t)step * trace_stride;
-        if (lane < nx) t[lane] = W.cur[lane];
-        if (lane == 0) {
-          t[nx + 0] = eo;
-          t[nx + 1] = e_cur;
-          t[nx + 2] = (float)mode;
-          t[nx + 3] = accept ? 1.f : 0.f;
-        }
-      }
-    }
-    __syncwarp();
-    if (++step > J.n_steps) break;
-    // ---- mutation of the current conformation (the next local optimisation's start)
-    {
+      // ---- mutation of the current conformation (the next local optimisation's start)
       const uint4 w0 = rs.block((uint32_t)step, 0);
       const int mode = (int)(((unsigned long long)(w0.x >> 8) * (unsigned long long)(2 + T)) >> 24);
       xt = load_conf(W.cur, T);
@@ -679,20 +724,30 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
         xt.p = xt.p + kMutationAmplitude * b;
       } else if (mode == 1) {
         const float3 b = unit_ball(rs, (uint32_t)step);
-        const float k = kMutationAmplitude * inv_gyr;
+        const float k = kMutationAmplitude * V.inv_gyr;
         xt.q = qnormalize(qmul(quat_from_rotvec(k * b.x, k * b.y, k * b.z), xt.q));
       } else if (lane == 6 + (mode - 2)) {
         xt.th = kPiF - kTwoPiF * ChainStream::to_uniform(w0.z);
       }
       phase = kStart;
+      V.step = step;
+      V.e_cur = e_cur;
+      V.e_best = e_best;
     }
+    V.phase = phase;
+    V.it = it;
+    V.trial = trial;
+    V.e = e;
+    V.gd = gd;
+    V.alpha = alpha;
+    V.e_opt_best = e_opt_best;
+    V.evals = evals;
+    if (lane < kHStride) {
+      Vg[lane] = g;
+      Vd[lane] = dir;
+    }
+    __syncwarp();
   }
-  if (lane < nx) J.chain_best_conf[(size_t)chain * nx + lane] = W.best[lane];
-  if (lane == 0) {
-    J.chain_best_e[chain] = e_best;
-    J.chain_evals[chain] = evals;
-  }
-  __syncwarp();
 }
 
 }  // namespace dsdp

@@ -52,3 +52,23 @@ def test_single_process_is_the_identity():
     assert bench.max_over_ranks(None, 7.0, "cpu") == 7.0
     assert bench.sum_over_ranks(None, 3.0, "cpu") == 3.0
     assert bench.job_throughput(1, 16, 10, 500.0) == pytest.approx(320.0)
+
+
+def test_fixed_tile_config_numbering():
+    """bench.py --tile-config takes the autotuner's numbering (1 + variant + 2
+    work queue + 4 log2 W); each maps back to the plan's tile_config (1 +
+    variant + 2 log2 W) and flags, and to its description."""
+
+    class Flags:
+        DSDP_PLAN_PERSISTENT = 1
+
+    seen = set()
+    for chosen in range(1, 13):
+        var, queue, w = (chosen - 1) % 2, ((chosen - 1) // 2) % 2, 1 << ((chosen - 1) // 4)
+        tc = bench.plan_tile_config(chosen)
+        assert 1 <= tc <= 6 and (tc - 1) % 2 == var and 1 << ((tc - 1) // 2) == w
+        assert bench.plan_flags(Flags, chosen) == (1 if queue else 0)
+        text = bench.describe_tile_config(chosen)
+        assert text.startswith(f"{(128, 96)[var]} regs, {w} chain") and text.endswith("work queue") == bool(queue)
+        seen.add((tc, queue))
+    assert len(seen) == 12
