@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--optimizer", default="bfgs", choices=["bfgs", "bb"])
     p.add_argument("--map-dtype", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=6)
     p.add_argument("--serve", action="store_true",
                    help="run the serving workload (Poisson arrivals, 8 receptors) and print its JSON line instead")
     p.add_argument("--serve-requests", type=int, default=4000)
@@ -55,6 +55,8 @@ def parse():
                    help="skip the one-job-per-launch and uneven-batch (CUDA graph) measurements")
     p.add_argument("--sweep", action="store_true",
                    help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
+    p.add_argument("--no-pipeline", dest="pipeline", action="store_false",
+                   help="time the device-resident steps on one stream only (no overlap of consecutive steps)")
     p.add_argument("--tile-config", type=int, default=-1,
                    help="chain kernel launch configuration: -1 autotune (default); 1..12 fixed, numbered as the "
                         "autotuner reports them: 1 + variant (0: 128 registers, 1: 96) + 2 work queue + 4 log2(chains "
@@ -239,6 +241,13 @@ def fp32_peak_tflops(sm_mhz):
 
 # ---------------------------------------------------------------- device-resident path
 def run_device(args, rank, world, dev, dist):
+    """The device-resident step (grid builds, chains, FP64 rescoring + top-k of
+    args.batch systems), timed twice: serially on one stream (stage times and the
+    kernel rooflines come from this pass) and pipelined, consecutive steps
+    alternating between two streams with their own maps and outputs so that a
+    step's grid builds and chains fill the SMs the previous step's last wave of
+    chains leaves idle (the headline throughput; each step still does all of its
+    work)."""
     import torch
     from paper_2303_09916_gb300 import dsdp
 
@@ -248,87 +257,97 @@ def run_device(args, rank, world, dev, dist):
     dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
     opt = dsdp.DSDP_OPT_BFGS if args.optimizer == "bfgs" else dsdp.DSDP_OPT_BB
     sysl = systems(rank, args.batch)
-    keep = []
-    jobs = []
-    boxes = []
-    lig_info = []
+    shared = []  # per system: receptor, ligand blob, box and grid geometry (read-only, shared by the slots)
     for seed, rec, lig in sysl:
         box = dsdp.make_box(rec.pocket_center, BOX, SPACING)
-        boxes.append(box)
-        nbytes = dsdp.dsdp_grid_map_bytes(box, dtype, dsdp.DSDP_GRID_EQ4)
-        d_maps = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-        d_xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
-        d_type = torch.from_numpy(rec.xs_type.copy()).to(dev)
         blob = dsdp.dsdp_ligand_pack(lig)
-        info = dsdp.dsdp_ligand_blob_info(blob)
-        lig_info.append(info)
-        d_blob = torch.from_numpy(blob.copy()).to(dev)
-        nx = 7 + info["n_torsions"]
-        outs = dict(conf=torch.empty((N_CHAINS, nx), dtype=torch.float32, device=dev),
-                    e=torch.empty(N_CHAINS, dtype=torch.float32, device=dev),
-                    evals=torch.zeros(N_CHAINS, dtype=torch.int32, device=dev),
-                    n=torch.zeros(1, dtype=torch.int32, device=dev),
-                    chain=torch.zeros(TOP_K, dtype=torch.int32, device=dev),
-                    score=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
-                    inter=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
-                    intra=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
-                    oconf=torch.zeros((TOP_K, nx), dtype=torch.float64, device=dev),
-                    coords=torch.zeros((TOP_K, N_LIG, 3), dtype=torch.float32, device=dev))
         n = [int(np.ceil(BOX / SPACING))] * 3
-        origin = [rec.pocket_center[a] - (n[a] - 1) * SPACING / 2 for a in range(3)]
-        j = dsdp.dsdp_job_device()
-        j.grid = dsdp.grid_view(d_maps.data_ptr(), n, origin, SPACING, dtype, dsdp.DSDP_GRID_EQ4)
-        j.receptor = dsdp.dsdp_receptor(N_REC, d_xyz.data_ptr(), d_type.data_ptr())
-        j.h_blob = blob.ctypes.data
-        j.d_blob = d_blob.data_ptr()
-        j.params = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=N_STEPS, n_opt_iters=N_ITERS, optimizer=opt,
-                                    seed=seed, top_k=TOP_K)
-        for a in range(3):
-            j.box_lo[a] = rec.pocket_center[a] - BOX / 2
-            j.box_size[a] = BOX
-        j.d_chain_best_conf = outs["conf"].data_ptr()
-        j.d_chain_best_e = outs["e"].data_ptr()
-        j.d_chain_evals = outs["evals"].data_ptr()
-        j.d_out_n = outs["n"].data_ptr()
-        j.d_out_chain = outs["chain"].data_ptr()
-        j.d_out_score = outs["score"].data_ptr()
-        j.d_out_inter = outs["inter"].data_ptr()
-        j.d_out_intra = outs["intra"].data_ptr()
-        j.d_out_conf = outs["oconf"].data_ptr()
-        j.d_out_coords = outs["coords"].data_ptr()
-        jobs.append(j)
-        keep.append((d_maps, d_xyz, d_type, blob, d_blob, outs))
-    plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
-    for (d_maps, d_xyz, d_type, *_), box in zip(keep, boxes):
-        dsdp.dsdp_grid_build_device(N_REC, d_xyz.data_ptr(), d_type.data_ptr(), box, dtype, dsdp.DSDP_GRID_EQ4,
-                                    d_maps.data_ptr(), d_maps.numel(), sptr)
+        shared.append(dict(seed=seed, rec=rec, box=box, blob=blob, info=dsdp.dsdp_ligand_blob_info(blob),
+                           d_xyz=torch.from_numpy(rec.xyz.copy()).to(dev),
+                           d_type=torch.from_numpy(rec.xs_type.copy()).to(dev),
+                           d_blob=torch.from_numpy(blob.copy()).to(dev), n=n,
+                           origin=[rec.pocket_center[a] - (n[a] - 1) * SPACING / 2 for a in range(3)],
+                           nbytes=dsdp.dsdp_grid_map_bytes(box, dtype, dsdp.DSDP_GRID_EQ4)))
+    lig_info = [sh["info"] for sh in shared]
+
+    def make_slot():
+        """Maps, outputs and job descriptors of one in-flight step."""
+        jobs, maps, outs_l = [], [], []
+        for sh in shared:
+            rec = sh["rec"]
+            d_maps = torch.empty(sh["nbytes"], dtype=torch.uint8, device=dev)
+            nx = 7 + sh["info"]["n_torsions"]
+            outs = dict(conf=torch.empty((N_CHAINS, nx), dtype=torch.float32, device=dev),
+                        e=torch.empty(N_CHAINS, dtype=torch.float32, device=dev),
+                        evals=torch.zeros(N_CHAINS, dtype=torch.int32, device=dev),
+                        n=torch.zeros(1, dtype=torch.int32, device=dev),
+                        chain=torch.zeros(TOP_K, dtype=torch.int32, device=dev),
+                        score=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                        inter=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                        intra=torch.zeros(TOP_K, dtype=torch.float64, device=dev),
+                        oconf=torch.zeros((TOP_K, nx), dtype=torch.float64, device=dev),
+                        coords=torch.zeros((TOP_K, N_LIG, 3), dtype=torch.float32, device=dev))
+            j = dsdp.dsdp_job_device()
+            j.grid = dsdp.grid_view(d_maps.data_ptr(), sh["n"], sh["origin"], SPACING, dtype, dsdp.DSDP_GRID_EQ4)
+            j.receptor = dsdp.dsdp_receptor(N_REC, sh["d_xyz"].data_ptr(), sh["d_type"].data_ptr())
+            j.h_blob = sh["blob"].ctypes.data
+            j.d_blob = sh["d_blob"].data_ptr()
+            j.params = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=N_STEPS, n_opt_iters=N_ITERS, optimizer=opt,
+                                        seed=sh["seed"], top_k=TOP_K)
+            for a in range(3):
+                j.box_lo[a] = rec.pocket_center[a] - BOX / 2
+                j.box_size[a] = BOX
+            j.d_chain_best_conf = outs["conf"].data_ptr()
+            j.d_chain_best_e = outs["e"].data_ptr()
+            j.d_chain_evals = outs["evals"].data_ptr()
+            j.d_out_n = outs["n"].data_ptr()
+            j.d_out_chain = outs["chain"].data_ptr()
+            j.d_out_score = outs["score"].data_ptr()
+            j.d_out_inter = outs["inter"].data_ptr()
+            j.d_out_intra = outs["intra"].data_ptr()
+            j.d_out_conf = outs["oconf"].data_ptr()
+            j.d_out_coords = outs["coords"].data_ptr()
+            jobs.append(j)
+            maps.append(d_maps)
+            outs_l.append(outs)
+        return dict(jobs=jobs, maps=maps, outs=outs_l)
+
+    def build_grids(slot, st):
+        for sh, d_maps in zip(shared, slot["maps"]):
+            dsdp.dsdp_grid_build_device(N_REC, sh["d_xyz"].data_ptr(), sh["d_type"].data_ptr(), sh["box"], dtype,
+                                        dsdp.DSDP_GRID_EQ4, d_maps.data_ptr(), d_maps.numel(), st)
+
+    slots = [make_slot() for _ in range(2 if args.pipeline else 1)]
+    plan = dsdp.dsdp_plan_create(None, slots[0]["jobs"], 0, 0)
+    build_grids(slots[0], sptr)
     if args.tile_config < 0:
         tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 2)  # register budget, chains per CTA, work queue
     else:
         dsdp.dsdp_plan_destroy(None, plan)
-        plan = dsdp.dsdp_plan_create(None, jobs, plan_flags(dsdp, args.tile_config), plan_tile_config(args.tile_config))
+        plan = dsdp.dsdp_plan_create(None, slots[0]["jobs"], plan_flags(dsdp, args.tile_config),
+                                     plan_tile_config(args.tile_config))
         tile_config = args.tile_config
+    plans = [plan] + [dsdp.dsdp_plan_create(None, sl["jobs"], plan_flags(dsdp, tile_config), plan_tile_config(tile_config))
+                      for sl in slots[1:]]
     n_plan_kernels = dsdp.dsdp_plan_kernel_count(plan)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    flushes = [torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev) for _ in slots]  # > 129 MB L2
 
-    def step(evs=None):
+    def step(i, st, evs=None):
         if evs:
-            evs[0].record(stream)
-        for (d_maps, d_xyz, d_type, *_), box in zip(keep, boxes):
-            dsdp.dsdp_grid_build_device(N_REC, d_xyz.data_ptr(), d_type.data_ptr(), box, dtype, dsdp.DSDP_GRID_EQ4,
-                                        d_maps.data_ptr(), d_maps.numel(), sptr)
+            evs[0].record(torch.cuda.current_stream())
+        build_grids(slots[i], st)
         if evs:
-            evs[1].record(stream)
-        dsdp.dsdp_plan_launch_stage(plan, dsdp.DSDP_STAGE_CHAINS, sptr)
+            evs[1].record(torch.cuda.current_stream())
+        dsdp.dsdp_plan_launch_stage(plans[i], dsdp.DSDP_STAGE_CHAINS, st)
         if evs:
-            evs[2].record(stream)
-        dsdp.dsdp_plan_launch_stage(plan, dsdp.DSDP_STAGE_RESCORE, sptr)
+            evs[2].record(torch.cuda.current_stream())
+        dsdp.dsdp_plan_launch_stage(plans[i], dsdp.DSDP_STAGE_RESCORE, st)
         if evs:
-            evs[3].record(stream)
+            evs[3].record(torch.cuda.current_stream())
 
     for _ in range(args.warmup):
-        flush.zero_()
-        step()
+        flushes[0].zero_()
+        step(0, sptr)
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -337,23 +356,53 @@ def run_device(args, rank, world, dev, dist):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # serial pass: one stream, stage events
     t0.record(stream)
     for k in range(args.steps):
-        flush.zero_()
-        step(evs[k])
+        flushes[0].zero_()
+        step(0, sptr, evs[k])
     t1.record(stream)
     torch.cuda.synchronize()
+    serial_ms = max_over_ranks(dist, t0.elapsed_time(t1), dev)
+    elapsed_ms = serial_ms
+    if args.pipeline:
+        # pipelined pass: step k on stream k % 2 with slot k % 2
+        streams = [torch.cuda.Stream(device=dev) for _ in slots]
+        for k in range(2):  # untimed: one step per slot and stream
+            with torch.cuda.stream(streams[k]):
+                flushes[k].zero_()
+                step(k, streams[k].cuda_stream)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        p0.record(stream)
+        for s in streams:
+            s.wait_event(p0)
+        for k in range(args.steps):
+            i = k % 2
+            with torch.cuda.stream(streams[i]):
+                flushes[i].zero_()
+                step(i, streams[i].cuda_stream)
+        for s in streams:
+            stream.wait_stream(s)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        elapsed_ms = max_over_ranks(dist, p0.elapsed_time(p1), dev)
     clk = clocks.stop()
-    elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), dev)
     grid_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     chain_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     rescore_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
-    evals = [int(o["evals"].sum().item()) for *_, o in keep]
+    evals = [int(o["evals"].sum().item()) for o in slots[0]["outs"]]
     total_evals = sum(evals)
+    # every slot docked the same systems with the same seeds: the same evaluations
+    same = all([int(o["evals"].sum().item()) for o in sl["outs"]] == evals for sl in slots[1:])
     flops = sum(ev * flops_per_eval(li["n_atoms"], li["n_pairs"], li["n_bodies"]) for ev, li in zip(evals, lig_info))
     gather_bytes = sum(ev * li["n_atoms"] * (128 if dtype == 0 else 64) for ev, li in zip(evals, lig_info))
-    results_ok = all(int(o["n"].item()) >= 1 and bool(torch.isfinite(o["score"][: int(o["n"].item())]).all())
-                     for *_, o in keep)
+    results_ok = same and all(int(o["n"].item()) >= 1 and bool(torch.isfinite(o["score"][: int(o["n"].item())]).all())
+                              for sl in slots for o in sl["outs"])
+    jobs = slots[0]["jobs"]
     # gather microbenchmark on the first system's maps (the L2-gather roofline)
     g_view = jobs[0].grid
     npts = 1 << 20
@@ -373,8 +422,10 @@ def run_device(args, rank, world, dev, dist):
     gb.record(stream)
     torch.cuda.synchronize()
     gather_gbs = 5 * npts * reps * (128 if dtype == 0 else 64) / (ga.elapsed_time(gb) * 1e-3) / 1e9
-    dsdp.dsdp_plan_destroy(None, plan)
-    return dict(tile_config=tile_config, elapsed_ms=elapsed_ms, grid_ms=grid_ms, chain_ms=chain_ms, rescore_ms=rescore_ms,
+    for pl in plans:
+        dsdp.dsdp_plan_destroy(None, pl)
+    return dict(tile_config=tile_config, elapsed_ms=elapsed_ms, serial_ms=serial_ms, grid_ms=grid_ms, chain_ms=chain_ms,
+                rescore_ms=rescore_ms,
                 total_evals=total_evals, flops=flops, gather_bytes=gather_bytes, clocks=clk,
                 launches_per_step=args.batch + n_plan_kernels, results_ok=results_ok, gather_gbs=gather_gbs)
 
@@ -690,14 +741,14 @@ def run_e2e(args, rank, dev):
     opt = dsdp.DSDP_OPT_BFGS if args.optimizer == "bfgs" else dsdp.DSDP_OPT_BB
     sysl = systems(rank, args.batch)
     blob_bytes = {seed: len(dsdp.dsdp_ligand_pack(lig)) for seed, rec, lig in sysl}  # counted, not timed
-    ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, args.batch))
+    window = 2 if args.pipeline else 1  # steps in flight: the next step is submitted before this one is read back
+    ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, window * args.batch))
     h2d = d2h = 0
     latencies = []
     try:
-        def one_step(count):
-            nonlocal h2d, d2h
-            t_sub = {}
-            grids, jids, bufs = [], [], []
+        def submit_step(count):
+            nonlocal h2d
+            t_sub, grids, jids, bufs = {}, [], [], []
             for seed, rec, lig in sysl:
                 box = dsdp.make_box(rec.pocket_center, BOX, SPACING)
                 t_sub[seed] = time.perf_counter()
@@ -709,6 +760,11 @@ def run_e2e(args, rank, dev):
                 bufs.append(dsdp.result_buffers(lig.n_atoms, lig.n_torsions, params))
                 if count:
                     h2d += rec.xyz.nbytes + rec.xs_type.nbytes + blob_bytes[seed]
+            return t_sub, grids, jids, bufs
+
+        def finish_step(st, count):
+            nonlocal d2h
+            t_sub, grids, jids, bufs = st
             for (seed, *_), j, b in zip(sysl, jids, bufs):
                 r = dsdp.dsdp_dock_poll(ctx, j, b, wait_ms=-1)
                 if count:
@@ -718,11 +774,16 @@ def run_e2e(args, rank, dev):
             for g in grids:
                 dsdp.dsdp_grid_free(ctx, g)
 
-        one_step(False)
+        finish_step(submit_step(False), False)
         torch.cuda.synchronize()
         t = time.perf_counter()
+        inflight = []
         for _ in range(args.e2e_steps):
-            one_step(True)
+            inflight.append(submit_step(True))
+            if len(inflight) == window:
+                finish_step(inflight.pop(0), True)
+        while inflight:
+            finish_step(inflight.pop(0), True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
     finally:
@@ -861,8 +922,13 @@ def main():
         "config": {"workload": "typical-4k", "systems_per_step": args.batch, "receptor_atoms": N_REC,
                    "grid": "80^3 x 8", "map_dtype": args.map_dtype, "ligand": f"{N_LIG} atoms / {T_LIG} torsions",
                    "chains": N_CHAINS, "mc_steps": N_STEPS, "opt_iters": N_ITERS, "optimizer": args.optimizer,
-                   "top_k": TOP_K, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
-                   "chain_kernel": describe_tile_config(r["tile_config"])},
+                   "top_k": TOP_K, "l2": "flushed before each step (256 MB write on the step's stream); each step builds 2.1 GB of maps", "parallelism": f"replicas x{world}",
+                   "chain_kernel": describe_tile_config(r["tile_config"]),
+                   "pipeline": ("2 streams: consecutive steps overlap (own maps and outputs per stream)"
+                                if args.pipeline else "none: steps back to back on one stream")},
+        "serial": {"value": job_throughput(world, args.batch, args.steps, r["serial_ms"]),
+                   "ms_per_step": r["serial_ms"] / args.steps,
+                   "note": "the same steps on one stream (stage_ms and the rooflines are from this pass)"},
         "evals_per_s": world * r["total_evals"] * args.steps / (r["elapsed_ms"] * 1e-3),
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
         "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,
