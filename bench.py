@@ -9,9 +9,16 @@ systems, each with its own receptor, end to end: grid build, chains, FP64
 rescoring and top-k.
 
   value  systems/s with inputs resident on the device (device-pointer API,
-         caller-owned memory), timed with CUDA events over exactly K steps
-  e2e    systems/s through the host API (dsdp_grid_build / dsdp_dock_submit /
-         dsdp_dock_poll) with host arrays, copies included
+         caller-owned memory), timed with CUDA events over exactly K steps;
+         consecutive steps alternate between two streams, each with its own
+         maps, outputs and plan, so that a step's grid builds and chains fill
+         the SMs the previous step's last wave of chains leaves idle
+         (--no-pipeline: one stream).  `serial` is the same K steps on one
+         stream; the stage times and rooflines come from that pass
+  e2e    systems/s through the host API (dsdp_grid_build / dsdp_dock_submit_many
+         / dsdp_dock_poll) with host arrays, copies included; two steps in
+         flight (the next step's requests go in before this step's results
+         are read back)
   --impl reference   the FP64 CPU oracle on the host cores (whole systems)
 
 N > 1 (torchrun): independent replicas, one per GPU; value sums all ranks'
@@ -47,6 +54,9 @@ def parse():
     p.add_argument("--map-dtype", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=6)
+    p.add_argument("--e2e-batch-chains", type=int, default=-1,
+                   help="the host API's largest batch in chains (dsdp_create_params.max_batch_chains): -1 = one "
+                        "step's chains (default), 0 = the library's default")
     p.add_argument("--serve", action="store_true",
                    help="run the serving workload (Poisson arrivals, 8 receptors) and print its JSON line instead")
     p.add_argument("--serve-requests", type=int, default=4000)
@@ -742,24 +752,29 @@ def run_e2e(args, rank, dev):
     sysl = systems(rank, args.batch)
     blob_bytes = {seed: len(dsdp.dsdp_ligand_pack(lig)) for seed, rec, lig in sysl}  # counted, not timed
     window = 2 if args.pipeline else 1  # steps in flight: the next step is submitted before this one is read back
-    ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, window * args.batch))
+    batch_chains = args.batch * N_CHAINS if args.e2e_batch_chains < 0 else args.e2e_batch_chains
+    ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, window * args.batch),
+                           max_batch_chains=batch_chains)
     h2d = d2h = 0
     latencies = []
     try:
         def submit_step(count):
+            # the step's grids are queued first (asynchronous builds), then its
+            # jobs in one dsdp_dock_submit_many call (ligands packed on several
+            # host threads, queued together: the runtime takes them in few batches)
             nonlocal h2d
-            t_sub, grids, jids, bufs = {}, [], [], []
+            t_sub, grids, jids, bufs, params = {}, [], [], [], []
             for seed, rec, lig in sysl:
                 box = dsdp.make_box(rec.pocket_center, BOX, SPACING)
                 t_sub[seed] = time.perf_counter()
-                g = dsdp.dsdp_grid_build(ctx, rec.xyz, rec.xs_type, box, dtype, dsdp.DSDP_GRID_EQ4)
-                params = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=N_STEPS, n_opt_iters=N_ITERS, optimizer=opt,
-                                          seed=seed, top_k=TOP_K)
-                jids.append(dsdp.dsdp_dock_submit(ctx, g, lig, params))
-                grids.append(g)
-                bufs.append(dsdp.result_buffers(lig.n_atoms, lig.n_torsions, params))
+                grids.append(dsdp.dsdp_grid_build(ctx, rec.xyz, rec.xs_type, box, dtype, dsdp.DSDP_GRID_EQ4))
+                p = dsdp.make_params(n_chains=N_CHAINS, n_mc_steps=N_STEPS, n_opt_iters=N_ITERS, optimizer=opt,
+                                     seed=seed, top_k=TOP_K)
+                params.append(p)
+                bufs.append(dsdp.result_buffers(lig.n_atoms, lig.n_torsions, p))
                 if count:
                     h2d += rec.xyz.nbytes + rec.xs_type.nbytes + blob_bytes[seed]
+            jids = dsdp.dsdp_dock_submit_many(ctx, grids, [lig for _, _, lig in sysl], params)
             return t_sub, grids, jids, bufs
 
         def finish_step(st, count):
@@ -776,6 +791,7 @@ def run_e2e(args, rank, dev):
 
         finish_step(submit_step(False), False)
         torch.cuda.synchronize()
+        batches0 = dsdp.dsdp_get_stats(ctx)["batches"]
         t = time.perf_counter()
         inflight = []
         for _ in range(args.e2e_steps):
@@ -786,10 +802,12 @@ def run_e2e(args, rank, dev):
             finish_step(inflight.pop(0), True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
+        batches = dsdp.dsdp_get_stats(ctx)["batches"] - batches0
     finally:
         dsdp.dsdp_destroy(ctx)
     return dict(value=args.e2e_steps * args.batch / dt, h2d=h2d // args.e2e_steps, d2h=d2h // args.e2e_steps,
-                p50_ms=1e3 * float(np.percentile(latencies, 50)), p99_ms=1e3 * float(np.percentile(latencies, 99)))
+                p50_ms=1e3 * float(np.percentile(latencies, 50)), p99_ms=1e3 * float(np.percentile(latencies, 99)),
+                batches_per_step=batches / args.e2e_steps)
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -952,7 +970,7 @@ def main():
     if e2e:
         line["e2e"] = {"value": e2e["value"], "unit": "systems/s", "h2d_bytes_per_step": e2e["h2d"],
                        "d2h_bytes_per_step": e2e["d2h"], "latency_p50_ms": e2e["p50_ms"],
-                       "latency_p99_ms": e2e["p99_ms"]}
+                       "latency_p99_ms": e2e["p99_ms"], "batches_per_step": e2e["batches_per_step"]}
     if single:
         line["forms"] = {"batched_plan": {"systems_per_s": value, "note": f"{args.batch} systems per launch"},
                          "one_job_per_launch": single,

@@ -198,12 +198,13 @@ typedef struct {
   dsdp_alloc_fn alloc;        /* NULL = cudaMallocAsync */
   dsdp_free_fn free;
   void* alloc_user;
+  int32_t max_batch_chains;   /* chains of one batch at most; 0 = 64 x the SM count */
 } dsdp_create_params;
 
 /* Create a context: owns streams, the job table and a progress thread that
  * admits queued jobs as device memory and slots free up (continuous
  * batching): whenever a stream is free, every queued job that fits (in
- * order; at most 64 x the SM count chains) is launched as one batch, a
+ * order; at most max_batch_chains chains) is launched as one batch, a
  * multi-job plan whose chains share one work queue, while earlier batches
  * drain on the other streams.  Thread-safe: any thread may call any function
  * on a ctx. */
@@ -254,6 +255,15 @@ dsdp_status dsdp_score_eval(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_lig
  * The grid must outlive the job. */
 dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_ligand* ligand,
                              const dsdp_dock_params* params, uint64_t* job_id);
+/* Submit n jobs at once (virtual screening: many ligands, one or a few
+ * grids): grids[i], ligands[i] and params[i] as for dsdp_dock_submit; job_ids
+ * receives n ids.  The ligands are packed on up to 8 host threads, then all n
+ * jobs are queued together, so the progress thread can take them in one batch
+ * (as many as max_batch_chains admits).  All or none: on any error no job is
+ * queued and the message names the first failing index.  Arrays are borrowed
+ * for the call. */
+dsdp_status dsdp_dock_submit_many(dsdp_ctx* ctx, int32_t n, const dsdp_grid* const* grids,
+                                  const dsdp_ligand* ligands, const dsdp_dock_params* params, uint64_t* job_ids);
 /* Wait up to wait_ms (0: do not block, < 0: forever) for a job.  DSDP_PENDING
  * while it runs; on DSDP_OK the results are copied into `out` and the job is
  * released (a second poll returns DSDP_ERR_NOT_FOUND).  A job that failed
@@ -267,6 +277,7 @@ typedef struct {
   uint64_t submitted, completed, failed, cancelled;
   int32_t queued, running;
   uint64_t bytes_in_use, bytes_budget;
+  uint64_t batches; /* batches launched (multi-job plans), since dsdp_create */
 } dsdp_stats;
 dsdp_status dsdp_get_stats(dsdp_ctx* ctx, dsdp_stats* out);
 

@@ -88,7 +88,7 @@ struct dsdp_ctx {
   uint64_t budget = 0;
   uint64_t in_use = 0;
   int max_inflight = 16;
-  int max_batch_chains = 0;            // chains per batch: 4 x the resident chain slots
+  int max_batch_chains = 0;            // chains per batch (default 64 per SM)
   std::vector<cudaStream_t> streams;   // one batch in flight per stream
   cudaStream_t sync_stream = nullptr;   // synchronous calls and grid builds
   cudaStream_t upload_stream = nullptr; // receptor uploads of grid builds (copy engines only)
@@ -442,6 +442,7 @@ void progress_loop(dsdp_ctx* ctx) {
       Batch* b = batch_launch(ctx, take, stream);
       if (b) {
         ctx->batches.push_back(b);
+        ctx->stats.batches++;
       } else {
         // a batch-wide failure: isolate it by running the jobs one by one
         const std::string why = dsdp_last_error();
@@ -449,6 +450,7 @@ void progress_loop(dsdp_ctx* ctx) {
           Batch* one = batch_launch(ctx, {j}, stream);
           if (one) {
             ctx->batches.push_back(one);
+            ctx->stats.batches++;
             continue;
           }
           job_fail(ctx, j, DSDP_ERR_DEVICE, why + "; alone: " + dsdp_last_error());
@@ -482,6 +484,7 @@ extern "C" dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** 
   if (p.device < 0 || p.device >= n_dev) return set_error(DSDP_ERR_INVALID_ARG, "device %d of %d", p.device, n_dev);
   if ((p.alloc == nullptr) != (p.free == nullptr))
     return set_error(DSDP_ERR_INVALID_ARG, "alloc and free callbacks go together");
+  if (p.max_batch_chains < 0) return set_error(DSDP_ERR_INVALID_ARG, "max_batch_chains < 0");
   e = cudaSetDevice(p.device);
   if (e != cudaSuccess) return check_cuda(e, "cudaSetDevice");
   int major = 0, minor = 0;
@@ -497,7 +500,7 @@ extern "C" dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** 
   cudaMemGetInfo(&free_b, &total_b);
   ctx->budget = p.mem_budget_bytes ? p.mem_budget_bytes : (uint64_t)(0.8 * (double)free_b);
   ctx->max_inflight = p.max_inflight_jobs > 0 ? p.max_inflight_jobs : 16;
-  ctx->max_batch_chains = 4 * 16 * ctx->sms;  // 16 resident chains (warps) per SM
+  ctx->max_batch_chains = p.max_batch_chains > 0 ? p.max_batch_chains : 4 * 16 * ctx->sms;
   const int ns = p.n_streams > 0 ? p.n_streams : 4;
   for (int i = 0; i < ns; ++i) {
     cudaStream_t s;
@@ -882,9 +885,14 @@ extern "C" dsdp_status dsdp_score_eval(dsdp_ctx* ctx, const dsdp_grid* grid, con
 }
 
 // ------------------------------------------------------------------ docking
-extern "C" dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_ligand* ligand,
-                                        const dsdp_dock_params* params, uint64_t* job_id) {
-  if (!ctx || !grid || !job_id) return set_error(DSDP_ERR_INVALID_ARG, "ctx/grid/job_id NULL");
+// A job from its arguments: parameters normalised, ligand packed, binding-site
+// points copied behind the blob, result layout computed.  Touches no ctx
+// state, so several threads may build jobs at once; on failure the message is
+// in this thread's dsdp_last_error().
+static dsdp_status job_build(const dsdp_grid* grid, const dsdp_ligand* ligand, const dsdp_dock_params* params,
+                             Job** out) {
+  *out = nullptr;
+  if (!grid) return set_error(DSDP_ERR_INVALID_ARG, "grid is NULL");
   if (!grid->d_rec_xyz) return set_error(DSDP_ERR_INVALID_ARG, "grid has no receptor atoms (needed to rescore)");
   Job* j = new Job();
   dsdp_status s = normalize_params(params, &j->params);
@@ -922,24 +930,84 @@ extern "C" dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, co
   j->params.site_points = nullptr;
   j->grid = grid;
   layout_results(j);
-  const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);
+  *out = j;
+  return DSDP_OK;
+}
+
+// Queue built jobs, all or none (a job larger than the whole budget refuses
+// the set), and wake the progress thread once: jobs queued together can be
+// taken in one batch.
+static dsdp_status job_enqueue(dsdp_ctx* ctx, const std::vector<Job*>& jobs, uint64_t* job_ids) {
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (need > ctx->budget) {
-      delete j;
-      return set_error(DSDP_ERR_OUT_OF_MEMORY, "job needs %llu bytes, budget %llu", (unsigned long long)need,
-                       (unsigned long long)ctx->budget);
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      const Job* j = jobs[i];
+      const uint64_t need = up256(j->blob.size()) + j->res_bytes + plan_scratch_estimate(j);
+      if (need > ctx->budget) {
+        for (Job* d : jobs) delete d;
+        return set_error(DSDP_ERR_OUT_OF_MEMORY, "job %zu needs %llu bytes, budget %llu", i,
+                         (unsigned long long)need, (unsigned long long)ctx->budget);
+      }
     }
-    j->id = ctx->next_id++;
-    j->t_submit = std::chrono::steady_clock::now();
-    const_cast<dsdp_grid*>(grid)->users++;
-    ctx->jobs[j->id] = j;
-    ctx->queue.push_back(j->id);
-    ctx->stats.submitted++;
-    *job_id = j->id;
+    const auto now = std::chrono::steady_clock::now();
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      Job* j = jobs[i];
+      j->id = ctx->next_id++;
+      j->t_submit = now;
+      const_cast<dsdp_grid*>(j->grid)->users++;
+      ctx->jobs[j->id] = j;
+      ctx->queue.push_back(j->id);
+      ctx->stats.submitted++;
+      job_ids[i] = j->id;
+    }
   }
   ctx->cv_work.notify_all();
   return DSDP_OK;
+}
+
+extern "C" dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_ligand* ligand,
+                                        const dsdp_dock_params* params, uint64_t* job_id) {
+  if (!ctx || !grid || !job_id) return set_error(DSDP_ERR_INVALID_ARG, "ctx/grid/job_id NULL");
+  Job* j = nullptr;
+  const dsdp_status s = job_build(grid, ligand, params, &j);
+  if (s != DSDP_OK) return s;
+  return job_enqueue(ctx, {j}, job_id);
+}
+
+extern "C" dsdp_status dsdp_dock_submit_many(dsdp_ctx* ctx, int32_t n, const dsdp_grid* const* grids,
+                                             const dsdp_ligand* ligands, const dsdp_dock_params* params,
+                                             uint64_t* job_ids) {
+  if (!ctx || n < 0 || (n > 0 && (!grids || !ligands || !params || !job_ids)))
+    return set_error(DSDP_ERR_INVALID_ARG, "ctx/grids/ligands/params/job_ids NULL or n < 0");
+  if (n == 0) return DSDP_OK;
+  std::vector<Job*> jobs((size_t)n, nullptr);
+  std::vector<dsdp_status> st((size_t)n, DSDP_OK);
+  std::vector<std::string> msg((size_t)n);
+  // ligand packing (torsion tree, pair list, step schedule) is the host's
+  // work per job: spread it over a few threads
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int n_thr = (int)std::min<unsigned>(std::min<unsigned>(hw, 8u), (unsigned)n);
+  auto work = [&](int t) {
+    for (int i = t; i < n; i += n_thr) {
+      st[i] = job_build(grids[i], &ligands[i], &params[i], &jobs[i]);
+      if (st[i] != DSDP_OK) msg[i] = dsdp_last_error();
+    }
+  };
+  if (n_thr == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    pool.reserve(n_thr - 1);
+    for (int t = 1; t < n_thr; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (std::thread& th : pool) th.join();
+  }
+  for (int i = 0; i < n; ++i)
+    if (st[i] != DSDP_OK) {
+      for (Job* j : jobs) delete j;
+      return set_error(st[i], "job %d: %s", i, msg[i].c_str());
+    }
+  return job_enqueue(ctx, jobs, job_ids);
 }
 
 static void copy_results(const Job* j, dsdp_dock_result* out) {

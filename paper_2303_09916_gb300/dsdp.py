@@ -78,13 +78,14 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 class dsdp_create_params(C.Structure):
     _fields_ = [("device", C.c_int32), ("mem_budget_bytes", C.c_uint64), ("n_streams", C.c_int32),
-                ("max_inflight_jobs", C.c_int32), ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p)]
+                ("max_inflight_jobs", C.c_int32), ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
+                ("max_batch_chains", C.c_int32)]
 
 
 class dsdp_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("cancelled", C.c_uint64), ("queued", C.c_int32), ("running", C.c_int32),
-                ("bytes_in_use", C.c_uint64), ("bytes_budget", C.c_uint64)]
+                ("bytes_in_use", C.c_uint64), ("bytes_budget", C.c_uint64), ("batches", C.c_uint64)]
 
 
 class dsdp_grid_view(C.Structure):
@@ -119,6 +120,8 @@ _sig = {
                                     C.c_void_p, C.c_uint32]),
     "dsdp_dock_submit": (C.c_int32, [C.c_void_p, C.c_void_p, P(dsdp_ligand), P(dsdp_dock_params),
                                      P(C.c_uint64)]),
+    "dsdp_dock_submit_many": (C.c_int32, [C.c_void_p, C.c_int32, P(C.c_void_p), P(dsdp_ligand), P(dsdp_dock_params),
+                                          P(C.c_uint64)]),
     "dsdp_dock_poll": (C.c_int32, [C.c_void_p, C.c_uint64, P(dsdp_dock_result), C.c_int32]),
     "dsdp_dock_cancel": (C.c_int32, [C.c_void_p, C.c_uint64]),
     "dsdp_get_stats": (C.c_int32, [C.c_void_p, P(dsdp_stats)]),
@@ -221,8 +224,9 @@ def make_params(n_chains=0, n_mc_steps=0, n_opt_iters=0, optimizer=DSDP_OPT_BFGS
 
 
 # ------------------------------------------------------------------ context / grids
-def dsdp_create(device=0, mem_budget_bytes=0, n_streams=0, max_inflight_jobs=0):
+def dsdp_create(device=0, mem_budget_bytes=0, n_streams=0, max_inflight_jobs=0, max_batch_chains=0):
     p = dsdp_create_params(int(device), int(mem_budget_bytes), int(n_streams), int(max_inflight_jobs))
+    p.max_batch_chains = int(max_batch_chains)
     out = C.c_void_p()
     _check(_lib.dsdp_create(C.byref(p), C.byref(out)))
     return out.value
@@ -295,6 +299,20 @@ def dsdp_dock_submit(ctx, grid, ligand, params: dsdp_dock_params) -> int:
     jid = C.c_uint64()
     _check(_lib.dsdp_dock_submit(ctx, grid, C.byref(lig.struct), C.byref(params), C.byref(jid)))
     return jid.value
+
+
+def dsdp_dock_submit_many(ctx, grids, ligands, params) -> list:
+    """Submit len(ligands) jobs at once (grids[i], ligands[i], params[i]); the job ids."""
+    n = len(ligands)
+    if len(grids) != n or len(params) != n:
+        raise ValueError("grids, ligands and params differ in length")
+    keep = [make_ligand(l) for l in ligands]
+    g_arr = (C.c_void_p * max(n, 1))(*grids)
+    l_arr = (dsdp_ligand * max(n, 1))(*[k.struct for k in keep])
+    p_arr = (dsdp_dock_params * max(n, 1))(*params)
+    ids = (C.c_uint64 * max(n, 1))()
+    _check(_lib.dsdp_dock_submit_many(ctx, n, g_arr, l_arr, p_arr, ids))
+    return [ids[i] for i in range(n)]
 
 
 class DockResult(dict):

@@ -196,3 +196,14 @@ def test_create_without_a_gpu_fails_cleanly():
     with pytest.raises(dsdp.DSDPError) as ei:
         dsdp.dsdp_create(0)
     assert ei.value.status == dsdp.DSDP_ERR_DEVICE
+
+
+def test_submit_many_rejects_bad_arguments_without_a_gpu():
+    """dsdp_dock_submit_many checks its arguments before touching a context."""
+    import ctypes as C
+
+    lib = dsdp._lib
+    ids = (C.c_uint64 * 1)()
+    assert lib.dsdp_dock_submit_many(None, 1, None, None, None, ids) == dsdp.DSDP_ERR_INVALID_ARG
+    assert "NULL" in dsdp.dsdp_last_error()
+    assert lib.dsdp_dock_submit_many(None, -1, None, None, None, ids) == dsdp.DSDP_ERR_INVALID_ARG

@@ -436,6 +436,38 @@ def test_determinism_and_batch_independence(ctx):
         assert np.array_equal(r["score"], r1["score"]) and list(r["chain"]) == list(r1["chain"])
 
 
+def test_submit_many_matches_single_submissions(ctx):
+    """dsdp_dock_submit_many (ligands packed on several host threads, queued
+    together) gives each job the results of its own dsdp_dock_submit, bitwise;
+    a set with one invalid job queues nothing."""
+    a = Complex(1500, 14.0, 18, 5, seed=41)
+    b = Complex(2500, 18.0, 40, 10, seed=42)
+    ga = dsdp.dsdp_grid_build(ctx, a.rec.xyz, a.rec.xs_type, _box(a))
+    gb = dsdp.dsdp_grid_build(ctx, b.rec.xyz, b.rec.xs_type, _box(b))
+    try:
+        pa = dsdp.make_params(n_chains=48, n_mc_steps=6, n_opt_iters=25, seed=7, top_k=6)
+        pb = dsdp.make_params(n_chains=64, n_mc_steps=6, n_opt_iters=25, seed=8, top_k=6)
+        ref_a = _run_job(ctx, ga, a.lig, a.T, n_chains=48, n_mc_steps=6, n_opt_iters=25, seed=7, top_k=6)
+        ref_b = _run_job(ctx, gb, b.lig, b.T, n_chains=64, n_mc_steps=6, n_opt_iters=25, seed=8, top_k=6)
+        items = [(gb, b, pb, ref_b), (ga, a, pa, ref_a), (gb, b, pb, ref_b), (ga, a, pa, ref_a)] * 3
+        ids = dsdp.dsdp_dock_submit_many(ctx, [g for g, *_ in items], [c.lig for _, c, *_ in items],
+                                         [p for _, _, p, _ in items])
+        assert len(set(ids)) == len(items)
+        for jid, (_, c, p, ref) in zip(ids, items):
+            r = dsdp.dsdp_dock_poll(ctx, jid, dsdp.result_buffers(c.lig.n_atoms, c.T, p), wait_ms=-1)
+            assert np.array_equal(r["chain_best_e"], ref["chain_best_e"])
+            assert np.array_equal(r["chain_best_conf"], ref["chain_best_conf"])
+            assert np.array_equal(r["score"], ref["score"]) and list(r["chain"]) == list(ref["chain"])
+        before = dsdp.dsdp_get_stats(ctx)["submitted"]
+        bad = dsdp.make_params(n_chains=-3, n_mc_steps=6, n_opt_iters=25, seed=8, top_k=6)
+        with pytest.raises(dsdp.DSDPError, match="job 1"):
+            dsdp.dsdp_dock_submit_many(ctx, [ga, gb, ga], [a.lig, b.lig, a.lig], [pa, bad, pa])
+        assert dsdp.dsdp_get_stats(ctx)["submitted"] == before
+    finally:
+        dsdp.dsdp_grid_free(ctx, ga)
+        dsdp.dsdp_grid_free(ctx, gb)
+
+
 def test_plan_launch_configurations_agree(ctx):
     """One uneven batch (ligands of 10-60 atoms, 0-15 torsions, two map formats)
     through the device plan in every launch configuration the autotuner chooses
