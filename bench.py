@@ -10,7 +10,7 @@ rescoring and top-k.
 
   value  systems/s with inputs resident on the device (device-pointer API,
          caller-owned memory), timed with CUDA events over exactly K steps;
-         consecutive steps alternate between two streams, each with its own
+         consecutive steps rotate over three streams (--pipeline-depth), each with its own
          maps, outputs and plan, so that a step's grid builds and chains fill
          the SMs the previous step's last wave of chains leaves idle
          (--no-pipeline: one stream).  `serial` is the same K steps on one
@@ -67,6 +67,7 @@ def parse():
                    help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
     p.add_argument("--no-pipeline", dest="pipeline", action="store_false",
                    help="time the device-resident steps on one stream only (no overlap of consecutive steps)")
+    p.add_argument("--pipeline-depth", type=int, default=3, help="streams (steps in flight) of the pipelined pass")
     p.add_argument("--tile-config", type=int, default=-1,
                    help="chain kernel launch configuration: -1 autotune (default); 1..12 fixed, numbered as the "
                         "autotuner reports them: 1 + variant (0: 128 registers, 1: 96) + 2 work queue + 4 log2(chains "
@@ -254,7 +255,7 @@ def run_device(args, rank, world, dev, dist):
     """The device-resident step (grid builds, chains, FP64 rescoring + top-k of
     args.batch systems), timed twice: serially on one stream (stage times and the
     kernel rooflines come from this pass) and pipelined, consecutive steps
-    alternating between two streams with their own maps and outputs so that a
+    rotating over --pipeline-depth streams with their own maps and outputs so that a
     step's grid builds and chains fill the SMs the previous step's last wave of
     chains leaves idle (the headline throughput; each step still does all of its
     work)."""
@@ -327,7 +328,7 @@ def run_device(args, rank, world, dev, dist):
             dsdp.dsdp_grid_build_device(N_REC, sh["d_xyz"].data_ptr(), sh["d_type"].data_ptr(), sh["box"], dtype,
                                         dsdp.DSDP_GRID_EQ4, d_maps.data_ptr(), d_maps.numel(), st)
 
-    slots = [make_slot() for _ in range(2 if args.pipeline else 1)]
+    slots = [make_slot() for _ in range(args.pipeline_depth if args.pipeline else 1)]
     plan = dsdp.dsdp_plan_create(None, slots[0]["jobs"], 0, 0)
     build_grids(slots[0], sptr)
     if args.tile_config < 0:
@@ -376,9 +377,9 @@ def run_device(args, rank, world, dev, dist):
     serial_ms = max_over_ranks(dist, t0.elapsed_time(t1), dev)
     elapsed_ms = serial_ms
     if args.pipeline:
-        # pipelined pass: step k on stream k % 2 with slot k % 2
+        # pipelined pass: step k on stream k % depth with slot k % depth
         streams = [torch.cuda.Stream(device=dev) for _ in slots]
-        for k in range(2):  # untimed: one step per slot and stream
+        for k in range(len(slots)):  # untimed: one step per slot and stream
             with torch.cuda.stream(streams[k]):
                 flushes[k].zero_()
                 step(k, streams[k].cuda_stream)
@@ -391,7 +392,7 @@ def run_device(args, rank, world, dev, dist):
         for s in streams:
             s.wait_event(p0)
         for k in range(args.steps):
-            i = k % 2
+            i = k % len(slots)
             with torch.cuda.stream(streams[i]):
                 flushes[i].zero_()
                 step(i, streams[i].cuda_stream)
@@ -942,7 +943,8 @@ def main():
                    "chains": N_CHAINS, "mc_steps": N_STEPS, "opt_iters": N_ITERS, "optimizer": args.optimizer,
                    "top_k": TOP_K, "l2": "flushed before each step (256 MB write on the step's stream); each step builds 2.1 GB of maps", "parallelism": f"replicas x{world}",
                    "chain_kernel": describe_tile_config(r["tile_config"]),
-                   "pipeline": ("2 streams: consecutive steps overlap (own maps and outputs per stream)"
+                   "pipeline": (f"{args.pipeline_depth} streams: consecutive steps overlap (own maps and outputs "
+                                "per stream)"
                                 if args.pipeline else "none: steps back to back on one stream")},
         "serial": {"value": job_throughput(world, args.batch, args.steps, r["serial_ms"]),
                    "ms_per_step": r["serial_ms"] / args.steps,
