@@ -72,7 +72,10 @@ def parse():
                    help="chain kernel launch configuration: -1 autotune (default); 1..12 fixed, numbered as the "
                         "autotuner reports them: 1 + variant (0: 128 registers, 1: 96) + 2 work queue + 4 log2(chains "
                         "per CTA)")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.pipeline_depth < 1:
+        p.error("--pipeline-depth must be at least 1")
+    return args
 
 
 def replica_seeds(rank, batch):
