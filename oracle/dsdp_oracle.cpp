@@ -845,7 +845,9 @@ V3 unit_ball(const ChainRng& rng, uint32_t step) {
 //     E' < E or u1 < exp(-(E' - E) / T_mc); an accepted state better than the
 //     best becomes the best.
 // Parity: unpinned against the paper (it does not print the MC rules); pinned
-// by determinism, batch independence and self-docking sanity in the tests.
+// by determinism, batch independence and self-docking sanity in the tests, and
+// the mutations against the moves stated here (mode uniform over 2 + T, move
+// sizes by their unit-ball distribution, one coordinate group per move).
 // ---------------------------------------------------------------------------
 struct DockSettings {
   int n_mc_steps = 40;

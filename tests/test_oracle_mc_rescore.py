@@ -153,3 +153,58 @@ def test_rescore_is_sorted_deduplicated_and_brute_force_exact():
             continue
         xp = lig.coords(confs[p])
         assert min(np.sqrt(((xp - lig.coords(confs[q])) ** 2).sum(1).mean()) for q in idx) < 1.0
+
+
+def test_mutations_follow_the_stated_moves():
+    """With local optimisation off (0 iterations) and every candidate accepted
+    (current energy +inf), one MC step returns the mutation itself.  The mode is
+    uniform over the 2 + T choices; a position move adds 2 A times a point
+    uniform in the unit ball and keeps q and the torsions; an orientation move
+    keeps p and the torsions and rotates by (2 / R_gyr) times a unit-ball point
+    (R_gyr about the root origin: the lowest atom of the body with most atoms);
+    a torsion move re-draws that torsion alone, in (-pi, pi]."""
+    rec, s, lig, grid, lo, size = _complex(3, n_lig=12, T=4)
+    body_of, _, _ = lig.bodies()
+    members = [np.flatnonzero(body_of == b) for b in range(lig.n_bodies)]
+    root = max(range(lig.n_bodies), key=lambda b: (len(members[b]), -members[b].min()))
+    xyz = s.xyz.astype(np.float64)
+    r_gyr = math.sqrt(np.mean(np.sum((xyz - xyz[members[root].min()]) ** 2, axis=1)))
+    assert lig.gyration_radius == pytest.approx(r_gyr, rel=1e-12)
+    k_rot = 2.0 / r_gyr
+    dp = oracle.dock_params_array(1, 0, 1.2, lo, size)
+    off = dict(max_iters=0)
+    n = 1500
+    modes, r3_pos, dirs, r3_rot = [], [], [], []
+    for chain in range(n):
+        cur = oracle.chain_init(lig, dp, 11, chain, opt=off)
+        new, _, rec_ = oracle.mc_step(lig, grid, 0, dp, 11, chain, 1, cur, 1e300, opt=off)
+        m = int(rec_[0])
+        assert rec_[1] == 1
+        modes.append(m)
+        d_p, th0, th1 = new[:3] - cur[:3], cur[7:], new[7:]
+        if m == 0:
+            assert np.array_equal(new[3:], cur[3:])
+            r = np.linalg.norm(d_p)
+            assert r <= 2.0 + 1e-12
+            r3_pos.append((r / 2.0) ** 3)
+            dirs.append(d_p / r)
+        elif m == 1:
+            assert np.array_equal(new[:3], cur[:3]) and np.array_equal(th1, th0)
+            dot = min(1.0, abs(float(np.dot(new[3:7], cur[3:7]))) / np.linalg.norm(new[3:7]) / np.linalg.norm(cur[3:7]))
+            angle = 2.0 * math.acos(dot)
+            assert angle <= k_rot + 1e-7
+            r3_rot.append((angle / k_rot) ** 3)
+        else:
+            t = m - 2
+            assert np.array_equal(new[:7], cur[:7])
+            assert np.array_equal(np.delete(th1, t), np.delete(th0, t))
+            assert -math.pi < th1[t] <= math.pi
+    counts = np.bincount(modes, minlength=2 + lig.T)
+    assert len(counts) == 2 + lig.T
+    expected = n / (2 + lig.T)
+    chi2 = float(np.sum((counts - expected) ** 2 / expected))
+    assert chi2 < 20.5  # 5 degrees of freedom: p ~ 1e-3
+    # |ball point|^3 is uniform on [0, 1] for a point uniform in the ball; directions isotropic
+    for r3 in (np.array(r3_pos), np.array(r3_rot)):
+        assert abs(r3.mean() - 0.5) < 4 * math.sqrt(1 / 12 / len(r3))
+    assert np.linalg.norm(np.mean(dirs, axis=0)) < 4 * math.sqrt(1 / 3 / len(dirs))
