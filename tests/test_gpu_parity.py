@@ -468,6 +468,34 @@ def test_submit_many_matches_single_submissions(ctx):
         dsdp.dsdp_grid_free(ctx, gb)
 
 
+def test_max_batch_chains_splits_batches_without_changing_results(ctx):
+    """A context whose batches hold at most two jobs' chains runs six jobs queued
+    together in at least three batches (dsdp_stats.batches), each job with the
+    results it has in a context without the limit."""
+    a = Complex(1500, 14.0, 18, 5, seed=51)
+    kw = dict(n_chains=64, n_mc_steps=4, n_opt_iters=20, top_k=4)
+    small = dsdp.dsdp_create(0, max_batch_chains=2 * kw["n_chains"], max_inflight_jobs=16)
+    try:
+        results = {}
+        for c in (ctx, small):
+            g = dsdp.dsdp_grid_build(c, a.rec.xyz, a.rec.xs_type, _box(a))
+            try:
+                params = [dsdp.make_params(seed=s, **kw) for s in range(6)]
+                b0 = dsdp.dsdp_get_stats(c)["batches"]
+                ids = dsdp.dsdp_dock_submit_many(c, [g] * 6, [a.lig] * 6, params)
+                results[c] = [dsdp.dsdp_dock_poll(c, j, dsdp.result_buffers(a.lig.n_atoms, a.T, p), wait_ms=-1)
+                              for j, p in zip(ids, params)]
+                if c == small:
+                    assert dsdp.dsdp_get_stats(c)["batches"] - b0 >= 3
+            finally:
+                dsdp.dsdp_grid_free(c, g)
+        for r0, r1 in zip(results[ctx], results[small]):
+            assert np.array_equal(r0["chain_best_e"], r1["chain_best_e"])
+            assert np.array_equal(r0["score"], r1["score"]) and list(r0["chain"]) == list(r1["chain"])
+    finally:
+        dsdp.dsdp_destroy(small)
+
+
 def test_plan_launch_configurations_agree(ctx):
     """One uneven batch (ligands of 10-60 atoms, 0-15 torsions, two map formats)
     through the device plan in every launch configuration the autotuner chooses
