@@ -621,3 +621,69 @@ def test_plan_replayed_from_a_cuda_graph_matches_the_eager_launch(ctx):
                     assert np.array_equal(d[k].cpu().numpy(), ref[k]), k
     finally:
         dsdp.dsdp_plan_destroy(None, plan)
+
+
+def test_plans_on_concurrent_streams_match_a_serial_launch(ctx):
+    """Steps in flight on several streams, as the pipelined bench runs them: each
+    stream builds its own maps and launches its own plan of the same jobs while
+    the others run; every stream's results equal one serial launch's, bitwise."""
+    dev = torch.device("cuda", 0)
+    rec = synth.receptor(1500, 73)
+    box = dsdp.make_box(rec.pocket_center, 14.0, 0.375)
+    nb = dsdp.dsdp_grid_map_bytes(box)
+    xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
+    ty = torch.from_numpy(rec.xs_type.copy()).to(dev)
+    ligs = [synth.ligand(na, T, 90 + i, center=rec.pocket_center) for i, (na, T) in enumerate([(18, 4), (30, 8), (41, 11)])]
+    blobs = [dsdp.dsdp_ligand_pack(lig) for lig in ligs]
+    dblobs = [torch.from_numpy(b.copy()).to(dev) for b in blobs]
+    n = [int(np.ceil(14.0 / 0.375))] * 3
+    origin = [rec.pocket_center[a] - (n[a] - 1) * 0.375 / 2 for a in range(3)]
+
+    def make_slot():
+        maps = torch.empty(nb, dtype=torch.uint8, device=dev)
+        keep, jobs = [], []
+        for i, (blob, dblob) in enumerate(zip(blobs, dblobs)):
+            nx = 7 + dsdp.dsdp_ligand_blob_info(blob)["n_torsions"]
+            d = dict(conf=torch.zeros((48, nx), dtype=torch.float32, device=dev),
+                     e=torch.zeros(48, dtype=torch.float32, device=dev),
+                     n=torch.zeros(1, dtype=torch.int32, device=dev),
+                     chain=torch.zeros(4, dtype=torch.int32, device=dev),
+                     score=torch.zeros(4, dtype=torch.float64, device=dev))
+            j = dsdp.dsdp_job_device()
+            j.grid = dsdp.grid_view(maps.data_ptr(), n, origin, 0.375)
+            j.receptor = dsdp.dsdp_receptor(len(ty), xyz.data_ptr(), ty.data_ptr())
+            j.h_blob, j.d_blob = blob.ctypes.data, dblob.data_ptr()
+            j.params = dsdp.make_params(n_chains=48, n_mc_steps=3, n_opt_iters=15, seed=20 + i, top_k=4)
+            for a in range(3):
+                j.box_lo[a] = rec.pocket_center[a] - 7.0
+                j.box_size[a] = 14.0
+            j.d_chain_best_conf, j.d_chain_best_e = d["conf"].data_ptr(), d["e"].data_ptr()
+            j.d_out_n, j.d_out_chain, j.d_out_score = d["n"].data_ptr(), d["chain"].data_ptr(), d["score"].data_ptr()
+            jobs.append(j)
+            keep.append(d)
+        return dict(maps=maps, jobs=jobs, keep=keep, plan=dsdp.dsdp_plan_create(None, jobs, dsdp.DSDP_PLAN_PERSISTENT, 0))
+
+    def step(slot, st):
+        dsdp.dsdp_grid_build_device(len(ty), xyz.data_ptr(), ty.data_ptr(), box, 0, 0, slot["maps"].data_ptr(), nb, st)
+        dsdp.dsdp_plan_launch(slot["plan"], st)
+
+    slots = [make_slot() for _ in range(3)]
+    try:
+        step(slots[0], torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        ref = [{k: v.cpu().numpy().copy() for k, v in d.items()} for d in slots[0]["keep"]]
+        streams = [torch.cuda.Stream() for _ in slots]
+        for d in (d for sl in slots for d in sl["keep"]):
+            for v in d.values():
+                v.zero_()
+        torch.cuda.synchronize()
+        for k in range(6):  # two rounds over the three streams, all in flight together
+            step(slots[k % 3], streams[k % 3].cuda_stream)
+        torch.cuda.synchronize()
+        for sl in slots:
+            for d, r in zip(sl["keep"], ref):
+                for key in ("conf", "e", "n", "chain", "score"):
+                    assert np.array_equal(d[key].cpu().numpy(), r[key]), key
+    finally:
+        for sl in slots:
+            dsdp.dsdp_plan_destroy(None, sl["plan"])
