@@ -9,8 +9,14 @@ Reported (printed) and bounded:
   format's rounding of the summed corner values (2^-8 relative for BF16,
   2^-11 for FP16) on top of the FP32 tolerance;
 * the final FP64 rescoring of the poses: exact against the oracle (1e-10);
-* top pose against the FP32-map run: score difference and heavy-atom RMSD.
+* top pose against the FP32-map run: score difference and heavy-atom RMSD;
+* top pose of every map format against the FP64 oracle's own search of the
+  system (FP64 maps, the same Philox streams and parameters): score
+  difference and heavy-atom RMSD (the chains separate chaotically, so this
+  measures whether both searches reach the same best pose, not rounding).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -49,7 +55,26 @@ def system():
                 dsdp.dsdp_grid_free(ctx, grid)
     finally:
         dsdp.dsdp_destroy(ctx)
-    return dict(rec=rec, lig=lig, olig=olig, og=og, runs=runs)
+    # the oracle's own search: 384 chains x 40 steps of BFGS on its FP64 maps, FP64 top 9
+    lo = rec.pocket_center - BOX / 2
+    dp = oracle.dock_params_array(40, 0, 1.2, lo, np.array([BOX] * 3))
+    best, _, _ = oracle.dock(olig, og, 0, dp, 0, 384, n_threads=os.cpu_count() or 1, opt=dict(max_iters=100))
+    o_scores, o_idx, _ = oracle.rescore_topk(olig, rec.xyz.astype(np.float64), rec.xs_type, best, 9, 1.0)
+    o_top = dict(score=float(o_scores[0]), coords=olig.coords(best[o_idx[0]]))
+    return dict(rec=rec, lig=lig, olig=olig, og=og, runs=runs, oracle_top=o_top)
+
+
+def _against_the_oracle_search(r, o_top):
+    rmsd = float(np.sqrt(((r["coords"][0] - o_top["coords"]) ** 2).sum(-1).mean()))
+    return float(r["score"][0] - o_top["score"]), rmsd
+
+
+def test_fp32_map_run_against_the_oracle_search(system):
+    r, o_top = system["runs"][dsdp.DSDP_MAP_F32], system["oracle_top"]
+    d, rmsd = _against_the_oracle_search(r, o_top)
+    assert np.isfinite(d) and np.isfinite(rmsd) and r["score"][0] < 0 and o_top["score"] < 0
+    print(f"maps f32: top-1 FP64 score {r['score'][0]:.4f} vs the oracle search's {o_top['score']:.4f} "
+          f"(diff {d:+.4f}), top-1 pose RMSD {rmsd:.3f} A")
 
 
 def _corner_abs_scale(olig, og, lig, conf):
@@ -92,3 +117,6 @@ def test_reduced_precision_map_errors(system, dtype):
           f"top-1 FP64 score {r['score'][0]:.4f} vs FP32-map run {f32['score'][0]:.4f} (diff {d_score:+.4f}), "
           f"top-1 pose RMSD to the FP32-map top-1 {top_rmsd:.3f} A; "
           f"best of 9 {r['score'].min():.4f} vs {f32['score'].min():.4f}")
+    d_o, rmsd_o = _against_the_oracle_search(r, system["oracle_top"])
+    print(f"maps {['f32', 'bf16', 'f16'][dtype]}: top-1 against the oracle search: score diff {d_o:+.4f}, "
+          f"pose RMSD {rmsd_o:.3f} A")
