@@ -246,6 +246,30 @@ def site_points(rec: Receptor, n_points: int = 100, seed: int = 0, spread: float
     return (rec.pocket_center + _ball(rng, n_points, spread)).astype(np.float32)
 
 
+def shell_receptor(lig: Ligand, seed: int = 0, per_atom: int = 24, radius: float = 4.0, gap: float = 3.6,
+                   spacing: float = 2.2, mouth_deg: float = 0.0) -> Receptor:
+    """A redocking receptor built around a ligand's own pose: points `radius`
+    from each ligand atom in random directions, none closer than `gap` to any
+    ligand atom, thinned to one per `spacing`; all hydrophobic carbons (C_H),
+    so the pose they were built around is the deepest minimum (dense enough
+    that it also ranks first by the exact inter score, which the rescoring
+    sorts by).  pocket_center = the ligand's centroid."""
+    rng = _rng(seed, "SHEL")
+    xyz = lig.xyz.astype(np.float64)
+    d = rng.normal(size=(len(xyz), per_atom, 3))
+    pts = (xyz[:, None, :] + radius * d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3)
+    pts = pts[np.min(np.linalg.norm(pts[:, None] - xyz[None], axis=-1), axis=1) > gap]
+    if mouth_deg > 0:  # an opening: no shell atom within mouth_deg of +z, seen from the centroid
+        v = pts - xyz.mean(axis=0)
+        pts = pts[v[:, 2] < np.cos(np.radians(mouth_deg)) * np.linalg.norm(v, axis=1)]
+    out = []
+    for p in pts:
+        if all(np.linalg.norm(p - q) >= spacing for q in out):
+            out.append(p)
+    out = np.array(out, dtype=np.float32).reshape(-1, 3)
+    return Receptor(out, np.zeros(len(out), dtype=np.uint8), xyz.mean(axis=0))
+
+
 def box_around(center, size, spacing=0.375) -> Box:
     s = np.array(size if np.ndim(size) else [size] * 3, dtype=np.float64)
     return Box(np.asarray(center, dtype=np.float64), s, float(spacing))
