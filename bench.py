@@ -690,9 +690,12 @@ def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18):
     """Redocking with one copies x steps setting (the accuracy side of the paper's
     Table 1): ligands of 12-30 atoms in receptor shells built around their own
     poses and open on one side (synth.shell_receptor, a 60 degree mouth), all in
-    one launch, in two boxes: 30 A cubes (chains starting anywhere must find
-    the pocket and enter it) and the paper's known-site box (the ligand's
-    extent plus 4 A on every side).  Reported per box: the fraction whose top
+    one launch, in three search regions: 30 A cubes (chains starting anywhere
+    must find the pocket and enter it), the same cubes intersected with 7 A
+    balls around 100 binding-site points within 3 A of the pocket centre (the
+    adaptive search space; stand-ins for the site network's points), and the
+    paper's known-site box (the ligand's extent plus 4 A on every side).
+    Reported per region: the fraction whose top
     pose lies within 2 A (and 5 A) heavy-atom RMSD of the pose the shell was
     built around, and the launch time."""
     from paper_2303_09916_gb300 import synth
@@ -703,16 +706,19 @@ def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18):
         lig = synth.ligand(na, t, 200 + i)
         cases.append((lig, synth.shell_receptor(lig, 200 + i, mouth_deg=60.0), 200 + i))
     out = {}
-    for tag in ("box30", "site"):
+    for tag in ("box30", "box30_sites", "site"):
         items = []
         for lig, rec, seed in cases:
-            if tag == "box30":
-                size, center = BOX, None
-            else:
+            sites = None
+            if tag == "site":
                 lo, hi = lig.xyz.min(axis=0) - 4.0, lig.xyz.max(axis=0) + 4.0
                 size, center = hi - lo, (lo + hi) / 2
+            else:
+                size, center = BOX, None
+                if tag == "box30_sites":  # the adaptive search space: 7 A balls around predicted points
+                    sites = synth.site_points(rec, 100, seed, spread=3.0)
             items.append(make_device_job(dsdp, torch, dev, rec, lig, seed, size, SPACING, dsdp.DSDP_MAP_F32, chains,
-                                         steps, N_ITERS, 1, coords=True, center=center))
+                                         steps, N_ITERS, 1, coords=True, center=center, sites=sites))
         for _, keep in items:
             build_grid(dsdp, keep["grid"], dsdp.DSDP_MAP_F32, sptr)
         plan = dsdp.dsdp_plan_create(None, [j for j, _ in items], 0, 0)
