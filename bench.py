@@ -446,7 +446,7 @@ def run_device(args, rank, world, dev, dist):
 
 # ---------------------------------------------------------------- other forms of the same work
 def make_device_job(dsdp, torch, dev, rec, lig, seed, box_size, spacing, dtype, n_chains, n_steps, n_iters, top_k,
-                    grid=None, sites=None, mode=0, coords=False, center=None):
+                    grid=None, sites=None, mode=0, coords=False, center=None, optimizer=0):
     """Device buffers and a dsdp_job_device for one docking job (caller-owned memory);
     box_size: edge length(s) of the box (scalar or per axis) around `center`
     (default: the receptor's pocket centre);
@@ -478,7 +478,7 @@ def make_device_job(dsdp, torch, dev, rec, lig, seed, box_size, spacing, dtype, 
     j.h_blob = blob.ctypes.data
     j.d_blob = keep["d_blob"].data_ptr()
     j.params = dsdp.make_params(n_chains=n_chains, n_mc_steps=n_steps, n_opt_iters=n_iters, seed=seed, top_k=top_k,
-                                site_points=sites)
+                                site_points=sites, optimizer=optimizer)
     if sites is not None:
         keep["sites"] = torch.from_numpy(np.ascontiguousarray(sites, dtype=np.float32)).to(dev)
         j.d_site_points = keep["sites"].data_ptr()
@@ -547,7 +547,10 @@ def run_variants(args, rank, dev, steps=2):
         points in the pocket (shape; Sec. 2 third modification);
       grid_mode: score + gradient maps interpolated (Eq. 4, 128 B gathered per
         atom) or score maps only with the gradient of the interpolant (Eq. 3,
-        32 B per atom)."""
+        32 B per atom).
+    Each variant also redocks the 18 open synthetic pockets of redock_success
+    (cube: 30 A boxes; shape: with site points; grid modes: known-site box and
+    30 A boxes with site points)."""
     import torch
     from paper_2303_09916_gb300 import dsdp, synth
 
@@ -581,6 +584,13 @@ def run_variants(args, rank, dev, steps=2):
         sec = a.elapsed_time(b) * 1e-3 / steps
         out[group][name] = dict(systems_per_s=len(jobs) / sec, evals_per_s=evals / sec,
                                 evals_per_system=evals / len(jobs), mean_top1_score=float(np.mean(top1)))
+        # redocking accuracy of the variant (open synthetic pockets, 384 x 40)
+        regions = {"cube": ("box30",), "shape": ("box30_sites",)}.get(name, ("site", "box30_sites"))
+        out[group][name].update(redock_success(dsdp, torch, dev, sptr, N_CHAINS, N_STEPS, regions=regions, mode=mode))
+        if group == "grid_mode":  # the paper pairs its Eq. 4 maps with Barzilai-Borwein
+            bb = redock_success(dsdp, torch, dev, sptr, N_CHAINS, N_STEPS, regions=regions, mode=mode,
+                                optimizer=dsdp.DSDP_OPT_BB)
+            out[group][name].update({k + "_bb": v for k, v in bb.items()})
     return out
 
 
@@ -686,7 +696,8 @@ def run_sweep(args, dev=0):
 REDOCK = [(12, 2), (16, 3), (20, 4), (24, 6), (28, 7), (30, 8)]
 
 
-def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18):
+def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18, regions=("box30", "box30_sites", "site"),
+                   mode=0, optimizer=0):
     """Redocking with one copies x steps setting (the accuracy side of the paper's
     Table 1): ligands of 12-30 atoms in receptor shells built around their own
     poses and open on one side (synth.shell_receptor, a 60 degree mouth), all in
@@ -697,7 +708,8 @@ def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18):
     paper's known-site box (the ligand's extent plus 4 A on every side).
     Reported per region: the fraction whose top
     pose lies within 2 A (and 5 A) heavy-atom RMSD of the pose the shell was
-    built around, and the launch time."""
+    built around, and the launch time.  mode: the grid maps (Eq. 4 or Eq. 3);
+    optimizer: BFGS or Barzilai-Borwein."""
     from paper_2303_09916_gb300 import synth
 
     cases = []
@@ -706,7 +718,7 @@ def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18):
         lig = synth.ligand(na, t, 200 + i)
         cases.append((lig, synth.shell_receptor(lig, 200 + i, mouth_deg=60.0), 200 + i))
     out = {}
-    for tag in ("box30", "box30_sites", "site"):
+    for tag in regions:
         items = []
         for lig, rec, seed in cases:
             sites = None
@@ -718,7 +730,8 @@ def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18):
                 if tag == "box30_sites":  # the adaptive search space: 7 A balls around predicted points
                     sites = synth.site_points(rec, 100, seed, spread=3.0)
             items.append(make_device_job(dsdp, torch, dev, rec, lig, seed, size, SPACING, dsdp.DSDP_MAP_F32, chains,
-                                         steps, N_ITERS, 1, coords=True, center=center, sites=sites))
+                                         steps, N_ITERS, 1, coords=True, center=center, sites=sites, mode=mode,
+                                         optimizer=optimizer))
         for _, keep in items:
             build_grid(dsdp, keep["grid"], dsdp.DSDP_MAP_F32, sptr)
         plan = dsdp.dsdp_plan_create(None, [j for j, _ in items], 0, 0)
