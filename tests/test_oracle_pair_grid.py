@@ -320,3 +320,27 @@ def test_synthetic_receptor_shape():
     frac = np.bincount(rec.xs_type, minlength=9) / 2000.0
     carbon = frac[C_H] + frac[C_P]
     assert 0.58 < carbon < 0.66
+
+
+@pytest.mark.parametrize("mouth", [0.0, 60.0])
+def test_shell_receptor_shape(mouth):
+    """The redocking shell keeps its stated geometry: every atom between the gap
+    and the radius from the nearest ligand atom (and exactly the radius from the
+    ligand atom it was drawn around), at least the thinning spacing apart, none
+    in the mouth, and the same shell from the same seed."""
+    lig = synth.ligand(20, 4, 3)
+    rec = synth.shell_receptor(lig, 7, mouth_deg=mouth)
+    xyz = lig.xyz.astype(np.float64)
+    pts = rec.xyz.astype(np.float64)
+    assert len(pts) > 20 and np.all(rec.xs_type == 0)
+    d = np.linalg.norm(pts[:, None] - xyz[None], axis=-1)
+    assert np.all(d.min(axis=1) > 3.6 - 1e-5) and np.all(d.min(axis=1) <= 4.0 + 1e-5)
+    assert np.all(np.abs(d - 4.0).min(axis=1) < 1e-5)
+    pp = np.linalg.norm(pts[:, None] - pts[None], axis=-1) + np.eye(len(pts)) * 1e9
+    assert pp.min() >= 2.2 - 1e-5
+    assert np.allclose(rec.pocket_center, xyz.mean(axis=0))
+    if mouth:
+        v = pts - xyz.mean(axis=0)
+        assert np.all(v[:, 2] < np.cos(np.radians(mouth)) * np.linalg.norm(v, axis=1) + 1e-5)
+    again = synth.shell_receptor(lig, 7, mouth_deg=mouth)
+    assert np.array_equal(again.xyz, rec.xyz)
