@@ -372,7 +372,10 @@ dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_devic
 dsdp_status dsdp_plan_autotune(dsdp_plan* plan, void* stream, int32_t repeats, int32_t* chosen);
 /* Enqueue the plan's kernels on `stream` (chains, then FP64 rescoring and
  * top-k).  No allocation and no host synchronisation: a launch can be
- * captured into a CUDA graph and replayed. */
+ * captured into a CUDA graph and replayed.  Different plans may run at once
+ * on different streams when no two of them write the same output buffers (or
+ * have their maps rebuilt while the other reads them); a plan's own launches
+ * must be ordered (they share its scratch and work-queue counters). */
 dsdp_status dsdp_plan_launch(dsdp_plan* plan, void* stream);
 /* Stages of a plan for dsdp_plan_launch_stage. */
 enum { DSDP_STAGE_CHAINS = 1, DSDP_STAGE_RESCORE = 2, DSDP_STAGE_ALL = 3 };
