@@ -189,8 +189,10 @@ def _run_job(ctx, grid, lig, T, **kw):
     return dsdp.dsdp_dock_poll(ctx, jid, dsdp.result_buffers(lig.n_atoms, T, params), wait_ms=-1)
 
 
-@pytest.mark.parametrize("optimizer", [dsdp.DSDP_OPT_BFGS, dsdp.DSDP_OPT_BB])
-def test_local_opt_short_horizon(ctx, chain_complex, optimizer):
+@pytest.mark.parametrize("optimizer,mode", [(dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ4),
+                                            (dsdp.DSDP_OPT_BB, dsdp.DSDP_GRID_EQ4),
+                                            (dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ3)])
+def test_local_opt_short_horizon(ctx, chain_complex, optimizer, mode):
     """The first local optimisation of each chain (step 0) after k = 0, 1, 2, 3, 5, 10
     iterations.  k = 0 is a pure evaluation of the Philox-drawn pose and k = 1 a
     single line search: every chain must agree.  Further iterations feed the
@@ -199,17 +201,19 @@ def test_local_opt_short_horizon(ctx, chain_complex, optimizer):
     update, so the two trajectories may separate; for k = 2, 3 most chains must
     still agree, and for every k each GPU result must be valid: its reported
     energy is the oracle's score of the pose it reports, and no worse than the
-    start."""
+    start.  Also on Eq. 3 maps (score maps only, the gradient of the
+    interpolant): the chain kernel's Eq. 3 path against the oracle's."""
     cx = chain_complex
     og = cx.oracle_grid()
-    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
-                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    maps = og.maps if mode == dsdp.DSDP_GRID_EQ4 else og.maps[..., :1]
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32, mode,
+                                    np.ascontiguousarray(maps, dtype=np.float32))
     nc = 32
     nx = 7 + cx.T
     dp = oracle.dock_params_array(0, optimizer, 1.2, cx.box_lo(), cx.size)
     starts = np.array([oracle.chain_init(cx.olig, dp, 7, c) for c in range(nc)])
-    e_start = np.array([cx.olig.score_grid(og, 0, c)[0].sum() for c in starts])
-    tol0 = np.array([E_REL * max(cx.abs_terms(og, 0, c), 1.0) for c in starts])
+    e_start = np.array([cx.olig.score_grid(og, mode, c)[0].sum() for c in starts])
+    tol0 = np.array([E_REL * max(cx.abs_terms(og, mode, c), 1.0) for c in starts])
     agree, base = {}, {}
     try:
         e0, _ = dsdp.dsdp_score_eval(ctx, grid, cx.lig, starts)
@@ -219,21 +223,23 @@ def test_local_opt_short_horizon(ctx, chain_complex, optimizer):
                            optimizer=optimizer, trace=1, top_k=1)
             a = b = 0
             for c in range(nc):
-                _, e_ref, _, _ = cx.olig.local_opt(og, 0, optimizer, starts[c], opt=dict(max_iters=iters))
-                _, e_f32, _, _ = cx.olig.local_opt(og, 0, optimizer, starts[c].astype(np.float32).astype(np.float64),
+                _, e_ref, _, _ = cx.olig.local_opt(og, mode, optimizer, starts[c], opt=dict(max_iters=iters))
+                _, e_f32, _, _ = cx.olig.local_opt(og, mode, optimizer,
+                                                   starts[c].astype(np.float32).astype(np.float64),
                                                    opt=dict(max_iters=iters))
                 e_gpu = float(res["trace"][c, 0, nx + 1])
                 pose = res["trace"][c, 0, :nx].astype(np.float64)
-                tol = E_REL * max(cx.abs_terms(og, 0, pose), 1.0)
+                tol = E_REL * max(cx.abs_terms(og, mode, pose), 1.0)
                 # validity: the reported energy is the score of the reported pose, and a descent
-                assert abs(cx.olig.score_grid(og, 0, pose)[0].sum() - e_gpu) <= tol, (iters, c)
+                assert abs(cx.olig.score_grid(og, mode, pose)[0].sum() - e_gpu) <= tol, (iters, c)
                 assert e_gpu <= e_start[c] + tol0[c], (iters, c)
                 a += abs(e_gpu - e_ref) <= max(tol, tol0[c])
                 b += abs(e_f32 - e_ref) <= tol0[c]
             agree[iters], base[iters] = int(a), int(b)
     finally:
         dsdp.dsdp_grid_free(ctx, grid)
-    print(f"optimizer {optimizer}: GPU vs oracle {agree}; oracle vs FP32-rounded start {base} (of {nc})")
+    print(f"optimizer {optimizer}, maps {'eq4' if mode == dsdp.DSDP_GRID_EQ4 else 'eq3'}: GPU vs oracle {agree}; "
+          f"oracle vs FP32-rounded start {base} (of {nc})")
     assert agree[0] == nc and agree[1] == nc, agree
     assert agree[2] >= 0.85 * nc and agree[3] >= 0.8 * nc, agree
 
