@@ -100,7 +100,10 @@ enum {
 typedef enum { DSDP_MAP_F32 = 0, DSDP_MAP_BF16 = 1, DSDP_MAP_F16 = 2 } dsdp_map_dtype;
 typedef enum { DSDP_GRID_EQ4 = 0, DSDP_GRID_EQ3 = 1 } dsdp_grid_mode;
 typedef enum { DSDP_OPT_BFGS = 0, DSDP_OPT_BB = 1 } dsdp_optimizer;
-enum { DSDP_TERM_INTER = 1, DSDP_TERM_INTRA = 2, DSDP_TERM_ALL = 3 };
+/* DSDP_TERM_NORMALISED (dsdp_score_eval only): the selected terms and their
+ * gradient divided by 1 + 0.0585 T (T torsions), the torsion normalisation of
+ * the reported docking scores; on the device in FP32. */
+enum { DSDP_TERM_INTER = 1, DSDP_TERM_INTRA = 2, DSDP_TERM_ALL = 3, DSDP_TERM_NORMALISED = 4 };
 
 /* Receptor atoms (host or device memory, see each call). */
 typedef struct {

@@ -833,10 +833,17 @@ static void grid_view_of(const dsdp_grid* g, dsdp_grid_view* v) {
 }
 
 // ------------------------------------------------------------------ scoring
+namespace dsdp {
+cudaError_t launch_scale_scores(float* energy, float* grad, int n_conf, int nd, int n_torsions, cudaStream_t st);
+}
+
 extern "C" dsdp_status dsdp_score_eval(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_ligand* ligand,
                                        const double* conf, int32_t n_conf, double* energy, double* grad,
                                        uint32_t flags) {
   if (!ctx || !grid || !conf || n_conf < 0) return set_error(DSDP_ERR_INVALID_ARG, "score_eval arguments");
+  if ((flags & DSDP_TERM_ALL) == 0 || (flags & ~(uint32_t)(DSDP_TERM_ALL | DSDP_TERM_NORMALISED)))
+    return set_error(DSDP_ERR_INVALID_ARG, "flags must select DSDP_TERM_INTER and/or DSDP_TERM_INTRA "
+                                           "(optionally with DSDP_TERM_NORMALISED)");
   if (n_conf == 0) return DSDP_OK;
   uint64_t bytes = 0;
   dsdp_status s = dsdp_ligand_pack(ligand, nullptr, 0, &bytes);
@@ -861,7 +868,11 @@ extern "C" dsdp_status dsdp_score_eval(dsdp_ctx* ctx, const dsdp_grid* grid, con
   grid_view_of(grid, &v);
   if (e == cudaSuccess) {
     s = dsdp_score_eval_device(&v, blob.data(), d, (const float*)(d + o_conf), n_conf, (float*)(d + o_e),
-                               grad ? (float*)(d + o_g) : nullptr, flags, (void*)ctx->sync_stream);
+                               grad ? (float*)(d + o_g) : nullptr, flags & DSDP_TERM_ALL, (void*)ctx->sync_stream);
+    if (s == DSDP_OK && (flags & DSDP_TERM_NORMALISED))
+      s = check_cuda(launch_scale_scores((float*)(d + o_e), grad ? (float*)(d + o_g) : nullptr, n_conf, (int)nd, T,
+                                         ctx->sync_stream),
+                     "score normalisation");
   } else {
     s = check_cuda(e, "score_eval upload");
   }

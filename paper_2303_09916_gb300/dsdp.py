@@ -28,7 +28,7 @@ DSDP_ERR_TIMEOUT, DSDP_ERR_CANCELLED, DSDP_ERR_DEVICE, DSDP_ERR_INTERNAL = -4, -
 DSDP_MAP_F32, DSDP_MAP_BF16, DSDP_MAP_F16 = 0, 1, 2
 DSDP_GRID_EQ4, DSDP_GRID_EQ3 = 0, 1
 DSDP_OPT_BFGS, DSDP_OPT_BB = 0, 1
-DSDP_TERM_INTER, DSDP_TERM_INTRA, DSDP_TERM_ALL = 1, 2, 3
+DSDP_TERM_INTER, DSDP_TERM_INTRA, DSDP_TERM_ALL, DSDP_TERM_NORMALISED = 1, 2, 3, 4
 DSDP_PLAN_PERSISTENT, DSDP_PLAN_NO_RESCORE = 1, 2
 DSDP_STAGE_CHAINS, DSDP_STAGE_RESCORE, DSDP_STAGE_ALL = 1, 2, 3
 DSDP_NUM_MAP_TYPES = 8

@@ -142,6 +142,28 @@ def test_score_eval_on_oracle_maps(ctx, scoring_complex, mode):
         dsdp.dsdp_grid_free(ctx, grid)
 
 
+def test_score_eval_normalised(ctx, scoring_complex):
+    """DSDP_TERM_NORMALISED divides the selected terms and their gradient by
+    1 + 0.0585 T (the torsion normalisation of the reported scores); undone, the
+    results match the oracle's FP64 terms within the FP32 tolerance."""
+    cx = scoring_complex
+    og = cx.oracle_grid()
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, _box(cx), dsdp.DSDP_MAP_F32,
+                                    dsdp.DSDP_GRID_EQ4, og.maps.astype(np.float32))
+    try:
+        confs = cx.random_confs(48, seed=3)
+        w = 1.0 + 0.0585 * cx.T
+        for flags in (dsdp.DSDP_TERM_ALL, dsdp.DSDP_TERM_INTER):
+            e, g = dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs, flags)
+            en, gn = dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs, flags | dsdp.DSDP_TERM_NORMALISED)
+            assert np.allclose(en, e / w, rtol=1e-6, atol=1e-6) and np.allclose(gn, g / w, rtol=1e-6, atol=1e-6)
+            _compare_scores(cx, og, 0, confs, en * w, gn * w, flags)
+        with pytest.raises(dsdp.DSDPError):
+            dsdp.dsdp_score_eval(ctx, grid, cx.lig, confs, dsdp.DSDP_TERM_NORMALISED)  # selects no term
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+
+
 def test_score_eval_end_to_end_on_gpu_maps(ctx, scoring_complex):
     """(ii) GPU-built maps and the scoring kernel together."""
     cx = scoring_complex
