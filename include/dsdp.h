@@ -202,6 +202,10 @@ typedef struct {
   dsdp_free_fn free;
   void* alloc_user;
   int32_t max_batch_chains;   /* chains of one batch at most; 0 = 64 x the SM count */
+  void* stream;               /* cudaStream_t for the synchronous work (grid builds, scoring):
+                                 ordered after the caller's earlier work on it; NULL = the
+                                 context's own high-priority stream.  Not destroyed by
+                                 dsdp_destroy. */
 } dsdp_create_params;
 
 /* Create a context: owns streams, the job table and a progress thread that

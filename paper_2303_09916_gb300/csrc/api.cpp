@@ -91,6 +91,7 @@ struct dsdp_ctx {
   int max_batch_chains = 0;            // chains per batch (default 64 per SM)
   std::vector<cudaStream_t> streams;   // one batch in flight per stream
   cudaStream_t sync_stream = nullptr;   // synchronous calls and grid builds
+  bool own_sync_stream = true;          // false: the caller's stream (dsdp_create_params.stream)
   cudaStream_t upload_stream = nullptr; // receptor uploads of grid builds (copy engines only)
   cudaStream_t alloc_stream = nullptr;  // allocations done outside a job stream
   cudaMemPool_t pool = nullptr;         // the context's own stream-ordered pool (no caller allocator)
@@ -512,7 +513,12 @@ extern "C" dsdp_status dsdp_create(const dsdp_create_params* params, dsdp_ctx** 
   // grid build does not wait for the docking kernels already on the GPU.
   int prio_least = 0, prio_greatest = 0;
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-  cudaStreamCreateWithPriority(&ctx->sync_stream, cudaStreamNonBlocking, prio_greatest);
+  if (p.stream) {
+    ctx->sync_stream = (cudaStream_t)p.stream;
+    ctx->own_sync_stream = false;
+  } else {
+    cudaStreamCreateWithPriority(&ctx->sync_stream, cudaStreamNonBlocking, prio_greatest);
+  }
   cudaStreamCreateWithPriority(&ctx->alloc_stream, cudaStreamNonBlocking, prio_greatest);
   cudaStreamCreateWithPriority(&ctx->upload_stream, cudaStreamNonBlocking, prio_greatest);
   ctx->alloc = p.alloc;
@@ -582,7 +588,8 @@ extern "C" dsdp_status dsdp_destroy(dsdp_ctx* ctx) {
   cudaStreamDestroy(ctx->alloc_stream);
   cudaStreamSynchronize(ctx->upload_stream);
   cudaStreamDestroy(ctx->upload_stream);
-  cudaStreamDestroy(ctx->sync_stream);
+  cudaStreamSynchronize(ctx->sync_stream);
+  if (ctx->own_sync_stream) cudaStreamDestroy(ctx->sync_stream);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return DSDP_OK;

@@ -79,7 +79,7 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 class dsdp_create_params(C.Structure):
     _fields_ = [("device", C.c_int32), ("mem_budget_bytes", C.c_uint64), ("n_streams", C.c_int32),
                 ("max_inflight_jobs", C.c_int32), ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
-                ("max_batch_chains", C.c_int32)]
+                ("max_batch_chains", C.c_int32), ("stream", C.c_void_p)]
 
 
 class dsdp_stats(C.Structure):
@@ -224,9 +224,11 @@ def make_params(n_chains=0, n_mc_steps=0, n_opt_iters=0, optimizer=DSDP_OPT_BFGS
 
 
 # ------------------------------------------------------------------ context / grids
-def dsdp_create(device=0, mem_budget_bytes=0, n_streams=0, max_inflight_jobs=0, max_batch_chains=0):
+def dsdp_create(device=0, mem_budget_bytes=0, n_streams=0, max_inflight_jobs=0, max_batch_chains=0, stream=None):
+    """stream: a cudaStream_t (int) for the context's synchronous work, e.g. torch.cuda.Stream().cuda_stream."""
     p = dsdp_create_params(int(device), int(mem_budget_bytes), int(n_streams), int(max_inflight_jobs))
     p.max_batch_chains = int(max_batch_chains)
+    p.stream = stream
     out = C.c_void_p()
     _check(_lib.dsdp_create(C.byref(p), C.byref(out)))
     return out.value

@@ -1,7 +1,8 @@
-"""The handle API's job lifecycle and status codes on a GPU: a queued job
-polled without waiting is pending, cancelling it frees it (its one poll
-reports CANCELLED, the next NOT_FOUND), a finished job is released by its poll,
-and a grid larger than the context's budget is refused with OUT_OF_MEMORY."""
+"""The handle API on a GPU: the job lifecycle and status codes (a queued job
+polled without waiting is pending, cancelling it frees it -- its one poll
+reports CANCELLED, the next NOT_FOUND --, a finished job is released by its
+poll, a grid larger than the context's budget is refused with OUT_OF_MEMORY),
+and a context working on the caller's stream."""
 import numpy as np
 import pytest
 
@@ -63,3 +64,32 @@ def test_grid_over_the_budget_is_refused():
         dsdp.dsdp_grid_free(ctx, g)
     finally:
         dsdp.dsdp_destroy(ctx)
+
+
+def test_context_on_the_callers_stream():
+    """A context given the caller's stream runs its grid builds and scoring on it
+    (same results as a context of its own) and leaves the stream alive."""
+    rec = synth.receptor(1500, 8)
+    lig = synth.ligand(14, 3, 8, center=rec.pocket_center)
+    box = dsdp.make_box(rec.pocket_center, 14.0, 0.375)
+    rng = np.random.default_rng(0)
+    confs = np.zeros((16, 7 + lig.n_torsions))
+    confs[:, :3] = rec.pocket_center + rng.uniform(-2, 2, (16, 3))
+    q = rng.normal(size=(16, 4))
+    confs[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    confs[:, 7:] = rng.uniform(-3, 3, (16, lig.n_torsions))
+    out = []
+    user = torch.cuda.Stream()
+    for stream in (None, user.cuda_stream):
+        ctx = dsdp.dsdp_create(0, stream=stream)
+        try:
+            g = dsdp.dsdp_grid_build(ctx, rec.xyz, rec.xs_type, box)
+            out.append(dsdp.dsdp_score_eval(ctx, g, lig, confs))
+            dsdp.dsdp_grid_free(ctx, g)
+        finally:
+            dsdp.dsdp_destroy(ctx)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    with torch.cuda.stream(user):  # still a valid stream after dsdp_destroy
+        x = torch.ones(8, device="cuda") * 2
+    user.synchronize()
+    assert float(x.sum()) == 16.0
