@@ -334,6 +334,10 @@ def dock(lig: Ligand, grid: Grid, mode, dock_params, seed, n_chains, chain0=0, n
 
 
 def rescore_topk(lig: Ligand, rec_xyz, rec_type, confs, k, rmsd_cut=1.0):
+    """FP64 rescoring of every conformation and the top k after RMSD de-duplication.
+    Returns (scores, idx, terms): scores[n] of every conformation in input order,
+    idx the kept top-k input indices (best first), terms[kept, 3] their (score,
+    inter, intra)."""
     rx, rxp = _d(rec_xyz)
     rt, rtp = _i(rec_type)
     c, cp = _d(confs)
