@@ -72,3 +72,24 @@ def test_fixed_tile_config_numbering():
         assert text.startswith(f"{(128, 96)[var]} regs, {w} chain") and text.endswith("work queue") == bool(queue)
         seen.add((tc, queue))
     assert len(seen) == 12
+
+
+def test_committed_chain_kernel_capture_is_consistent():
+    """The committed ncu record of the chain kernel covers every launch
+    configuration the autotuner can choose, each internally consistent (DRAM
+    bytes = read + write, instructions per evaluation = instructions /
+    evaluations, the same evaluation count: results do not depend on the
+    configuration)."""
+    import json
+
+    with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "dock_chains_kernel_traffic.json")) as f:
+        rec = json.load(f)
+    caps = {c["tile_config"]: c for c in rec["captures"]}
+    assert sorted(caps) == list(range(1, 13))
+    evals = {c["evaluations"] for c in caps.values()}
+    assert len(evals) == 1
+    for k, c in caps.items():
+        assert c["chain_kernel"] == bench.describe_tile_config(k)
+        assert c["dram_bytes_per_launch"] == c["dram_read_bytes"] + c["dram_write_bytes"]
+        assert abs(c["warp_instructions_per_eval"] - c["warp_instructions"] / c["evaluations"]) < 0.1
+    assert rec["systems_per_launch"] == 32 and len(rec["sources_sha256"]) == 64
