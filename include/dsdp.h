@@ -420,8 +420,15 @@ dsdp_status dsdp_gather_bench_device(const dsdp_grid_view* grid, const float* d_
  *     d_out_coords (NULL skips one).  Grid, box and trace fields are ignored.
  *   - Errors: DSDP_ERR_INVALID_ARG for n_chains above the limit or missing
  *     arrays, DSDP_ERR_DEVICE when a launch fails.
- *   - The first call on a device resolves the array's device address (with
- *     that device current); make that first call before capturing a stream.
+ *   - The first call on a device is a set-up call: it resolves the array's
+ *     device address (with that device current) and, under CUDA's lazy module
+ *     loading (the default), may load this library's rescoring kernels and
+ *     commit the array -- device memory the driver allocates.  Make that first
+ *     call outside any phase that must not allocate (a warm-up at start-up) and
+ *     before capturing a stream; later calls on that device allocate nothing.
+ *   - The resolved address is kept for the life of the process: do not use the
+ *     library across a cudaDeviceReset or after the primary context is
+ *     destroyed and re-created.
  *   - Every call shares the array and it keeps the last call's contents; no
  *     field has to start at zero, since each value read is written earlier in
  *     the same call.  Calls that overlap on the GPU (other streams, or other

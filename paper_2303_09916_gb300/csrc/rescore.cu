@@ -359,8 +359,12 @@ __global__ void noalloc_tables_kernel(DevJob job, DevJob* job_out, Tile* tiles_o
   }
 }
 
-// Device address of g_noalloc_scratch, resolved once per device (the host-side
-// symbol is only a stand-in and must never reach a kernel).
+// Device address of g_noalloc_scratch, resolved once per device by the first
+// call there (the host-side symbol is only a stand-in and must never reach a
+// kernel).  Under lazy module loading that first call may also load this
+// file's kernels and commit the array; the cached address is valid for the
+// life of the device's primary context, so the library is not used across a
+// device reset.
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};
 
