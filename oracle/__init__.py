@@ -81,6 +81,10 @@ def lib():
             "orc_apply_step": (None, [vp, dp, dp]),
             "orc_local_opt": (None, [vp, dp, ip, dp, d, i, i, dp, dp, dp]),
             "orc_opt_test": (None, [i, i, i, dp, dp, dp, dp, dp]),
+            "orc_opt_test_log": (None, [i, i, i, dp, dp, dp, dp, dp, dp, i, ip]),
+            "orc_local_opt_log": (None, [vp, dp, ip, dp, d, i, i, dp, dp, dp, dp, i, ip]),
+            "orc_mc_step_log": (None, [vp, dp, ip, dp, d, i, dp, dp, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.c_uint32, dp, dp, dp, dp, i, ip]),
             "orc_bfgs_update": (None, [i, dp, dp, dp]),
             "orc_philox": (None, [u32p, u32p, u32p]),
             "orc_unit_ball": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, dp]),
@@ -270,13 +274,49 @@ class Ligand:
         lib().orc_apply_step(self.h, _d(c)[1], sp)
         return c
 
-    def local_opt(self, grid: Grid, mode: int, optimizer: int, conf, opt=None):
+    def local_opt(self, grid: Grid, mode: int, optimizer: int, conf, opt=None, log=False):
+        """Returns (conf, E, evals, iters), plus the decisions taken (Decisions) when log."""
         c = np.array(conf, dtype=np.float64)
         o, op = _d(_opt_array(opt))
         out = np.zeros(3)
         m, n, og, h = grid.cargs()
-        lib().orc_local_opt(self.h, m, n, og, h, int(mode), int(optimizer), op, _d(c)[1], _d(out)[1])
-        return c, out[0], int(out[1]), int(out[2])
+        if not log:
+            lib().orc_local_opt(self.h, m, n, og, h, int(mode), int(optimizer), op, _d(c)[1], _d(out)[1])
+            return c, out[0], int(out[1]), int(out[2])
+        buf, cnt = _log_buffer(o)
+        lib().orc_local_opt_log(self.h, m, n, og, h, int(mode), int(optimizer), op, _d(c)[1], _d(out)[1],
+                                _d(buf)[1], len(buf), ctypes.byref(cnt))
+        return c, out[0], int(out[1]), int(out[2]), Decisions(buf, cnt.value)
+
+
+DECISION_KINDS = {0: "armijo", 1: "bb_best", 2: "metropolis", 3: "bfgs_curvature", 4: "bb_curvature"}
+
+
+class Decisions:
+    """Decisions a local optimisation or MC step took, in order: kind (see
+    DECISION_KINDS), margin (the quantity whose sign picks the branch) and scale
+    (|s||y| for the curvature tests, else 0)."""
+
+    def __init__(self, buf, count):
+        if count > len(buf):
+            raise RuntimeError(f"decision log overflow: {count} > {len(buf)}")
+        self.kind = buf[:count, 0].astype(np.int32)
+        self.margin = buf[:count, 1].copy()
+        self.scale = buf[:count, 2].copy()
+
+    def __len__(self):
+        return len(self.kind)
+
+    def taken(self):
+        """The branch of each decision: True for accept / update / new best."""
+        return np.where((self.kind == 0), self.margin <= 0,
+                        np.where((self.kind == 1) | (self.kind == 2), self.margin < 0, self.margin > 0))
+
+
+def _log_buffer(opt_arr):
+    # at most max_iters x (max_trials + 1) + 1 decisions per local optimisation, + 1 Metropolis
+    cap = int(opt_arr[0]) * (int(opt_arr[3]) + 2) + 8
+    return np.zeros((cap, 3)), ctypes.c_int()
 
 
 def dock_params_array(n_mc_steps, optimizer, temperature, box_lo, box_size, sites=None, site_radius=7.0):
@@ -309,16 +349,23 @@ def run_chain(lig: Ligand, grid: Grid, mode, dock_params, seed, chain, opt=None,
     return dict(best=best, e_best=out[0], evals=int(out[1]), trace_conf=tc, trace_rec=tr)
 
 
-def mc_step(lig: Ligand, grid: Grid, mode, dock_params, seed, chain, step, cur, e_cur, opt=None):
+def mc_step(lig: Ligand, grid: Grid, mode, dock_params, seed, chain, step, cur, e_cur, opt=None, log=False):
+    """One MC step replayed from (cur, e_cur): (state, energy, record[mode, accepted,
+    e_candidate, e_current, evals]), plus the decisions taken (Decisions) when log."""
     dp, dpp = _d(dock_params)
     o, op = _d(_opt_array(opt))
     c = np.array(cur, dtype=np.float64)
     e = ctypes.c_double(float(e_cur))
     rec = np.zeros(5)
     m, n, og, h = grid.cargs()
-    lib().orc_mc_step(lig.h, m, n, og, h, int(mode), dpp, op, int(seed), int(chain), int(step), _d(c)[1],
-                      ctypes.byref(e), _d(rec)[1])
-    return c, e.value, rec
+    if not log:
+        lib().orc_mc_step(lig.h, m, n, og, h, int(mode), dpp, op, int(seed), int(chain), int(step), _d(c)[1],
+                          ctypes.byref(e), _d(rec)[1])
+        return c, e.value, rec
+    buf, cnt = _log_buffer(o)
+    lib().orc_mc_step_log(lig.h, m, n, og, h, int(mode), dpp, op, int(seed), int(chain), int(step), _d(c)[1],
+                          ctypes.byref(e), _d(rec)[1], _d(buf)[1], len(buf), ctypes.byref(cnt))
+    return c, e.value, rec, Decisions(buf, cnt.value)
 
 
 def dock(lig: Ligand, grid: Grid, mode, dock_params, seed, n_chains, chain0=0, n_threads=1, opt=None):
@@ -350,15 +397,20 @@ def rescore_topk(lig: Ligand, rec_xyz, rec_type, confs, k, rmsd_cut=1.0):
     return scores, idx[:kept], terms[:kept]
 
 
-def opt_test(kind, optimizer, x0, A=None, b=None, opt=None):
+def opt_test(kind, optimizer, x0, A=None, b=None, opt=None, log=False):
     x = np.array(x0, dtype=np.float64)
     n = len(x)
     A_, Ap = _d(A if A is not None else np.zeros((1,)))
     b_, bp = _d(b if b is not None else np.zeros((1,)))
     o, op = _d(_opt_array(opt))
     out = np.zeros(3)
-    lib().orc_opt_test(int(kind), int(optimizer), n, Ap, bp, op, _d(x)[1], _d(out)[1])
-    return x, out[0], int(out[1]), int(out[2])
+    if not log:
+        lib().orc_opt_test(int(kind), int(optimizer), n, Ap, bp, op, _d(x)[1], _d(out)[1])
+        return x, out[0], int(out[1]), int(out[2])
+    buf, cnt = _log_buffer(o)
+    lib().orc_opt_test_log(int(kind), int(optimizer), n, Ap, bp, op, _d(x)[1], _d(out)[1], _d(buf)[1], len(buf),
+                           ctypes.byref(cnt))
+    return x, out[0], int(out[1]), int(out[2]), Decisions(buf, cnt.value)
 
 
 def bfgs_update(H, s, y):

@@ -596,7 +596,27 @@ struct Objective {
   virtual ~Objective() {}
 };
 
+// A decision the search takes by comparing two computed quantities, with its
+// margin: the quantity whose sign selects the branch.  Recorded (optionally)
+// so that a test can tell a near tie -- a branch FP32 and FP64 arithmetic may
+// take differently -- from a real disagreement.  kind and margin:
+//   0 Armijo test of a BFGS trial (Nocedal & Wright Alg. 6.1 with backtracking):
+//     E(x + alpha d) - (E(x) + c1 alpha g.d); the trial is accepted iff <= 0
+//   1 Barzilai-Borwein best iterate: E_new - E_best; a new best iff < 0
+//   2 Metropolis acceptance of an MC candidate: (E' - E) + T ln u; accepted iff < 0
+//     (equivalent to E' < E or u < exp(-(E' - E) / T) for u in [0, 1))
+//   3 BFGS curvature condition: y.s - min_curvature; H is updated iff > 0
+//   4 Barzilai-Borwein curvature: s.y; the BB1 step is taken iff > 0
+// scale: |s| |y| for kinds 3 and 4 (the size of the product whose sign is
+// tested), 0 otherwise (the energies' own scale applies).
+struct Decision {
+  int kind;
+  double margin;
+  double scale;
+};
+
 struct OptSettings {
+  std::vector<Decision>* log = nullptr;  // decisions taken, appended in order (recording only)
   int max_iters = 100;
   // BFGS (Nocedal & Wright, Algorithm 6.1 with backtracking Armijo search)
   double c1 = 1e-4;
@@ -661,6 +681,7 @@ OptResult bfgs(Objective& f, double* x, const OptSettings& st) {
       f.step(xt.data(), s.data());
       et = f.eval(xt.data(), gt.data());
       ++R.evals;
+      if (st.log) st.log->push_back(Decision{0, et - (e + st.c1 * alpha * gd), 0.0});
       if (et <= e + st.c1 * alpha * gd) {
         accepted = true;
         break;
@@ -675,6 +696,11 @@ OptResult bfgs(Objective& f, double* x, const OptSettings& st) {
     for (int i = 0; i < n; ++i) g[i] = gt[i];
     e = et;
     R.iters = it + 1;
+    if (st.log) {
+      double ss = 0.0, yy = 0.0;
+      for (int i = 0; i < n; ++i) ss += s[i] * s[i], yy += y[i] * y[i];
+      st.log->push_back(Decision{3, sy - st.min_curvature, std::sqrt(ss * yy)});
+    }
     if (sy > st.min_curvature) bfgs_update(n, H, s.data(), y.data());
   }
   R.e = e;
@@ -702,6 +728,11 @@ OptResult barzilai_borwein(Objective& f, double* x, const OptSettings& st) {
       sy += s[i] * (gn[i] - g[i]);
       ss += s[i] * s[i];
     }
+    if (st.log) {
+      double yy = 0.0;
+      for (int i = 0; i < n; ++i) yy += (gn[i] - g[i]) * (gn[i] - g[i]);
+      st.log->push_back(Decision{4, sy, std::sqrt(ss * yy)});
+    }
     if (sy > 0.0) {
       alpha = ss / sy;
       if (alpha < st.bb_alpha_min) alpha = st.bb_alpha_min;
@@ -712,6 +743,7 @@ OptResult barzilai_borwein(Objective& f, double* x, const OptSettings& st) {
     for (int i = 0; i < n; ++i) g[i] = gn[i];
     e = en;
     R.iters = it + 1;
+    if (st.log) st.log->push_back(Decision{1, e - ebest, 0.0});
     if (e < ebest) {
       ebest = e;
       for (int i = 0; i < nx; ++i) xbest[i] = x[i];
@@ -962,6 +994,8 @@ StepRecord mc_step(const Ligand& L, DockObjective& obj, const ChainRng& rng, con
   rec.e_candidate = r.e;
   const double u = rng.uniform(step, 0, 1);
   rec.accepted = (r.e < *e_cur) || (u < std::exp(-(r.e - *e_cur) / ds.temperature));
+  if (ds.opt.log)
+    ds.opt.log->push_back(Decision{2, u > 0.0 ? (r.e - *e_cur) + ds.temperature * std::log(u) : -1e300, 0.0});
   if (rec.accepted) {
     for (int i = 0; i < nx; ++i) cur[i] = cand[i];
     *e_cur = r.e;
@@ -1177,10 +1211,44 @@ void orc_local_opt(void* h, const double* maps, const int* n, const double* orig
   out[0] = r.e, out[1] = (double)r.evals, out[2] = r.iters;
 }
 
+// Copies a decision log into [cap][3] rows (kind, margin, scale); returns the
+// number of decisions taken (rows beyond cap are dropped).
+static int copy_log(const std::vector<Decision>& log, double* out, int cap) {
+  for (int i = 0; i < (int)log.size() && i < cap; ++i)
+    out[3 * i] = log[i].kind, out[3 * i + 1] = log[i].margin, out[3 * i + 2] = log[i].scale;
+  return (int)log.size();
+}
+
+// orc_local_opt with the decisions it takes (see Decision); *n_log = their count.
+void orc_local_opt_log(void* h, const double* maps, const int* n, const double* origin, double hh, int mode,
+                       int optimizer, const double* opt_params, double* conf, double* out, double* log_out,
+                       int log_cap, int* n_log) {
+  const Ligand& L = *(Ligand*)h;
+  Grid G{{n[0], n[1], n[2]}, {origin[0], origin[1], origin[2]}, hh, maps};
+  DockObjective obj(&L, &G, mode);
+  OptSettings st = opt_from(opt_params);
+  std::vector<Decision> log;
+  st.log = &log;
+  const OptResult r = optimizer == 0 ? bfgs(obj, conf, st) : barzilai_borwein(obj, conf, st);
+  out[0] = r.e, out[1] = (double)r.evals, out[2] = r.iters;
+  *n_log = copy_log(log, log_out, log_cap);
+}
+
 // Optimisers on test objectives.  kind 0: quadratic 0.5 x^T A x - b^T x; kind 1: Rosenbrock.
+// orc_opt_test_log also returns the decisions taken (see Decision).
+void orc_opt_test_log(int kind, int optimizer, int n, const double* A, const double* b, const double* opt_params,
+                      double* x, double* out, double* log_out, int log_cap, int* n_log);
 void orc_opt_test(int kind, int optimizer, int n, const double* A, const double* b, const double* opt_params,
                   double* x, double* out) {
-  const OptSettings st = opt_from(opt_params);
+  int n_log = 0;
+  orc_opt_test_log(kind, optimizer, n, A, b, opt_params, x, out, nullptr, 0, &n_log);
+}
+
+void orc_opt_test_log(int kind, int optimizer, int n, const double* A, const double* b, const double* opt_params,
+                      double* x, double* out, double* log_out, int log_cap, int* n_log) {
+  OptSettings st = opt_from(opt_params);
+  std::vector<Decision> log;
+  st.log = &log;
   OptResult r;
   if (kind == 0) {
     QuadObjective q(n, A, b);
@@ -1190,6 +1258,7 @@ void orc_opt_test(int kind, int optimizer, int n, const double* A, const double*
     r = optimizer == 0 ? bfgs(q, x, st) : barzilai_borwein(q, x, st);
   }
   out[0] = r.e, out[1] = (double)r.evals, out[2] = r.iters;
+  *n_log = copy_log(log, log_out, log_cap);
 }
 
 void orc_bfgs_update(int n, double* H, const double* s, const double* y) {
@@ -1266,6 +1335,27 @@ void orc_mc_step(void* h, const double* maps, const int* n, const double* origin
   rec_out[0] = r.mode, rec_out[1] = r.accepted, rec_out[2] = r.e_candidate, rec_out[3] = r.e_current;
   rec_out[4] = (double)r.evals;
 }
+
+// orc_mc_step with the decisions it takes (local optimisation, then Metropolis).
+void orc_mc_step_log(void* h, const double* maps, const int* n, const double* origin, double hh, int mode,
+                     const double* dock_params, const double* opt_params, uint64_t seed, uint32_t chain,
+                     uint32_t step, double* cur, double* e_cur, double* rec_out, double* log_out, int log_cap,
+                     int* n_log) {
+  const Ligand& L = *(Ligand*)h;
+  Grid G{{n[0], n[1], n[2]}, {origin[0], origin[1], origin[2]}, hh, maps};
+  DockSettings ds = dock_from(dock_params, opt_params);
+  std::vector<Decision> log;
+  ds.opt.log = &log;
+  DockObjective obj(&L, &G, mode);
+  ChainRng rng{{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)}, chain};
+  std::vector<double> best(7 + L.T);
+  double e_best = -1e300;
+  const StepRecord r = mc_step(L, obj, rng, ds, step, cur, e_cur, best.data(), &e_best);
+  rec_out[0] = r.mode, rec_out[1] = r.accepted, rec_out[2] = r.e_candidate, rec_out[3] = r.e_current;
+  rec_out[4] = (double)r.evals;
+  *n_log = copy_log(log, log_out, log_cap);
+}
+
 
 // A whole docking job: chains [chain0, chain0 + n_chains) split over n_threads.
 // best (n_chains x (7+T)), e_best (n_chains), evals (n_chains).

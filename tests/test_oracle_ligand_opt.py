@@ -357,3 +357,80 @@ def test_unit_ball_points():
     assert r2.max() <= 1.0
     assert abs(r2.mean() - 3 / 5) < 0.03  # E|b|^2 = 3/5 for the uniform ball
     assert np.abs(pts.mean(0)).max() < 0.06
+
+
+# ---------------------------------------------------------------- decision logs
+# The optional decision log records, for every branch the optimisers and the MC
+# step take, the quantity whose sign picks the branch.  The GPU parity tests use
+# it to tell a near tie from a real disagreement, so it is pinned here: against
+# closed forms on a one-dimensional quadratic, against the outcomes the
+# optimisers report, and it must not change any result.
+
+def test_bfgs_decision_log_on_a_1d_quadratic_matches_the_closed_form():
+    # f(x) = 0.5 a x^2 - b x from x0, H0 = 1, d = -g: trial alpha has
+    # x_t = x0 - alpha g0 and Armijo margin f(x_t) - f(x0) + c1 alpha g0^2
+    a, b, x0, c1 = 4.0, 1.0, 2.0, 1e-4
+    f = lambda x: 0.5 * a * x * x - b * x
+    g0 = a * x0 - b
+    x, e, evals, iters, log = oracle.opt_test(0, 0, np.array([x0]), np.array([[a]]), np.array([b]),
+                                              opt=dict(max_iters=1, c1=c1), log=True)
+    expect = []
+    alpha = 1.0
+    while True:
+        m = f(x0 - alpha * g0) - (f(x0) - c1 * alpha * g0 * g0)
+        expect.append(m)
+        if m <= 0:
+            break
+        alpha *= 0.5
+    arm = log.margin[log.kind == 0]
+    assert np.allclose(arm, expect, rtol=1e-12, atol=1e-12)
+    assert evals == 1 + len(expect)
+    # then the curvature test of the accepted step: y.s = a s^2 (minus the threshold)
+    s = -alpha * g0
+    curv = log.kind == 3
+    assert curv.sum() == 1
+    assert log.margin[curv][0] == pytest.approx(a * s * s - 1e-10, rel=1e-12)
+    assert log.scale[curv][0] == pytest.approx(abs(s) * abs(a * s), rel=1e-12)
+
+
+def test_decision_logs_agree_with_the_reported_outcomes_and_change_nothing():
+    rng = np.random.default_rng(3)
+    n = 6
+    M = rng.normal(size=(n, n))
+    A = M @ M.T + np.eye(n)
+    bvec = rng.normal(size=n)
+    for optimizer in (0, 1):
+        opt = dict(max_iters=25, bb_alpha0=0.05)
+        ref = oracle.opt_test(0, optimizer, np.ones(n), A, bvec, opt=opt)
+        x, e, evals, iters, log = oracle.opt_test(0, optimizer, np.ones(n), A, bvec, opt=opt, log=True)
+        assert np.array_equal(x, ref[0]) and e == ref[1] and evals == ref[2] and iters == ref[3]
+        taken = log.taken()
+        if optimizer == 0:
+            arm = log.kind == 0
+            assert arm.sum() == evals - 1  # one Armijo test per trial evaluation
+            assert taken[arm].sum() == iters  # one accepted trial per iteration
+            # convex quadratic: y.s = s^T A s >= 0 (the margin subtracts the 1e-10 threshold)
+            assert np.all(log.margin[log.kind == 3] + 1e-10 >= 0)
+        else:
+            assert (log.kind == 4).sum() == iters and (log.kind == 1).sum() == iters
+            assert np.all(log.margin[log.kind == 4] > 0)  # s^T A s > 0
+
+
+def test_mc_step_log_ends_with_the_metropolis_decision():
+    s, lig, rec_xyz, rec_t = _tiny_complex(2, n_lig=9, T=3, n_rec=120)
+    size = np.array([12.0, 12.0, 12.0])
+    grid = oracle.grid_build(rec_xyz, rec_t, np.zeros(3), size, 0.5)
+    dp = oracle.dock_params_array(6, 0, 1.2, -size / 2, size)
+    opt = dict(max_iters=10)
+    r = oracle.run_chain(lig, grid, 0, dp, 4, 1, opt=opt)
+    for st in range(1, 7):
+        cur, e_cur = r["trace_conf"][st - 1], r["trace_rec"][st - 1, 3]
+        c_ref, e_ref, rec_ref = oracle.mc_step(lig, grid, 0, dp, 4, 1, st, cur, e_cur, opt=opt)
+        c, e, rec, log = oracle.mc_step(lig, grid, 0, dp, 4, 1, st, cur, e_cur, opt=opt, log=True)
+        assert np.array_equal(c, c_ref) and e == e_ref and np.array_equal(rec, rec_ref)
+        assert log.kind[-1] == 2 and (log.kind == 2).sum() == 1
+        w = oracle.philox([1, st, 0, 0], [4, 0])
+        u = (int(w[1]) >> 8) / 2.0 ** 24
+        assert log.margin[-1] == pytest.approx((rec[2] - e_cur) + 1.2 * math.log(u), rel=1e-12, abs=1e-12)
+        assert bool(log.taken()[-1]) == bool(rec[1])
+        assert (log.kind == 0).sum() == int(rec[4]) - 1  # Armijo tests: every evaluation after the first
