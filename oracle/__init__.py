@@ -295,7 +295,7 @@ DECISION_KINDS = {0: "armijo", 1: "bb_best", 2: "metropolis", 3: "bfgs_curvature
 class Decisions:
     """Decisions a local optimisation or MC step took, in order: kind (see
     DECISION_KINDS), margin (the quantity whose sign picks the branch) and scale
-    (|s||y| for the curvature tests, else 0)."""
+    (|s|_1 (|g|_inf + |g'|_inf) for the curvature tests, else 0)."""
 
     def __init__(self, buf, count):
         if count > len(buf):

@@ -607,8 +607,9 @@ struct Objective {
 //     (equivalent to E' < E or u < exp(-(E' - E) / T) for u in [0, 1))
 //   3 BFGS curvature condition: y.s - min_curvature; H is updated iff > 0
 //   4 Barzilai-Borwein curvature: s.y; the BB1 step is taken iff > 0
-// scale: |s| |y| for kinds 3 and 4 (the size of the product whose sign is
-// tested), 0 otherwise (the energies' own scale applies).
+// scale: |s|_1 (|g|_inf + |g'|_inf) for kinds 3 and 4 -- the bound on how far
+// s.y moves when each gradient component moves by a fraction of its norm --,
+// 0 otherwise (the energies' own scale applies).
 struct Decision {
   int kind;
   double margin;
@@ -696,10 +697,11 @@ OptResult bfgs(Objective& f, double* x, const OptSettings& st) {
     for (int i = 0; i < n; ++i) g[i] = gt[i];
     e = et;
     R.iters = it + 1;
-    if (st.log) {
-      double ss = 0.0, yy = 0.0;
-      for (int i = 0; i < n; ++i) ss += s[i] * s[i], yy += y[i] * y[i];
-      st.log->push_back(Decision{3, sy - st.min_curvature, std::sqrt(ss * yy)});
+    if (st.log) {  // g is already the new gradient; the old one is g - y
+      double s1 = 0.0, gi = 0.0, go = 0.0;
+      for (int i = 0; i < n; ++i)
+        s1 += std::fabs(s[i]), gi = std::max(gi, std::fabs(g[i])), go = std::max(go, std::fabs(g[i] - y[i]));
+      st.log->push_back(Decision{3, sy - st.min_curvature, s1 * (gi + go)});
     }
     if (sy > st.min_curvature) bfgs_update(n, H, s.data(), y.data());
   }
@@ -729,9 +731,10 @@ OptResult barzilai_borwein(Objective& f, double* x, const OptSettings& st) {
       ss += s[i] * s[i];
     }
     if (st.log) {
-      double yy = 0.0;
-      for (int i = 0; i < n; ++i) yy += (gn[i] - g[i]) * (gn[i] - g[i]);
-      st.log->push_back(Decision{4, sy, std::sqrt(ss * yy)});
+      double s1 = 0.0, gi = 0.0, go = 0.0;
+      for (int i = 0; i < n; ++i)
+        s1 += std::fabs(s[i]), gi = std::max(gi, std::fabs(gn[i])), go = std::max(go, std::fabs(g[i]));
+      st.log->push_back(Decision{4, sy, s1 * (gi + go)});
     }
     if (sy > 0.0) {
       alpha = ss / sy;

@@ -1,0 +1,321 @@
+"""Monte Carlo chains and local optimisations on the GPU against the FP64 oracle,
+for ligands on every chain-kernel tile: one atom per lane (16 atoms), two atoms
+per lane (40 and 60 atoms, 10 and 15 torsions) and batches that mix both (the
+mixed-tile kernel).
+
+FP32 and FP64 arithmetic may take different branches where a decision is a
+near tie, after which the trajectories separate.  Every separation is
+therefore explained or the test fails: at a chain's first divergence from the
+oracle's own run, the step is replayed on the oracle from the GPU's state at
+that point (A) and from the oracle's own state (B), both recording the margin
+of every decision they take (the Armijo test, Barzilai-Borwein's best iterate
+and curvature test, BFGS's curvature test, the Metropolis acceptance):
+  * if the GPU reproduces A, the GPU did exactly what the oracle does from
+    the GPU's state, and the separation comes from a decision that A and B
+    take differently; that decision's margin must be within its tolerance;
+  * otherwise the GPU took a branch other than A's from the same state, and
+    some decision of A must be a near tie.
+Tolerances: energies E_REL * max(sum_i |e_i|, 1) each, so a margin of two
+energies is a tie within twice that; a curvature product s.y within
+G_REL * |s|_1 (|g|_inf + |g'|_inf).
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_09916_gb300 import dsdp  # noqa: E402
+
+from gpu_util import E_REL, G_REL, Complex  # noqa: E402
+
+# (receptor atoms, box edge, ligand atoms, torsions, seed): one and two atoms per lane
+SHAPES = {"16at": (1500, 14.0, 16, 4, 5), "40at": (2500, 18.0, 40, 10, 6), "60at": (2500, 20.0, 60, 15, 8)}
+_complexes = {}
+
+
+def complex_for(shape):
+    if shape not in _complexes:
+        _complexes[shape] = Complex(*SHAPES[shape][:4], seed=SHAPES[shape][4])
+    return _complexes[shape]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = dsdp.dsdp_create(0)
+    yield c
+    dsdp.dsdp_destroy(c)
+
+
+def _grid(ctx, cx, mode=dsdp.DSDP_GRID_EQ4):
+    og = cx.oracle_grid()
+    maps = og.maps if mode == dsdp.DSDP_GRID_EQ4 else og.maps[..., :1]
+    return dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type,
+                                    dsdp.make_box(cx.center, cx.size, cx.spacing), dsdp.DSDP_MAP_F32, mode,
+                                    np.ascontiguousarray(maps, dtype=np.float32))
+
+
+def _run_job(ctx, grid, lig, T, **kw):
+    params = dsdp.make_params(**kw)
+    jid = dsdp.dsdp_dock_submit(ctx, grid, lig, params)
+    return dsdp.dsdp_dock_poll(ctx, jid, dsdp.result_buffers(lig.n_atoms, T, params), wait_ms=-1)
+
+
+def energy_tol(cx, og, mode, *poses):
+    return E_REL * max([cx.abs_terms(og, mode, p) for p in poses] + [1.0])
+
+
+def _normalised_margin(log, i, tol_e):
+    k = int(log.kind[i])
+    tol = 2.0 * tol_e if k in (0, 1, 2) else G_REL * max(float(log.scale[i]), 1e-30)
+    return abs(float(log.margin[i])) / tol
+
+
+def explain_divergence(log_a, log_b, gpu_matches_a, tol_e):
+    """(explained, description) of a divergence; see the module docstring."""
+    if gpu_matches_a:
+        ta, tb = log_a.taken(), log_b.taken()
+        for i in range(min(len(log_a), len(log_b))):
+            if log_a.kind[i] != log_b.kind[i] or ta[i] != tb[i]:
+                r = min(_normalised_margin(log_a, i, tol_e), _normalised_margin(log_b, i, tol_e))
+                name = oracle.DECISION_KINDS[int(log_a.kind[i])]
+                return r <= 1.0, (f"GPU = oracle from the GPU state; decision {i} ({name}) differs from the "
+                                  f"oracle's own run, margin {r:.3f} of its tolerance")
+        return False, "GPU = oracle from the GPU state, and no decision differs from the oracle's own run"
+    if len(log_a) == 0:
+        return False, "GPU departs from the oracle's replay of its state, which took no decision"
+    rs = [_normalised_margin(log_a, i, tol_e) for i in range(len(log_a))]
+    i = int(np.argmin(rs))
+    return rs[i] <= 1.0, (f"GPU departs from the oracle's replay of its state; nearest tie: decision {i} "
+                          f"({oracle.DECISION_KINDS[int(log_a.kind[i])]}) at {rs[i]:.3f} of its tolerance")
+
+
+# ---------------------------------------------------------------- local optimisation
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("optimizer,mode", [(dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ4),
+                                            (dsdp.DSDP_OPT_BB, dsdp.DSDP_GRID_EQ4),
+                                            (dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ3)])
+def test_local_opt_short_horizon(ctx, shape, optimizer, mode):
+    """The first local optimisation of each chain (step 0) after k = 0, 1, 2, 3, 5, 10
+    iterations.  k = 0 is a pure evaluation of the Philox-drawn pose: every chain
+    agrees.  For k = 1, 2, 3 every chain agrees with the oracle or its divergence
+    is an explained near tie (module docstring; A starts from the FP32-rounded
+    start, within an ulp of the GPU's own).  For every k each GPU result is
+    valid: its reported energy is the oracle's score of the pose it reports, and
+    no worse than the start.  Eq. 3 maps (score maps only, the gradient of the
+    interpolant) run the chain kernel's Eq. 3 path."""
+    cx = complex_for(shape)
+    og = cx.oracle_grid()
+    grid = _grid(ctx, cx, mode)
+    nc, nx = 32, 7 + cx.T
+    dp = oracle.dock_params_array(1, optimizer, 1.2, cx.box_lo(), cx.size)
+    starts = np.array([oracle.chain_init(cx.olig, dp, 7, c) for c in range(nc)])
+    starts32 = starts.astype(np.float32).astype(np.float64)
+    e_start = np.array([cx.olig.score_grid(og, mode, c)[0].sum() for c in starts])
+    tol0 = np.array([energy_tol(cx, og, mode, c) for c in starts])
+    agree, flips = {}, []
+    try:
+        e0, _ = dsdp.dsdp_score_eval(ctx, grid, cx.lig, starts)
+        agree[0] = int(np.sum(np.abs(e0 - e_start) <= tol0))
+        for iters in (1, 2, 3, 5, 10):
+            res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=1, n_opt_iters=iters, seed=7,
+                           optimizer=optimizer, trace=1, top_k=1)
+            a = 0
+            for c in range(nc):
+                e_gpu = float(res["trace"][c, 0, nx + 1])
+                pose = res["trace"][c, 0, :nx].astype(np.float64)
+                tol = max(energy_tol(cx, og, mode, pose), tol0[c])
+                # validity: the reported energy is the score of the reported pose, and a descent
+                assert abs(cx.olig.score_grid(og, mode, pose)[0].sum() - e_gpu) <= tol, (iters, c)
+                assert e_gpu <= e_start[c] + tol0[c], (iters, c)
+                o = dict(max_iters=iters)
+                _, e_b, _, _, log_b = cx.olig.local_opt(og, mode, optimizer, starts[c], opt=o, log=True)
+                if abs(e_gpu - e_b) <= tol:
+                    a += 1
+                    continue
+                if iters > 3:
+                    continue
+                _, e_a, _, _, log_a = cx.olig.local_opt(og, mode, optimizer, starts32[c], opt=o, log=True)
+                ok, why = explain_divergence(log_a, log_b, abs(e_gpu - e_a) <= tol, tol)
+                flips.append((iters, c, why))
+                assert ok, (iters, c, e_gpu, e_a, e_b, why)
+            agree[iters] = a
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    print(f"{shape}, optimizer {optimizer}, maps {'eq4' if mode == dsdp.DSDP_GRID_EQ4 else 'eq3'}: "
+          f"chains agreeing with the oracle after k iterations {agree} (of {nc})")
+    for f in flips:
+        print("  explained divergence (k, chain, why):", f)
+    assert agree[0] == nc, agree
+
+
+# ---------------------------------------------------------------- Monte Carlo chains
+def check_traces(cx, og, res, nc, S, iters, optimizer, seed, label):
+    """Step-for-step comparison of GPU chain traces with the oracle's own chains:
+    mutation modes bit-exact at every step, every GPU state's energy the oracle's
+    score of that state, and each chain's first divergence explained.  Also each
+    chain's best energy is the oracle's score of its best pose.  Returns the
+    steps agreeing before each chain's first divergence."""
+    nx = 7 + cx.T
+    tr = res["trace"]
+    dp = oracle.dock_params_array(S, optimizer, 1.2, cx.box_lo(), cx.size)
+    o = dict(max_iters=iters)
+    agree_steps, notes = [], []
+    for c in range(nc):
+        ref = oracle.run_chain(cx.olig, og, 0, dp, seed, c, opt=o)
+        first_div = S + 1
+        for s in range(S + 1):
+            if s > 0:
+                assert int(tr[c, s, nx + 2]) == int(ref["trace_rec"][s, 0]), (label, c, s, "mutation mode")
+            pose = tr[c, s, :nx].astype(np.float64)
+            tol = energy_tol(cx, og, 0, pose)
+            assert abs(cx.olig.score_grid(og, 0, pose)[0].sum() - tr[c, s, nx + 1]) <= tol, (label, c, s)
+            if first_div <= S:
+                continue
+            e_gpu, acc_gpu = float(tr[c, s, nx + 0]), int(tr[c, s, nx + 3])
+            if s > 0:
+                prev = tr[c, s - 1, :nx].astype(np.float64)
+                tol = max(tol, energy_tol(cx, og, 0, prev))
+            if abs(e_gpu - ref["trace_rec"][s, 2]) <= tol and acc_gpu == int(ref["trace_rec"][s, 1]):
+                continue
+            first_div = s
+            if s == 0:
+                start = oracle.chain_init(cx.olig, dp, seed, c)
+                _, e_a, _, _, log_a = cx.olig.local_opt(og, 0, optimizer, start.astype(np.float32).astype(np.float64),
+                                                        opt=o, log=True)
+                _, _, _, _, log_b = cx.olig.local_opt(og, 0, optimizer, start, opt=o, log=True)
+                match_a = abs(e_gpu - e_a) <= tol
+            else:
+                e_prev = float(tr[c, s - 1, nx + 1])
+                _, _, rec_a, log_a = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, prev, e_prev, opt=o, log=True)
+                _, _, _, log_b = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, ref["trace_conf"][s - 1],
+                                                ref["trace_rec"][s - 1, 3], opt=o, log=True)
+                match_a = abs(e_gpu - rec_a[2]) <= tol and acc_gpu == int(rec_a[1])
+            ok, why = explain_divergence(log_a, log_b, match_a, tol)
+            notes.append((c, s, why))
+            assert ok, (label, c, s, why)
+        agree_steps.append(first_div)
+        e_best = float(res["chain_best_e"][c])
+        best = res["chain_best_conf"][c].astype(np.float64)
+        assert abs(cx.olig.score_grid(og, 0, best)[0].sum() - e_best) <= energy_tol(cx, og, 0, best), (label, c)
+    print(f"{label}: steps agreeing before the first separation per chain: {agree_steps}")
+    for n in notes:
+        print("  explained divergence (chain, step, why):", n)
+    return agree_steps
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("optimizer", [dsdp.DSDP_OPT_BFGS, dsdp.DSDP_OPT_BB])
+def test_chains_step_for_step(ctx, shape, optimizer):
+    """Identical Philox streams, short runs (5 MC steps, one BFGS / two BB
+    iterations per local optimisation): every mutation matches exactly, every
+    accepted GPU state's energy is the oracle's score of that state, and the
+    chains agree with the oracle step by step until a divergence that is an
+    explained near tie."""
+    cx = complex_for(shape)
+    og = cx.oracle_grid()
+    grid = _grid(ctx, cx)
+    S, nc = 5, 16
+    iters = 1 if optimizer == dsdp.DSDP_OPT_BFGS else 2
+    try:
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=7,
+                       optimizer=optimizer, trace=1, top_k=4)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    check_traces(cx, og, res, nc, S, iters, optimizer, 7, f"{shape} optimizer {optimizer}")
+
+
+@pytest.mark.parametrize("shape,nc,S", [("16at", 24, 40), ("40at", 12, 20), ("60at", 12, 20)])
+def test_replay_one_step_transitions(ctx, shape, nc, S):
+    """Long chains (100 BFGS iterations per local optimisation): re-seed the oracle
+    with the GPU state at each step start and replay one step.  The mutation must
+    match exactly, the Metropolis decision must follow from the GPU's own
+    energies, an accepted pose's energy must equal the oracle's score of that
+    pose.  The candidate energies are compared with the agreement of the oracle
+    with itself when its start is moved by one FP32 ulp (the separation of
+    100-iteration trajectories at near ties is a property of the optimiser)."""
+    import math
+
+    cx = complex_for(shape)
+    og = cx.oracle_grid()
+    grid = _grid(ctx, cx)
+    iters = 100
+    try:
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=11, trace=1,
+                       top_k=4)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    nx = 7 + cx.T
+    tr = res["trace"].astype(np.float64)
+    dp = oracle.dock_params_array(S, 0, 1.2, cx.box_lo(), cx.size)
+    n_steps = n_match = n_base = 0
+    for c in range(nc):
+        for s in range(1, S + 1):
+            cur, e_cur = tr[c, s - 1, :nx], tr[c, s - 1, nx + 1]
+            _, _, rec = oracle.mc_step(cx.olig, og, 0, dp, 11, c, s, cur, e_cur, opt=dict(max_iters=iters))
+            nudged = cur.copy()
+            nudged[:3] = np.nextafter(cur[:3].astype(np.float32), np.float32(np.inf)).astype(np.float64)
+            _, _, rec2 = oracle.mc_step(cx.olig, og, 0, dp, 11, c, s, nudged, e_cur, opt=dict(max_iters=iters))
+            g_cand, g_cur, g_mode, g_acc = tr[c, s, nx:nx + 4]
+            assert int(g_mode) == int(rec[0])
+            # Metropolis from the GPU's energies and the Philox uniform of this step
+            w = oracle.philox([c, s, 0, 0], [11, 0])
+            u = (int(w[1]) >> 8) / 2.0 ** 24
+            p_acc = 1.0 if g_cand < e_cur else math.exp(-(g_cand - e_cur) / 1.2)
+            if abs(u - p_acc) > 1e-5 and g_cand != e_cur:
+                assert bool(g_acc) == (u < p_acc), (c, s)
+            if g_acc:
+                tol = energy_tol(cx, og, 0, tr[c, s, :nx])
+                assert abs(cx.olig.score_grid(og, 0, tr[c, s, :nx])[0].sum() - g_cand) <= tol, (c, s)
+            tol = energy_tol(cx, og, 0, cur)
+            n_steps += 1
+            n_match += abs(rec[2] - g_cand) <= tol
+            n_base += abs(rec[2] - rec2[2]) <= tol
+    print(f"{shape} replay: GPU vs oracle candidate energies agree on {n_match}/{n_steps} steps; "
+          f"oracle vs oracle nudged by one FP32 ulp: {n_base}/{n_steps}")
+    assert n_match >= n_base - 0.1 * n_steps
+
+
+def test_mixed_tile_batch_against_the_oracle(ctx):
+    """Ligands of 18, 33 and 60 atoms submitted together run in one batch: the
+    mixed-tile chain kernel (one- and two-atoms-per-lane chains in one launch).
+    Short chains are checked step for step against the oracle (module
+    docstring); longer ones on their results: every chain's best energy is the
+    oracle's score of its best pose, and the top-k equals the oracle's FP64
+    rescoring of the chains' best poses (scores within 1e-10, chain order
+    identical)."""
+    shapes = [(1500, 16.0, 18, 5, 12), (1500, 16.0, 33, 9, 13), (2500, 20.0, 60, 15, 8)]
+    cxs = [Complex(*s[:4], seed=s[4]) for s in shapes]
+    grids = [_grid(ctx, cx) for cx in cxs]
+    try:
+        for S, iters, trace in ((5, 1, 1), (12, 30, 0)):
+            params = [dsdp.make_params(n_chains=24, n_mc_steps=S, n_opt_iters=iters, seed=3 + i, trace=trace,
+                                       top_k=9) for i in range(len(cxs))]
+            b0 = dsdp.dsdp_get_stats(ctx)["batches"]
+            ids = dsdp.dsdp_dock_submit_many(ctx, grids, [cx.lig for cx in cxs], params)
+            res = [dsdp.dsdp_dock_poll(ctx, j, dsdp.result_buffers(cx.lig.n_atoms, cx.T, p), wait_ms=-1)
+                   for j, cx, p in zip(ids, cxs, params)]
+            assert dsdp.dsdp_get_stats(ctx)["batches"] - b0 == 1  # one launch holds all three
+            for i, (cx, r) in enumerate(zip(cxs, res)):
+                og = cx.oracle_grid()
+                label = f"mixed batch, {cx.lig.n_atoms} atoms, {S} x {iters}"
+                if trace:
+                    check_traces(cx, og, r, 24, S, iters, dsdp.DSDP_OPT_BFGS, 3 + i, label)
+                else:
+                    for c in range(24):
+                        best = r["chain_best_conf"][c].astype(np.float64)
+                        e = cx.olig.score_grid(og, 0, best)[0].sum()
+                        assert abs(e - float(r["chain_best_e"][c])) <= energy_tol(cx, og, 0, best), (label, c)
+                confs = r["chain_best_conf"].astype(np.float64)
+                _, idx, terms = oracle.rescore_topk(cx.olig, cx.rec_xyz64, cx.rec.xs_type, confs, k=9, rmsd_cut=1.0)
+                assert list(r["chain"]) == list(idx), label
+                assert np.allclose(r["score"], terms[:, 0], rtol=1e-10, atol=1e-12), label
+                assert np.allclose(r["inter"], terms[:, 1], rtol=1e-10, atol=1e-12), label
+                assert np.allclose(r["intra"], terms[:, 2], rtol=1e-10, atol=1e-12), label
+    finally:
+        for g in grids:
+            dsdp.dsdp_grid_free(ctx, g)

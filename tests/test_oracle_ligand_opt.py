@@ -390,7 +390,7 @@ def test_bfgs_decision_log_on_a_1d_quadratic_matches_the_closed_form():
     curv = log.kind == 3
     assert curv.sum() == 1
     assert log.margin[curv][0] == pytest.approx(a * s * s - 1e-10, rel=1e-12)
-    assert log.scale[curv][0] == pytest.approx(abs(s) * abs(a * s), rel=1e-12)
+    assert log.scale[curv][0] == pytest.approx(abs(s) * (abs(g0) + abs(g0 + a * s)), rel=1e-12)
 
 
 def test_decision_logs_agree_with_the_reported_outcomes_and_change_nothing():
