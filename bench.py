@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--serve-streams", type=int, default=8, help="batches in flight (one per stream)")
     p.add_argument("--no-forms", dest="forms", action="store_false",
                    help="skip the one-job-per-launch and uneven-batch (CUDA graph) measurements")
+    p.add_argument("--gather-bench", action="store_true",
+                   help="run the L2-gather microbenchmark alone on one typical-4k system's maps and print its JSON line")
     p.add_argument("--sweep", action="store_true",
                    help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
     p.add_argument("--no-pipeline", dest="pipeline", action="store_false",
@@ -243,6 +245,49 @@ def chain_kernel_capture(batch, map_dtype, chain_kernel):
     return None
 
 
+def mufu_per_eval(n_pairs, n_bodies):
+    # special-function (MUFU) operations of one evaluation: per intra pair a
+    # reciprocal square root and two exp2; per torsion body sin and cos of the
+    # half angle; one reciprocal square root normalising the orientation
+    return 3 * n_pairs + 2 * (n_bodies - 1) + 1
+
+
+def mufu_peak_per_s(sm_mhz):
+    # 152 SMs x 16 special-function results per clock (4 per SM sub-partition)
+    return 152 * 16 * sm_mhz * 1e6
+
+
+def chain_roofline(gather_bytes, flops, mufu_ops, chain_s, gather_gbs, peaks, peaks_src, sm_mhz, capture):
+    """The chain kernel's roofline as the maximum of its three bounds -- corner
+    gathers at the measured HBM copy bandwidth, FP32 FMA work at the FP32 peak,
+    special-function work at the MUFU peak -- per launch: `bound` names the
+    binding one, `achieved` its algorithmic work / the launch's event-timed
+    duration, `frac` = achieved / peak.  The gather bound is also given against
+    the L2-gather microbenchmark (the same random 8-corner reads, no arithmetic)."""
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    bounds = {"gather_hbm": gather_bytes / hbm, "fp32_fma": flops / (fp32_peak_tflops(sm_mhz) * 1e12),
+              "mufu": mufu_ops / mufu_peak_per_s(sm_mhz)}
+    binding = max(bounds, key=bounds.get)
+    if binding == "gather_hbm":
+        out = {"bound": "hbm", "achieved": gather_bytes / chain_s / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+               "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks_src})"}
+    elif binding == "fp32_fma":
+        out = {"bound": "alu", "achieved": flops / chain_s / 1e12, "peak": fp32_peak_tflops(sm_mhz),
+               "unit": "TFLOP/s", "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    else:
+        out = {"bound": "alu", "achieved": mufu_ops / chain_s / 1e12, "peak": mufu_peak_per_s(sm_mhz) / 1e12,
+               "unit": "Tops/s (MUFU)", "peak_source": f"derived: 152 SMs x 16 MUFU x {sm_mhz:.0f} MHz"}
+    out["frac"] = out["achieved"] / out["peak"]
+    out.update({"kernel": "dock_chains_kernel", "binding": binding,
+                "traffic": capture["dram_bytes_per_launch"] if capture else None,
+                "traffic_unit": "DRAM bytes per launch (ncu)",
+                "algorithmic": {"gather_bytes": gather_bytes, "fp32_flop": flops, "mufu_ops": mufu_ops},
+                "bounds_ms": {k: 1e3 * v for k, v in bounds.items()}, "launch_ms": 1e3 * chain_s,
+                "frac_of_gather_microbench": gather_bytes / chain_s / 1e9 / gather_gbs,
+                "gather_microbench_gbs": gather_gbs})
+    return out
+
+
 def issue_peak_per_s(sm_mhz):
     # 152 SMs x 4 schedulers x one warp instruction per cycle
     return 152 * 4 * sm_mhz * 1e6
@@ -251,6 +296,48 @@ def issue_peak_per_s(sm_mhz):
 def fp32_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def gather_microbench(dsdp, torch, dev, g_view, dtype, stream, npts=1 << 20, reps=16):
+    """The L2-gather roofline: 1 M threads x 16 random 8-corner gathers (one map
+    type each) over the maps of one system, no arithmetic; algorithmic bytes /
+    event-timed duration (GB/s), 5 launches after 3 untimed."""
+    sptr = stream.cuda_stream
+    rng = np.random.default_rng(0)
+    pts = (np.array(g_view.origin) + rng.uniform(0, (np.array(g_view.n) - 1) * g_view.spacing, size=(npts, 3))).astype(
+        np.float32)
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_ty = torch.from_numpy(rng.integers(0, 8, npts).astype(np.uint8)).to(dev)
+    d_out = torch.empty(npts, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        dsdp.dsdp_gather_bench_device(g_view, d_pts.data_ptr(), d_ty.data_ptr(), npts, reps, d_out.data_ptr(), sptr)
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ga.record(stream)
+    for _ in range(5):
+        dsdp.dsdp_gather_bench_device(g_view, d_pts.data_ptr(), d_ty.data_ptr(), npts, reps, d_out.data_ptr(), sptr)
+    gb.record(stream)
+    torch.cuda.synchronize()
+    return 5 * npts * reps * (128 if dtype == 0 else 64) / (ga.elapsed_time(gb) * 1e-3) / 1e9
+
+
+def run_gather_bench(args):
+    """The gather microbenchmark alone on the first typical-4k system's maps
+    (the command the committed ncu capture of gather_bench_kernel runs)."""
+    import torch
+    from paper_2303_09916_gb300 import dsdp
+
+    dev = 0
+    torch.cuda.set_device(dev)
+    (seed, rec, lig), = systems(0, 1)
+    dtype = {"f32": dsdp.DSDP_MAP_F32, "bf16": dsdp.DSDP_MAP_BF16, "f16": dsdp.DSDP_MAP_F16}[args.map_dtype]
+    j, keep = make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dtype, N_CHAINS, N_STEPS, N_ITERS,
+                              TOP_K)
+    stream = torch.cuda.current_stream()
+    build_grid(dsdp, keep["grid"], dtype, stream.cuda_stream)
+    gbs = gather_microbench(dsdp, torch, dev, j.grid, dtype, stream)
+    return {"metric": "random 8-corner map gathers, algorithmic GB/s", "value": gbs, "unit": "GB/s",
+            "map_dtype": args.map_dtype, "maps_bytes": int(keep["grid"]["maps"].numel()),
+            "points": 1 << 20, "repeats": 16}
 
 
 # ---------------------------------------------------------------- device-resident path
@@ -413,34 +500,17 @@ def run_device(args, rank, world, dev, dist):
     # every slot docked the same systems with the same seeds: the same evaluations
     same = all([int(o["evals"].sum().item()) for o in sl["outs"]] == evals for sl in slots[1:])
     flops = sum(ev * flops_per_eval(li["n_atoms"], li["n_pairs"], li["n_bodies"]) for ev, li in zip(evals, lig_info))
+    mufu = sum(ev * mufu_per_eval(li["n_pairs"], li["n_bodies"]) for ev, li in zip(evals, lig_info))
     gather_bytes = sum(ev * li["n_atoms"] * (128 if dtype == 0 else 64) for ev, li in zip(evals, lig_info))
     results_ok = same and all(int(o["n"].item()) >= 1 and bool(torch.isfinite(o["score"][: int(o["n"].item())]).all())
                               for sl in slots for o in sl["outs"])
     jobs = slots[0]["jobs"]
-    # gather microbenchmark on the first system's maps (the L2-gather roofline)
-    g_view = jobs[0].grid
-    npts = 1 << 20
-    rng = np.random.default_rng(0)
-    pts = (np.array(g_view.origin) + rng.uniform(0, (np.array(g_view.n) - 1) * SPACING, size=(npts, 3))).astype(
-        np.float32)
-    d_pts = torch.from_numpy(pts).to(dev)
-    d_ty = torch.from_numpy(rng.integers(0, 8, npts).astype(np.uint8)).to(dev)
-    d_out = torch.empty(npts, dtype=torch.float32, device=dev)
-    reps = 16
-    for _ in range(3):
-        dsdp.dsdp_gather_bench_device(g_view, d_pts.data_ptr(), d_ty.data_ptr(), npts, reps, d_out.data_ptr(), sptr)
-    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ga.record(stream)
-    for _ in range(5):
-        dsdp.dsdp_gather_bench_device(g_view, d_pts.data_ptr(), d_ty.data_ptr(), npts, reps, d_out.data_ptr(), sptr)
-    gb.record(stream)
-    torch.cuda.synchronize()
-    gather_gbs = 5 * npts * reps * (128 if dtype == 0 else 64) / (ga.elapsed_time(gb) * 1e-3) / 1e9
+    gather_gbs = gather_microbench(dsdp, torch, dev, jobs[0].grid, dtype, stream)  # the first system's maps
     for pl in plans:
         dsdp.dsdp_plan_destroy(None, pl)
     return dict(tile_config=tile_config, elapsed_ms=elapsed_ms, serial_ms=serial_ms, grid_ms=grid_ms, chain_ms=chain_ms,
                 rescore_ms=rescore_ms,
-                total_evals=total_evals, flops=flops, gather_bytes=gather_bytes, clocks=clk,
+                total_evals=total_evals, flops=flops, mufu=mufu, gather_bytes=gather_bytes, clocks=clk,
                 launches_per_step=args.batch + n_plan_kernels, results_ok=results_ok, gather_gbs=gather_gbs)
 
 
@@ -637,6 +707,103 @@ def run_uneven_graph(args, dev, steps=3):
                 results_ok=ok)
 
 
+def _timed_plan(dsdp, torch, items, dtype, sptr, steps, optimizer=0):
+    """Grid builds + one plan launch (chains, FP64 rescoring, top-k) of all the
+    items, timed over `steps` repetitions after one untimed run: seconds per step."""
+    plan = dsdp.dsdp_plan_create(None, [j for j, _ in items], 0, 0)
+    try:
+        for _, keep in items:
+            build_grid(dsdp, keep["grid"], dtype, sptr)
+        dsdp.dsdp_plan_launch(plan, sptr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(steps):
+            for _, keep in items:
+                build_grid(dsdp, keep["grid"], dtype, sptr)
+            dsdp.dsdp_plan_launch(plan, sptr)
+        b.record()
+        torch.cuda.synchronize()
+    finally:
+        dsdp.dsdp_plan_destroy(None, plan)
+    return a.elapsed_time(b) * 1e-3 / steps
+
+
+def run_configs(args, rank, dev, steps=2):
+    """The other workloads of the method, each timed as grid builds + one plan
+    launch (chains, FP64 rescoring, top-k) on one stream:
+      map_dtype: the typical-4k batch with BF16 and FP16 maps (FP32
+        accumulation).  Error stated per dtype: each chain's best search energy
+        against the same pose scored on FP32 maps by the FP32 score kernel (which
+        matches the FP64 oracle within 1e-4 of the term scale), relative to
+        max(|E|, 1), median / p95 / max over all chains; and the top-1 FP64
+        score against the FP32-map run's (median |difference| over systems);
+      optimizer_bb: the typical-4k batch with Barzilai-Borwein local
+        optimisation (the paper's, Sec. 2 second modification; 100 iterations);
+      plain_2k: the plain-method workload (2,000-atom receptor, 20 A box -> 54^3
+        maps, 20-atom ligand with 4 torsions, 64 chains x 100 steps): one system
+        per launch (its latency) and `--batch` systems per launch."""
+    import torch
+    from paper_2303_09916_gb300 import dsdp, synth
+
+    sptr = torch.cuda.current_stream().cuda_stream
+    sysl = systems(rank, args.batch)
+    out = {}
+    # ---- map storage precision
+    runs = {}
+    for name, dtype in (("f32", dsdp.DSDP_MAP_F32), ("bf16", dsdp.DSDP_MAP_BF16), ("f16", dsdp.DSDP_MAP_F16)):
+        items = [make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dtype, N_CHAINS, N_STEPS, N_ITERS,
+                                 TOP_K) for seed, rec, lig in sysl]
+        sec = _timed_plan(dsdp, torch, items, dtype, sptr, steps)
+        evals = sum(int(k["evals"].sum().item()) for _, k in items)
+        runs[name] = (items, dict(systems_per_s=len(items) / sec, evals_per_s=evals / sec))
+    f32_items = runs["f32"][0]
+    for name in ("bf16", "f16"):
+        items, row = runs[name]
+        rel, top1 = [], []
+        for (j32, k32), (j, k) in zip(f32_items, items):
+            e32 = torch.empty(N_CHAINS, dtype=torch.float32, device=dev)
+            dsdp.dsdp_score_eval_device(j32.grid, k["blob"], k["d_blob"].data_ptr(), k["conf"].data_ptr(), N_CHAINS,
+                                        e32.data_ptr(), 0, dsdp.DSDP_TERM_ALL, sptr)
+            torch.cuda.synchronize()
+            e_red = k["e"].cpu().numpy().astype(np.float64)
+            e_ref = e32.cpu().numpy().astype(np.float64)
+            rel.extend((np.abs(e_red - e_ref) / np.maximum(np.abs(e_ref), 1.0)).tolist())
+            top1.append(abs(float(k["score"][0].item()) - float(k32["score"][0].item())))
+        row["search_energy_rel_err_vs_f32_maps"] = dict(median=float(np.median(rel)),
+                                                        p95=float(np.percentile(rel, 95)), max=float(np.max(rel)))
+        row["top1_fp64_score_abs_diff_vs_f32_run_median"] = float(np.median(top1))
+        row["rescoring"] = "FP64 gridless (exact for the reported poses)"
+        out.setdefault("map_dtype", {})[name] = row
+    out["map_dtype"]["f32"] = runs["f32"][1]
+    del runs, f32_items
+    # ---- Barzilai-Borwein (the paper's local optimiser)
+    items = [make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dsdp.DSDP_MAP_F32, N_CHAINS, N_STEPS,
+                             N_ITERS, TOP_K, optimizer=dsdp.DSDP_OPT_BB) for seed, rec, lig in sysl]
+    sec = _timed_plan(dsdp, torch, items, dsdp.DSDP_MAP_F32, sptr, steps)
+    evals = sum(int(k["evals"].sum().item()) for _, k in items)
+    out["optimizer_bb"] = dict(systems_per_s=len(items) / sec, evals_per_s=evals / sec,
+                               evals_per_system=evals / len(items),
+                               mean_top1_score=float(np.mean([float(k["score"][0].item()) for _, k in items])))
+    del items
+    # ---- plain method, one system (2,000 atoms, 54^3 maps, 20 atoms / 4 torsions, 64 x 100)
+    plain = []
+    for b in range(args.batch):
+        seed = 2000 + 1000 * rank + b
+        rec = synth.receptor(2000, seed)
+        plain.append((seed, rec, synth.ligand(20, 4, seed, center=rec.pocket_center)))
+    items = [make_device_job(dsdp, torch, dev, rec, lig, seed, 20.0, SPACING, dsdp.DSDP_MAP_F32, 64, 100, N_ITERS,
+                             TOP_K) for seed, rec, lig in plain]
+    one = _timed_plan(dsdp, torch, items[:1], dsdp.DSDP_MAP_F32, sptr, 3)
+    sec = _timed_plan(dsdp, torch, items, dsdp.DSDP_MAP_F32, sptr, steps)
+    evals = sum(int(k["evals"].sum().item()) for _, k in items)
+    out["plain_2k"] = dict(one_system_ms=1e3 * one, batched_systems_per_s=len(items) / sec,
+                           evals_per_s=evals / sec, systems_per_launch=len(items),
+                           workload="2,000-atom receptor, 20 A box (54^3 x 8 FP32 maps), 20-atom ligand / 4 "
+                                    "torsions, 64 chains x 100 steps, top-9 FP64 rescoring")
+    return out
+
+
 # ---------------------------------------------------------------- copies x steps sweep
 SWEEP = [(128, 20), (384, 40), (512, 40), (512, 200), (1024, 200), (2048, 200)]
 
@@ -750,7 +917,7 @@ def redock_success(dsdp, torch, dev, sptr, chains, steps, n_ligands=18, regions=
 
 
 # ---------------------------------------------------------------- serving (continuous batching)
-def run_serving(args):
+def run_serving(args, n_requests=None, loads=(0.5, 0.8, 0.95)):
     """Poisson arrivals of docking requests over 8 resident receptors (2,000-8,000
     atoms, boxes 20-40 A, BF16 maps), ligands of 10-60 atoms and 0-15 torsions,
     64-384 chains x 40 steps each, admitted by a device-memory budget while other
@@ -769,7 +936,7 @@ def run_serving(args):
     pool = []
     for i in range(64):
         pool.append(synth.ligand(int(rng.integers(10, 61)), int(rng.integers(0, 16)), 500 + i))
-    n_req = args.serve_requests
+    n_req = n_requests or args.serve_requests
     reqs = [(int(rng.integers(0, 8)), int(rng.integers(0, len(pool))), int(rng.integers(64, 385))) for _ in range(n_req)]
     map_bytes = sum(dsdp.dsdp_grid_map_bytes(dsdp.make_box([0, 0, 0], b, SPACING), dsdp.DSDP_MAP_BF16) for _, b in recs)
     # grids (+ receptor copies) plus 48 MB for jobs: admission has to wait for memory as well as for slots
@@ -808,7 +975,7 @@ def run_serving(args):
 
         sat = run(None)
         out["saturated"] = sat
-        for f in (0.5, 0.8, 0.95):
+        for f in loads:
             out[f"load_{f}"] = run(f * sat["systems_per_s"])
         st = dsdp.dsdp_get_stats(ctx)
         out["admission"] = {"budget_bytes": budget, "grid_bytes": map_bytes, "completed": st["completed"],
@@ -976,6 +1143,12 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.gather_bench:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        print(json.dumps(run_gather_bench(args)), flush=True)
+        return
     if args.sweep:
         import __graft_entry__
 
@@ -1020,6 +1193,8 @@ def main():
     single = run_one_job_per_launch(args, rank, local, 2) if args.forms else None
     uneven = run_uneven_graph(args, local) if args.forms and rank == 0 else None
     variants = run_variants(args, rank, local) if args.forms and rank == 0 else None
+    configs = run_configs(args, rank, local) if args.forms and rank == 0 else None
+    serving = run_serving(args, n_requests=400, loads=(0.8,)) if args.forms and rank == 0 else None
     e2e_total = sum_over_ranks(dist, e2e["value"] if e2e else 0.0, local)
     if e2e:
         e2e["value"] = e2e_total
@@ -1052,14 +1227,10 @@ def main():
                    "note": "the same steps on one stream (stage_ms and the rooflines are from this pass)"},
         "evals_per_s": world * r["total_evals"] * args.steps / (r["elapsed_ms"] * 1e-3),
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
-        "roofline": {"kernel": "dock_chains_kernel", "bound": "alu", "achieved": achieved_tflops,
-                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": capture["dram_bytes_per_launch"] if capture else None,
-                     "traffic_unit": "DRAM bytes per launch (ncu)",
-                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
-                                    f"(clock from MEASURED_PEAKS.json, {peaks_src})"},
-        "l2_gather": {"achieved_gbs": r["gather_bytes"] / per_launch_s / 1e9, "microbench_gbs": r["gather_gbs"],
-                      "frac": (r["gather_bytes"] / per_launch_s / 1e9) / r["gather_gbs"]},
+        "roofline": chain_roofline(r["gather_bytes"], r["flops"], r["mufu"], per_launch_s, r["gather_gbs"], peaks,
+                                   peaks_src, sm_mhz, capture),
+        "fp32": {"achieved_tflops": achieved_tflops, "peak_tflops": peak_tflops,
+                 "frac": achieved_tflops / peak_tflops},
         "issue": None if not capture else {
             "warp_instructions_per_eval": capture["warp_instructions_per_eval"],
             "achieved_per_s": capture["warp_instructions_per_eval"] * r["total_evals"] / per_launch_s,
@@ -1084,6 +1255,14 @@ def main():
         line["uneven_5k_batch"] = uneven
     if variants:
         line.update(variants)
+    if configs:
+        line["configs"] = configs
+    if serving:
+        line["serving"] = dict(serving, workload="400 requests over 8 resident receptors (2,000-8,000 atoms, "
+                                                 "20-40 A boxes, BF16 maps), ligands of 10-60 atoms / 0-15 "
+                                                 "torsions, 64-384 chains x 40 steps; all queued at once "
+                                                 "(saturated), then Poisson arrivals at 0.8 of it",
+                               one_job_per_launch=single)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

@@ -393,9 +393,11 @@ dsdp_status dsdp_plan_launch_stage(dsdp_plan* plan, uint32_t stages, void* strea
 int32_t dsdp_plan_kernel_count(const dsdp_plan* plan);
 dsdp_status dsdp_plan_destroy(dsdp_ctx* ctx, dsdp_plan* plan);
 
-/* Gather microbenchmark behind the roofline: n_points random positions in a
- * grid, each reading the 8 cell corners of one map type (same bytes as the
- * score path, no arithmetic beyond the sum that keeps the loads live).
+/* Gather microbenchmark behind the roofline: n_points threads each sample
+ * `repeats` positions in the grid -- the first from d_points / d_types, the
+ * others independent pseudo-random positions and map types -- reading the 8
+ * cell corners of one map at each (the bytes of the score path's inter term,
+ * Eq. 2-4, with no arithmetic beyond the sum that keeps the loads live).
  * Writes one float per point into d_out.  d_points [n_points][3] device. */
 dsdp_status dsdp_gather_bench_device(const dsdp_grid_view* grid, const float* d_points, const uint8_t* d_types,
                                      int32_t n_points, int32_t repeats, float* d_out, void* stream);

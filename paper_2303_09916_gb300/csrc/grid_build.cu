@@ -190,26 +190,41 @@ __global__ void __launch_bounds__(kThreads) grid_build_kernel(int n_rec, const f
   store_node<FMT>(maps, 7 * nxyz + v, Eb.y, Xb.y, Yb.y, Zb.y);                                     // S_P
 }
 
+// 32-bit mixing hash (multiply-xorshift; the finaliser of MurmurHash3) for the
+// microbenchmark's pseudo-random sample points.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return x;
+}
+
+// Each thread samples `repeats` points: the first is its input point, each later
+// one an independent pseudo-random position in the grid (hash of the point
+// index and the repeat) with a pseudo-random map type, so that consecutive
+// samples share no cell and the corner reads are the random 8-corner gathers of
+// the scoring path, with none of its arithmetic.
 template <int FMT>
 __global__ void __launch_bounds__(256) gather_bench_kernel(MapView M, const float* __restrict__ pts,
                                                            const uint8_t* __restrict__ types, int n, int repeats,
                                                            float* __restrict__ out) {
   const int stride = gridDim.x * blockDim.x;
+  const float ex = (M.nx - 1) * M.h, ey = (M.ny - 1) * M.h, ez = (M.nz - 1) * M.h;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     float3 p = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
-    const int t = types[i];
+    int t = types[i];
     float acc = 0.f;
     for (int r = 0; r < repeats; ++r) {
       float3 g;
       const float e = sample_map<FMT>(M, t, p, g);
       acc += e + g.x + g.y + g.z;
-      // next position: a fixed irrational shift keeps the cells changing
-      p.x += 0.618f * M.h;
-      p.y += 0.414f * M.h;
-      p.z += 0.732f * M.h;
-      if (p.x > M.ox + (M.nx - 2) * M.h) p.x -= (M.nx - 2) * M.h;
-      if (p.y > M.oy + (M.ny - 2) * M.h) p.y -= (M.ny - 2) * M.h;
-      if (p.z > M.oz + (M.nz - 2) * M.h) p.z -= (M.nz - 2) * M.h;
+      const uint32_t h0 = mix32((uint32_t)i * 0x9E3779B9u + (uint32_t)r + 1u);
+      const uint32_t h1 = mix32(h0 ^ 0x68E31DA4u), h2 = mix32(h1 ^ 0xB5297A4Du);
+      p = make_float3(M.ox + ex * ((h0 >> 8) * (1.f / 16777216.f)), M.oy + ey * ((h1 >> 8) * (1.f / 16777216.f)),
+                      M.oz + ez * ((h2 >> 8) * (1.f / 16777216.f)));
+      t = (int)(h2 & 7u);
     }
     out[i] = acc;
   }
