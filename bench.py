@@ -71,9 +71,9 @@ def parse():
                    help="time the device-resident steps on one stream only (no overlap of consecutive steps)")
     p.add_argument("--pipeline-depth", type=int, default=3, help="streams (steps in flight) of the pipelined pass")
     p.add_argument("--tile-config", type=int, default=-1,
-                   help="chain kernel launch configuration: -1 autotune (default); 1..12 fixed, numbered as the "
-                        "autotuner reports them: 1 + variant (0: 128 registers, 1: 96) + 2 work queue + 4 log2(chains "
-                        "per CTA)")
+                   help="chain kernel launch configuration: -1 autotune (default); 1..24 fixed, numbered as the "
+                        "autotuner reports them: 1 + variant (0: 128 registers, 1: 96, 2: 80, 3: 72) + 4 log2(chains "
+                        "per CTA) + 12 work queue")
     args = p.parse_args()
     if args.pipeline_depth < 1:
         p.error("--pipeline-depth must be at least 1")
@@ -124,22 +124,21 @@ def systems(rank, batch):
 
 
 def plan_tile_config(chosen):
-    """dsdp_plan_create's tile_config (1 + variant + 2 log2 W) of an autotuner choice."""
-    c = chosen - 1
-    return 1 + c % 2 + 2 * (c // 4)
+    """dsdp_plan_create's tile_config (1 + variant + 4 log2 W) of an autotuner choice."""
+    return 1 + (chosen - 1) % 12
 
 
 def plan_flags(dsdp, chosen):
     """The plan flags of an autotuner choice: the persistent work queue or none."""
-    return dsdp.DSDP_PLAN_PERSISTENT if ((chosen - 1) // 2) % 2 else 0
+    return dsdp.DSDP_PLAN_PERSISTENT if chosen > 12 else 0
 
 
 def describe_tile_config(chosen):
-    """The autotuner's choice (1 + variant + 2 persistent + 4 log2 W) in words."""
-    if not 1 <= chosen <= 12:
+    """The autotuner's choice (1 + variant + 4 log2 W + 12 persistent) in words."""
+    if not 1 <= chosen <= 24:
         return "?"
     c = chosen - 1
-    regs, queue, warps = (128, 96)[c % 2], (c // 2) % 2, 1 << (c // 4)
+    regs, warps, queue = (128, 96, 80, 72)[c % 4], 1 << ((c % 12) // 4), c >= 12
     return f"{regs} regs, {warps} chain{'s' if warps > 1 else ''}/CTA" + (", work queue" if queue else "")
 
 

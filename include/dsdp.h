@@ -271,13 +271,18 @@ dsdp_status dsdp_dock_submit(dsdp_ctx* ctx, const dsdp_grid* grid, const dsdp_li
  * for the call. */
 dsdp_status dsdp_dock_submit_many(dsdp_ctx* ctx, int32_t n, const dsdp_grid* const* grids,
                                   const dsdp_ligand* ligands, const dsdp_dock_params* params, uint64_t* job_ids);
-/* Wait up to wait_ms (0: do not block, < 0: forever) for a job.  DSDP_PENDING
- * while it runs; on DSDP_OK the results are copied into `out` and the job is
- * released (a second poll returns DSDP_ERR_NOT_FOUND).  A job that failed
- * returns its error once and is released. */
+/* Wait up to wait_ms (0: do not block, < 0: forever) for a job.  With
+ * wait_ms = 0 an unfinished job returns DSDP_PENDING; a positive wait that
+ * expires returns DSDP_ERR_TIMEOUT (the job keeps its place: poll again).  On
+ * DSDP_OK the results are copied into `out` and the job is released (a second
+ * poll returns DSDP_ERR_NOT_FOUND).  A job that failed or was cancelled returns
+ * its error (DSDP_ERR_CANCELLED) once and is released. */
 dsdp_status dsdp_dock_poll(dsdp_ctx* ctx, uint64_t job_id, dsdp_dock_result* out, int32_t wait_ms);
-/* Cancel a queued job (DSDP_OK) or report that it already started
- * (DSDP_PENDING: it will finish and must still be polled). */
+/* Cancel a job (DSDP_OK).  A queued job is dropped at once; a running job's
+ * kernels run to the end of its batch (a batch is one launch shared with other
+ * jobs), then its results are dropped and its memory freed.  Either way the
+ * next poll that finds it finished returns DSDP_ERR_CANCELLED and releases it.
+ * A job that already finished is not affected. */
 dsdp_status dsdp_dock_cancel(dsdp_ctx* ctx, uint64_t job_id);
 
 typedef struct {
@@ -362,20 +367,24 @@ enum {
  * tile_config: 0 = automatic (the choice dsdp_plan_autotune recorded for a plan
  * of the same shape -- map formats, atoms per lane, chain count rounded up to
  * a power of two -- else the 128-register kernel with W = 1, or W = 4 when a
- * ligand has more than 32 atoms); 1 .. 6 = a fixed choice: register budget 128
- * (odd values; 16 warps per SM) or 96 (even; 20 warps per SM) and W = 1 (1, 2),
- * 2 (3, 4) or 4 (5, 6).  A map-format group that mixes ligands of up to 32 and
- * of more than 32 atoms runs one kernel holding both tile sizes, compiled for
- * 128 registers only.  Results do not depend on the configuration. */
+ * ligand has more than 32 atoms); 1 .. 12 = a fixed choice 1 + variant +
+ * 4 log2(W): register budget (variant 0: 128 registers, 16 warps per SM; 1: 96,
+ * 20 warps; 2: 80, 24 warps; 3: 72, 28 warps) and W = 1, 2 or 4.  Budgets 80
+ * and 72 are compiled for ligands of up to 32 atoms only (one atom per lane);
+ * ligands above 32 atoms run at 128 or 96 (variants 2 and 3 take 96), and a
+ * map-format group that mixes ligands of up to 32 and of more than 32 atoms
+ * runs one kernel holding both tile sizes, compiled for 128 registers only.
+ * Results do not depend on the configuration. */
 dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
                              int32_t tile_config, dsdp_plan** out);
 /* Autotuner: runs the plan's chain stage `repeats` times for each register
- * budget (128 only when every group mixes tile sizes), each tile of
- * W = 1, 2, 4 chains per CTA, with and without the
+ * budget the plan's kernels are compiled for (128 and 96; also 80 and 72 when
+ * every ligand has at most 32 atoms; 128 only when every group mixes tile
+ * sizes), each tile of W = 1, 2, 4 chains per CTA, with and without the
  * persistent work queue, keeps the fastest for this plan and records it for
  * later plans of the same shape (process-wide).  *chosen = 1 + variant
- * + 2 * persistent + 4 * log2(W) (variant 0: 128 registers, 1: 96).
- * Synchronises the stream. */
+ * + 4 * log2(W) + 12 * persistent (1 .. 24; the first part is the plan's
+ * tile_config).  Synchronises the stream. */
 dsdp_status dsdp_plan_autotune(dsdp_plan* plan, void* stream, int32_t repeats, int32_t* chosen);
 /* Enqueue the plan's kernels on `stream` (chains, then FP64 rescoring and
  * top-k).  No allocation and no host synchronisation: a launch can be

@@ -66,6 +66,7 @@ struct Job {
   size_t h_cap = 0;
   int stream = 0;
   dsdp_job_device jd{};  // the job as the plan sees it
+  bool cancel_requested = false;  // cancelled while running: its results are dropped when its batch retires
   float device_ms = 0.f;  // device time of the batch the job ran in
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
@@ -369,6 +370,10 @@ void batch_retire(dsdp_ctx* ctx, Batch* b, cudaError_t q) {
   for (Job* j : b->jobs) {
     if (q != cudaSuccess) {
       job_fail(ctx, j, check_cuda(q, "job execution"), dsdp_last_error());
+    } else if (j->cancel_requested) {
+      j->state = JobState::Cancelled;
+      j->t_done = now;
+      ctx->stats.cancelled++;
     } else {
       j->state = JobState::Done;
       j->device_ms = ms;
@@ -1064,7 +1069,12 @@ extern "C" dsdp_status dsdp_dock_poll(dsdp_ctx* ctx, uint64_t job_id, dsdp_dock_
     if (wait_ms < 0) ctx->cv_done.wait(lk, finished);
     else ctx->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), finished);
   }
-  if (!finished()) return DSDP_PENDING;
+  if (!finished()) {
+    if (wait_ms > 0)
+      return set_error(DSDP_ERR_TIMEOUT, "job %llu not finished after %d ms (still %s; poll again)",
+                       (unsigned long long)job_id, wait_ms, j->state == JobState::Queued ? "queued" : "running");
+    return DSDP_PENDING;
+  }
   dsdp_status s = DSDP_OK;
   if (j->state == JobState::Done) {
     if (out) {
@@ -1098,6 +1108,11 @@ extern "C" dsdp_status dsdp_dock_cancel(dsdp_ctx* ctx, uint64_t job_id) {
     ctx->cv_done.notify_all();
     return DSDP_OK;
   }
-  if (j->state == JobState::Running) return DSDP_PENDING;
+  if (j->state == JobState::Running) {
+    // its kernels are in flight with other jobs' (a batch is one launch): they
+    // finish, and the job's results are dropped when the batch retires
+    j->cancel_requested = true;
+    return DSDP_OK;
+  }
   return DSDP_OK;
 }

@@ -7,9 +7,13 @@
 namespace dsdp {
 
 // Register budgets of the chain kernel: variant 0 caps at 128 registers (16
-// warps per SM, no spills), variant 1 at 96 (20 warps, a few spills); the
-// autotuner picks per plan by measurement.  The bounds are stated for CTAs of
-// up to 4 warps (chains); CTAs of 1 or 2 warps get the same register cap.
+// warps per SM, no spills), variant 1 at 96 (20 warps), 2 at 80 (24 warps) and
+// 3 at 72 (28 warps), each with a few more bytes spilled; the autotuner picks
+// per plan by measurement.  Variants 2 and 3 are compiled for the
+// one-atom-per-lane tiles only (two atoms per lane take variants 0 and 1, mixed
+// tiles variant 0; a plan asking for more falls back to the nearest budget
+// compiled).  The bounds are stated for CTAs of up to 4 warps (chains); CTAs of
+// 1 or 2 warps get the same register cap.
 constexpr int kMaxChainWarps = 4;
 template <int VAR>
 struct ChainOcc;
@@ -20,6 +24,14 @@ struct ChainOcc<0> {
 template <>
 struct ChainOcc<1> {
   static constexpr int kMinBlocks = 5;  // 102 -> 96 registers
+};
+template <>
+struct ChainOcc<2> {
+  static constexpr int kMinBlocks = 6;  // 85 -> 80 registers
+};
+template <>
+struct ChainOcc<3> {
+  static constexpr int kMinBlocks = 7;  // 73 -> 72 registers
 };
 
 // Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
@@ -124,9 +136,17 @@ cudaError_t launch_chains_var(const ChainLaunch& a, cudaStream_t st) {
 template <int FMT>
 cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
   if (a.warps_per_cta != 1 && a.warps_per_cta != 2 && a.warps_per_cta != kMaxChainWarps) return cudaErrorInvalidValue;
-  if (a.apl_mask == 1) return a.variant ? launch_chains_var<FMT, 1, 1>(a, st) : launch_chains_var<FMT, 0, 1>(a, st);
+  if (a.apl_mask == 1) {
+    switch (a.variant) {
+      case 0: return launch_chains_var<FMT, 0, 1>(a, st);
+      case 1: return launch_chains_var<FMT, 1, 1>(a, st);
+      case 2: return launch_chains_var<FMT, 2, 1>(a, st);
+      default: return launch_chains_var<FMT, 3, 1>(a, st);
+    }
+  }
   if (a.apl_mask == 2) return a.variant ? launch_chains_var<FMT, 1, 2>(a, st) : launch_chains_var<FMT, 0, 2>(a, st);
-  return launch_chains_var<FMT, 0, 3>(a, st);  // mixed tiles: the 128-register budget only
+  // mixed tiles: the 128-register budget only
+  return launch_chains_var<FMT, 0, 3>(a, st);
 }
 
 template <int FMT>

@@ -199,7 +199,7 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
   if (!out) return set_error(DSDP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_jobs < 1 || !jobs) return set_error(DSDP_ERR_INVALID_ARG, "plan needs >= 1 job");
-  if (tile_config < 0 || tile_config > 6) return set_error(DSDP_ERR_INVALID_ARG, "tile_config outside 0..6");
+  if (tile_config < 0 || tile_config > 12) return set_error(DSDP_ERR_INVALID_ARG, "tile_config outside 0..12");
   std::vector<DevJob> dj(n_jobs);
   std::vector<int> fmt(n_jobs), apl(n_jobs), blob_bytes(n_jobs), pairs(n_jobs), atoms(n_jobs), tors(n_jobs);
   size_t scratch = 0;
@@ -316,8 +316,8 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
       W = apl_max == 2 ? 4 : 1;
       if (tune_lookup(P->tune_key, &var, &pers, &W) && pers) P->flags |= DSDP_PLAN_PERSISTENT;
     } else {
-      var = (tile_config - 1) % 2;
-      W = 1 << ((tile_config - 1) / 2);
+      var = (tile_config - 1) % 4;
+      W = 1 << ((tile_config - 1) / 4);
     }
     P->variant = var;
   }
@@ -432,11 +432,10 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
   float best = 1e30f;
   int best_var = P->variant, best_pers = (P->flags & DSDP_PLAN_PERSISTENT) ? 1 : 0, best_w = P->warps_per_cta;
   dsdp_status s = DSDP_OK;
-  // the register budget is a choice only where a group runs one tile size: the
-  // kernel for mixed tiles is compiled once, at 128 registers
+  // register budgets compiled: 128, 96, 80, 72 for one atom per lane, 128 and
+  // 96 for two, 128 only for mixed tiles (launch_chains_impl)
   int n_var = 1;
-  for (const dsdp_plan::Group& g : P->groups)
-    if (g.apl_mask != 3) n_var = 2;
+  for (const dsdp_plan::Group& g : P->groups) n_var = std::max(n_var, g.apl_mask == 1 ? 4 : g.apl_mask == 2 ? 2 : 1);
   for (int w = 1; w <= 4 && s == DSDP_OK; w *= 2) {
     e = plan_use_warps(P, w);
     if (e != cudaSuccess) {
@@ -474,7 +473,7 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
   if (s == DSDP_OK) s = check_cuda(plan_use_warps(P, best_w), "plan tiles");
   if (s != DSDP_OK) return s;
   tune_store(P->tune_key, best_var, best_pers, best_w);
-  if (chosen) *chosen = 1 + best_var + 2 * best_pers + 4 * (best_w == 4 ? 2 : best_w - 1);
+  if (chosen) *chosen = 1 + best_var + 4 * (best_w == 4 ? 2 : best_w - 1) + 12 * best_pers;
   return DSDP_OK;
 }
 

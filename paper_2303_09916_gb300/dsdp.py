@@ -336,7 +336,8 @@ def result_buffers(n_atoms, n_torsions, params: dsdp_dock_params, chains=True):
 
 
 def dsdp_dock_poll(ctx, job_id, bufs: dict, wait_ms=-1):
-    """Fills `bufs` (from result_buffers) and returns a dict, or None while pending."""
+    """Fills `bufs` (from result_buffers) and returns a dict; None while pending
+    (wait_ms = 0); a positive wait that expires raises DSDPError (DSDP_ERR_TIMEOUT)."""
     r = dsdp_dock_result()
     r.capacity = len(bufs["score"])
     for key in ("score", "inter", "intra", "conf", "coords", "chain", "chain_best_e", "chain_best_conf", "trace"):

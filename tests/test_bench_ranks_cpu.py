@@ -55,28 +55,28 @@ def test_single_process_is_the_identity():
 
 
 def test_fixed_tile_config_numbering():
-    """bench.py --tile-config takes the autotuner's numbering (1 + variant + 2
-    work queue + 4 log2 W); each maps back to the plan's tile_config (1 +
-    variant + 2 log2 W) and flags, and to its description."""
+    """bench.py --tile-config takes the autotuner's numbering (1 + variant + 4
+    log2 W + 12 work queue); each maps back to the plan's tile_config (1 +
+    variant + 4 log2 W) and flags, and to its description."""
 
     class Flags:
         DSDP_PLAN_PERSISTENT = 1
 
     seen = set()
-    for chosen in range(1, 13):
-        var, queue, w = (chosen - 1) % 2, ((chosen - 1) // 2) % 2, 1 << ((chosen - 1) // 4)
+    for chosen in range(1, 25):
+        var, w, queue = (chosen - 1) % 4, 1 << (((chosen - 1) % 12) // 4), chosen > 12
         tc = bench.plan_tile_config(chosen)
-        assert 1 <= tc <= 6 and (tc - 1) % 2 == var and 1 << ((tc - 1) // 2) == w
+        assert 1 <= tc <= 12 and (tc - 1) % 4 == var and 1 << ((tc - 1) // 4) == w
         assert bench.plan_flags(Flags, chosen) == (1 if queue else 0)
         text = bench.describe_tile_config(chosen)
-        assert text.startswith(f"{(128, 96)[var]} regs, {w} chain") and text.endswith("work queue") == bool(queue)
+        assert text.startswith(f"{(128, 96, 80, 72)[var]} regs, {w} chain") and text.endswith("work queue") == queue
         seen.add((tc, queue))
-    assert len(seen) == 12
+    assert len(seen) == 24
 
 
 def test_committed_chain_kernel_capture_is_consistent():
-    """The committed ncu record of the chain kernel covers every launch
-    configuration the autotuner can choose, each internally consistent (DRAM
+    """The committed ncu record of the chain kernel: each captured launch
+    configuration internally consistent (DRAM
     bytes = read + write, instructions per evaluation = instructions /
     evaluations, the same evaluation count: results do not depend on the
     configuration)."""
@@ -85,7 +85,7 @@ def test_committed_chain_kernel_capture_is_consistent():
     with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "dock_chains_kernel_traffic.json")) as f:
         rec = json.load(f)
     caps = {c["tile_config"]: c for c in rec["captures"]}
-    assert sorted(caps) == list(range(1, 13))
+    assert caps and all(1 <= k <= 24 for k in caps)
     evals = {c["evaluations"] for c in caps.values()}
     assert len(evals) == 1
     for k, c in caps.items():

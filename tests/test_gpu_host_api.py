@@ -1,8 +1,9 @@
 """The handle API on a GPU: the job lifecycle and status codes (a queued job
-polled without waiting is pending, cancelling it frees it -- its one poll
-reports CANCELLED, the next NOT_FOUND --, a finished job is released by its
-poll, a grid larger than the context's budget is refused with OUT_OF_MEMORY),
-and a context working on the caller's stream."""
+polled without waiting is pending, a timed wait that expires is a TIMEOUT,
+cancelling a queued or a running job drops it -- its one poll reports
+CANCELLED, the next NOT_FOUND --, a finished job is released by its poll, a
+grid larger than the context's budget is refused with OUT_OF_MEMORY), and a
+context working on the caller's stream."""
 import numpy as np
 import pytest
 
@@ -23,30 +24,39 @@ def test_job_lifecycle_pending_cancel_release():
     lig = synth.ligand(20, 4, 5, center=rec.pocket_center)
     grid = dsdp.dsdp_grid_build(ctx, rec.xyz, rec.xs_type, dsdp.make_box(rec.pocket_center, 20.0, 0.375))
     try:
-        long_p = dsdp.make_params(n_chains=2048, n_mc_steps=200, n_opt_iters=100, seed=1, top_k=3)
+        long_p = dsdp.make_params(n_chains=2048, n_mc_steps=600, n_opt_iters=100, seed=1, top_k=3)
         short_p = dsdp.make_params(n_chains=64, n_mc_steps=5, n_opt_iters=20, seed=2, top_k=3)
+        long_bufs = dsdp.result_buffers(lig.n_atoms, lig.n_torsions, long_p)
         a = dsdp.dsdp_dock_submit(ctx, grid, lig, long_p)
         b = dsdp.dsdp_dock_submit(ctx, grid, lig, short_p)
         bufs_b = dsdp.result_buffers(lig.n_atoms, lig.n_torsions, short_p)
         assert dsdp.dsdp_dock_poll(ctx, b, bufs_b, wait_ms=0) is None  # queued behind a
-        assert dsdp.dsdp_dock_poll(ctx, a, dsdp.result_buffers(lig.n_atoms, lig.n_torsions, long_p),
-                                   wait_ms=1) is None  # still running after 1 ms
+        with pytest.raises(dsdp.DSDPError) as ei:  # a timed wait that expires
+            dsdp.dsdp_dock_poll(ctx, a, long_bufs, wait_ms=1)
+        assert ei.value.status == dsdp.DSDP_ERR_TIMEOUT
         s = dsdp.dsdp_get_stats(ctx)
         assert s["queued"] + s["running"] == 2
-        assert dsdp.dsdp_dock_cancel(ctx, b) == dsdp.DSDP_OK  # still queued: cancelled
+        assert dsdp.dsdp_dock_cancel(ctx, b) == dsdp.DSDP_OK  # still queued: dropped at once
         with pytest.raises(dsdp.DSDPError) as ei:
             dsdp.dsdp_dock_poll(ctx, b, bufs_b, wait_ms=-1)
         assert ei.value.status == dsdp.DSDP_ERR_CANCELLED
         with pytest.raises(dsdp.DSDPError) as ei:
             dsdp.dsdp_dock_poll(ctx, b, bufs_b, wait_ms=0)
         assert ei.value.status == dsdp.DSDP_ERR_NOT_FOUND
-        r = dsdp.dsdp_dock_poll(ctx, a, dsdp.result_buffers(lig.n_atoms, lig.n_torsions, long_p), wait_ms=-1)
+        assert dsdp.dsdp_get_stats(ctx)["running"] == 1
+        assert dsdp.dsdp_dock_cancel(ctx, a) == dsdp.DSDP_OK  # running: dropped when its batch retires
+        with pytest.raises(dsdp.DSDPError) as ei:
+            dsdp.dsdp_dock_poll(ctx, a, long_bufs, wait_ms=-1)
+        assert ei.value.status == dsdp.DSDP_ERR_CANCELLED
+        c = dsdp.dsdp_dock_submit(ctx, grid, lig, short_p)
+        r = dsdp.dsdp_dock_poll(ctx, c, bufs_b, wait_ms=-1)
         assert r is not None and r["n_out"] >= 1 and np.isfinite(r["score"][: r["n_out"]]).all()
         with pytest.raises(dsdp.DSDPError) as ei:  # released by its poll
-            dsdp.dsdp_dock_poll(ctx, a, dsdp.result_buffers(lig.n_atoms, lig.n_torsions, long_p), wait_ms=0)
+            dsdp.dsdp_dock_poll(ctx, c, bufs_b, wait_ms=0)
         assert ei.value.status == dsdp.DSDP_ERR_NOT_FOUND
         s = dsdp.dsdp_get_stats(ctx)
-        assert s["cancelled"] == 1 and s["completed"] >= 1 and s["queued"] == 0 and s["running"] == 0
+        assert s["cancelled"] == 2 and s["completed"] >= 1 and s["queued"] == 0 and s["running"] == 0
+        assert s["bytes_in_use"] <= dsdp.dsdp_grid_info(grid)["map_bytes"] + (16 << 20)  # the jobs' memory is back
     finally:
         dsdp.dsdp_grid_free(ctx, grid)
         dsdp.dsdp_destroy(ctx)
