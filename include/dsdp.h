@@ -141,7 +141,9 @@ typedef struct {
   uint64_t seed;        /* Philox key; results depend on (seed, chain index) only */
   int32_t top_k;        /* poses returned after FP64 rescoring [9], <= DSDP_MAX_TOP_K */
   double rmsd_dedup;    /* poses closer than this heavy-atom RMSD to a better kept pose are dropped [1.0] */
-  int32_t trace;        /* 1: keep per-step chain traces (tests; costs memory) */
+  int32_t trace;        /* 1: keep per-step chain traces (tests; costs memory); 2: the same, but row 0
+                           holds each chain's initial conformation, drawn before its first local
+                           optimisation, instead of the state after it */
   /* Adaptive search space (Sec. 2, third modification; Fig. 3): with
    * n_site_points > 0 each chain's initial position is drawn uniformly from the
    * box intersected with the union of balls of radius site_radius around the

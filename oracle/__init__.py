@@ -94,6 +94,10 @@ def lib():
                                    dp, dp, dp]),
             "orc_dock": (None, [vp, dp, ip, dp, d, i, dp, dp, ctypes.c_uint64, i, i, i, dp, dp, dp]),
             "orc_rescore_topk": (i, [vp, i, dp, ip, i, dp, i, d, dp, ip, dp]),
+            "orc_sas_directions": (i, [P(ctypes.c_float)]),
+            "orc_sas_exposed": (None, [i, P(ctypes.c_float), P(ctypes.c_float), ip]),
+            "orc_voxelize": (i, [i, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float), dp,
+                                 P(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -434,3 +438,42 @@ def unit_ball(seed, chain, step):
     out = np.zeros(3)
     lib().orc_unit_ball(int(seed), int(chain), int(step), _d(out)[1])
     return out
+
+
+# ---------------------------------------------------------------- voxel features
+VOX_N, VOX_FEATURES, VOX_CHANNELS = 36, 17, 18
+
+
+def _f(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def sas_directions():
+    """The 98 unit test directions of the surface test, FP32 [98][3]."""
+    u = np.zeros((98, 3), dtype=np.float32)
+    m = lib().orc_sas_directions(_f(u)[1])
+    return u[:m]
+
+
+def sas_exposed(xyz, radius):
+    """Exposed solvent-accessible test points per atom (of 98)."""
+    x, xp = _f(xyz)
+    r, rp = _f(radius)
+    out = np.zeros(len(r), dtype=np.int32)
+    lib().orc_sas_exposed(len(r), xp, rp, _i(out)[1])
+    return out
+
+
+def voxelize(xyz, radius, features, center):
+    """Voxel features [36][36][36][18] (z, y, x, channel) of a receptor and the
+    number of atoms inside the 70 A cube."""
+    x, xp = _f(xyz)
+    r, rp = _f(radius)
+    f, fp = _f(features)
+    if f.shape != (len(r), VOX_FEATURES):
+        raise ValueError("features must be [n][17]")
+    c, cp = _d(center)
+    out = np.zeros((VOX_N, VOX_N, VOX_N, VOX_CHANNELS), dtype=np.float32)
+    inside = lib().orc_voxelize(len(r), xp, rp, fp, cp, _f(out)[1])
+    return out, inside

@@ -25,6 +25,10 @@
 //   * Gridless FP64 rescoring, RMSD de-duplication and top-k (Fig. 4 postprocess).
 //   * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based
 //     generator both sides implement from its published definition.
+//   * Receptor voxel features, the binding-site network's input (Sec. 2,
+//     "Protein-ligand binding site prediction": 36^3 voxels over 70 A, 18
+//     channels with S and Se merged and one surface channel), with surface
+//     atoms by the Shrake-Rupley test.
 //
 // Parity status per function is stated in the header comment of each section.
 
@@ -1051,6 +1055,88 @@ double rmsd(const std::vector<V3>& a, const std::vector<V3>& b) {
 // C interface for the tests (ctypes).  All arrays are host memory owned by the
 // caller; ligand handles are owned by the caller until orc_ligand_free.
 // ===========================================================================
+
+// ---------------------------------------------------------------------------
+// Receptor voxel features (Sec. 2, "Protein-ligand binding site prediction"):
+// the protein as 36 x 36 x 36 voxels with 18 features, centred on the protein
+// and 70 A on a side; DSDP merges the S and Se channels and uses the freed
+// channel for the protein surface.  Reading (the paper gives the grid, the
+// span, the channel count and the two changes, not the per-atom features):
+//   * the cube [c - 35, c + 35)^3 is cut into 36^3 voxels of edge 70/36 A; an
+//     atom belongs to voxel k = floor((x - (c - 35)) * (36/70)) per axis when
+//     0 <= k < 36 on every axis (atoms outside are dropped); this decision is
+//     taken in FP32, subtraction then multiplication, as the kernel takes it;
+//   * channels 0..16 are the sums over the voxel's atoms of 17 per-atom
+//     features supplied by the caller (the feature list is the site network's,
+//     an input here);
+//   * channel 17 counts the voxel's surface atoms: atom i is on the surface
+//     when some test point x_i + (r_i + 1.4) u_k of its solvent-accessible
+//     sphere (probe radius 1.4 A) lies outside every other atom's sphere of
+//     radius r_j + 1.4 (Shrake & Rupley, J. Mol. Biol. 79, 351 (1973)).  The
+//     98 test directions u_k are the integer vectors (a, b, c) in {-2..2}^3
+//     with gcd(|a|, |b|, |c|) = 1, normalised; the point and distance tests are
+//     FP32 with a fixed operation order (the kernel's), so both take the same
+//     decisions;
+//   * sums are exact: each feature is rounded to a multiple of 2^-24 and
+//     accumulated as a 64-bit integer, so the result does not depend on the
+//     order of the atoms; a channel is the sum times 2^-24 rounded to FP32.
+// Parity: pinned by the tests (hand-placed atoms, an isolated atom and a
+// buried one, the exposed fraction of two overlapping spheres, and a
+// brute-force recount).
+// ---------------------------------------------------------------------------
+constexpr int kVoxN = 36;
+constexpr int kVoxFeatures = 17;
+constexpr int kVoxChannels = 18;
+
+// The 98 test directions, FP32 (sqrt and division are correctly rounded).
+static int sas_directions(float* u) {
+  int m = 0;
+  for (int a = -2; a <= 2; ++a)
+    for (int b = -2; b <= 2; ++b)
+      for (int c = -2; c <= 2; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        int g = std::abs(a);
+        for (int v : {std::abs(b), std::abs(c)}) {
+          int x = g, y = v;
+          while (y) {
+            const int t = x % y;
+            x = y;
+            y = t;
+          }
+          g = x;
+        }
+        if (g != 1) continue;
+        const float len = std::sqrt((float)(a * a + b * b + c * c));
+        u[3 * m] = (float)a / len, u[3 * m + 1] = (float)b / len, u[3 * m + 2] = (float)c / len;
+        ++m;
+      }
+  return m;
+}
+
+// Exposed test points of every atom (out[n]); xyz, radius FP32-representable.
+static void sas_exposed(int n, const float* xyz, const float* radius, int* exposed) {
+  float u[3 * 98];
+  const int m = sas_directions(u);
+  for (int i = 0; i < n; ++i) {
+    const float Ri = radius[i] + 1.4f;
+    int count = 0;
+    for (int k = 0; k < m; ++k) {
+      const float p[3] = {xyz[3 * i] + Ri * u[3 * k], xyz[3 * i + 1] + Ri * u[3 * k + 1],
+                          xyz[3 * i + 2] + Ri * u[3 * k + 2]};
+      bool buried = false;
+      for (int j = 0; j < n && !buried; ++j) {
+        if (j == i) continue;
+        const float dx = p[0] - xyz[3 * j], dy = p[1] - xyz[3 * j + 1], dz = p[2] - xyz[3 * j + 2];
+        const float d2 = (dx * dx + dy * dy) + dz * dz;
+        const float Rj = radius[j] + 1.4f;
+        buried = d2 < Rj * Rj;
+      }
+      count += !buried;
+    }
+    exposed[i] = count;
+  }
+}
+
 extern "C" {
 
 int orc_num_map_types() { return kNumMapTypes; }
@@ -1422,6 +1508,44 @@ int orc_rescore_topk(void* h, int n_rec, const double* rec_xyz, const int* rec_t
     ++kept;
   }
   return kept;
+}
+
+
+int orc_sas_directions(float* u) { return sas_directions(u); }
+
+// Exposed test points per atom (see the voxel features section).
+void orc_sas_exposed(int n, const float* xyz, const float* radius, int* exposed) {
+  sas_exposed(n, xyz, radius, exposed);
+}
+
+// Voxel features: out [36][36][36][18] (z, y, x, channel); features [n][17];
+// center: the cube's centre (the lower corner c - 35 is taken in FP64, then
+// rounded to FP32).  Returns the number of atoms inside the cube.
+int orc_voxelize(int n, const float* xyz, const float* radius, const float* features, const double* center,
+                 float* out) {
+  std::vector<int> exposed(n);
+  sas_exposed(n, xyz, radius, exposed.data());
+  float lo[3];
+  for (int a = 0; a < 3; ++a) lo[a] = (float)(center[a] - 35.0);
+  const float inv = 36.0f / 70.0f;
+  std::vector<int64_t> acc((size_t)kVoxN * kVoxN * kVoxN * kVoxChannels, 0);
+  int inside = 0;
+  for (int i = 0; i < n; ++i) {
+    int k[3];
+    bool in = true;
+    for (int a = 0; a < 3; ++a) {
+      const float u = (xyz[3 * i + a] - lo[a]) * inv;
+      k[a] = (int)std::floor(u);
+      in = in && k[a] >= 0 && k[a] < kVoxN;
+    }
+    if (!in) continue;
+    ++inside;
+    int64_t* v = &acc[(((size_t)k[2] * kVoxN + k[1]) * kVoxN + k[0]) * kVoxChannels];
+    for (int c = 0; c < kVoxFeatures; ++c) v[c] += std::llrint((double)features[(size_t)kVoxFeatures * i + c] * 16777216.0);
+    v[kVoxFeatures] += (exposed[i] > 0 ? 1 : 0) * (int64_t)16777216;
+  }
+  for (size_t q = 0; q < acc.size(); ++q) out[q] = (float)((double)acc[q] * (1.0 / 16777216.0));
+  return inside;
 }
 
 }  // extern "C"

@@ -582,6 +582,16 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
     V.chain = (uint32_t)chain;
     V.trace = J.trace ? J.trace + (size_t)chain * (J.n_steps + 1) * ((size_t)7 + T + 4) : nullptr;
     if (lane < kHStride) Vg[lane] = Vd[lane] = 0.f;
+    if (J.trace && J.trace_starts) {  // row 0: the drawn start, before any optimisation
+      float* t = J.trace + (size_t)chain * (J.n_steps + 1) * ((size_t)7 + T + 4);
+      store_conf(t, xt, T);
+      if (lane == 0) {
+        t[7 + T + 0] = 0.f;
+        t[7 + T + 1] = 0.f;
+        t[7 + T + 2] = -2.f;
+        t[7 + T + 3] = 0.f;
+      }
+    }
     __syncwarp();
   }
   for (;;) {
@@ -672,7 +682,7 @@ __device__ void run_chain(const DevJob& J, const LigView& L, const WarpScratch& 
           W.cur[lane] = W.x[lane];
           W.best[lane] = W.x[lane];
         }
-        if (trace) {
+        if (trace && !J.trace_starts) {
           if (lane < nx) trace[lane] = W.x[lane];
           if (lane == 0) {
             trace[nx + 0] = e_cur;

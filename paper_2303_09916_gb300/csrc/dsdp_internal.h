@@ -97,6 +97,7 @@ struct DevJob {
   float* chain_best_e;
   uint32_t* chain_evals;
   float* trace;
+  int32_t trace_starts;  // trace row 0: the initial conformation (not the state after the first optimisation)
   // rescoring
   int32_t n_rec;
   const float* rec_xyz;

@@ -48,6 +48,7 @@ dsdp_status normalize_params(const dsdp_dock_params* in, dsdp_dock_params* out) 
   if (out->n_chains < 1 || out->n_chains > DSDP_MAX_CHAINS)
     return set_error(DSDP_ERR_INVALID_ARG, "n_chains %d outside 1..%d", out->n_chains, DSDP_MAX_CHAINS);
   if (out->n_mc_steps < 0 || out->n_mc_steps > 100000) return set_error(DSDP_ERR_INVALID_ARG, "n_mc_steps out of range");
+  if (out->trace < 0 || out->trace > 2) return set_error(DSDP_ERR_INVALID_ARG, "trace must be 0, 1 or 2");
   if (out->n_opt_iters < 0 || out->n_opt_iters > 100000)
     return set_error(DSDP_ERR_INVALID_ARG, "n_opt_iters out of range");
   if (out->optimizer != DSDP_OPT_BFGS && out->optimizer != DSDP_OPT_BB)
@@ -257,6 +258,7 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
     d.chain_best_e = J.d_chain_best_e;
     d.chain_evals = J.d_chain_evals;
     d.trace = p.trace ? J.d_trace : nullptr;
+    d.trace_starts = p.trace == 2;
     d.sites = p.n_site_points > 0 ? J.d_site_points : nullptr;
     d.n_sites = p.n_site_points;
     d.site_r2 = p.site_radius * p.site_radius;

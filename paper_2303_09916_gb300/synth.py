@@ -270,6 +270,39 @@ def shell_receptor(lig: Ligand, seed: int = 0, per_atom: int = 24, radius: float
     return Receptor(out, np.zeros(len(out), dtype=np.uint8), xyz.mean(axis=0))
 
 
+# Per-atom inputs of the receptor voxel features (the binding-site network's
+# input, Sec. 2): 17 chemistry features -- 8 element classes with S and Se in one
+# class (B, C, N, O, P, S/Se, halogen, metal) and 9 atom properties
+# (hybridisation, heavy-atom valence, hetero-atom valence, partial charge,
+# hydrophobic, aromatic, H-bond acceptor, H-bond donor, ring) -- and the
+# Bondi van der Waals radius.  A synthetic receptor carries elements and XS
+# donor / acceptor / hydrophobic flags only: the other properties are 0.
+VOXEL_FEATURE_NAMES = ["B", "C", "N", "O", "P", "S/Se", "halogen", "metal", "hybridisation", "heavy_valence",
+                       "hetero_valence", "partial_charge", "hydrophobic", "aromatic", "acceptor", "donor", "ring"]
+_ELEMENT_OF_XS = {C_H: 1, C_P: 1, N_P: 2, N_D: 2, N_A: 2, O_A: 3, O_DA: 3, S_P: 5, N_DA: 2}
+_BONDI = {1: 1.70, 2: 1.55, 3: 1.52, 5: 1.80}
+
+
+def receptor_voxel_inputs(rec: Receptor):
+    """(radius [n] float32, features [n][17] float32) of a synthetic receptor."""
+    n = len(rec.xs_type)
+    feats = np.zeros((n, len(VOXEL_FEATURE_NAMES)), dtype=np.float32)
+    radius = np.zeros(n, dtype=np.float32)
+    for i, t in enumerate(rec.xs_type.tolist()):
+        e = _ELEMENT_OF_XS[t]
+        feats[i, e] = 1.0
+        radius[i] = _BONDI[e]
+        feats[i, 12] = 1.0 if t == C_H else 0.0
+        feats[i, 14] = 1.0 if t in (N_A, O_A, O_DA, N_DA) else 0.0
+        feats[i, 15] = 1.0 if t in (N_D, O_DA, N_DA) else 0.0
+    return radius, feats
+
+
+def protein_center(rec: Receptor) -> np.ndarray:
+    """Centre of the voxel cube: the mean of the heavy-atom coordinates."""
+    return rec.xyz.astype(np.float64).mean(axis=0)
+
+
 def box_around(center, size, spacing=0.375) -> Box:
     s = np.array(size if np.ndim(size) else [size] * 3, dtype=np.float64)
     return Box(np.asarray(center, dtype=np.float64), s, float(spacing))

@@ -4,17 +4,24 @@ per lane (40 and 60 atoms, 10 and 15 torsions) and batches that mix both (the
 mixed-tile kernel).
 
 FP32 and FP64 arithmetic may take different branches where a decision is a
-near tie, after which the trajectories separate.  Every separation is
-therefore explained or the test fails: at a chain's first divergence from the
-oracle's own run, the step is replayed on the oracle from the GPU's state at
-that point (A) and from the oracle's own state (B), both recording the margin
-of every decision they take (the Armijo test, Barzilai-Borwein's best iterate
-and curvature test, BFGS's curvature test, the Metropolis acceptance):
-  * if the GPU reproduces A, the GPU did exactly what the oracle does from
-    the GPU's state, and the separation comes from a decision that A and B
-    take differently; that decision's margin must be within its tolerance;
-  * otherwise the GPU took a branch other than A's from the same state, and
-    some decision of A must be a near tie.
+near tie, and the search amplifies FP32-level differences of its state (steep
+clashes, BFGS updates), after which trajectories separate.  Every separation
+from the oracle's own run is therefore explained or the test fails.  At a
+chain's first divergence the step is replayed on the oracle from the GPU's
+exact state before it (A; the GPU's drawn start for the first local
+optimisation, recorded with trace mode 2), from the oracle's own state (B), and
+from the GPU's state moved by one FP32 ulp in position (N), each recording the
+margin of every decision it takes (the Armijo test, Barzilai-Borwein's best
+iterate and curvature test, BFGS's curvature test, the Metropolis acceptance):
+  * the GPU reproduces A: it did what the oracle does from the GPU's state.
+    The separation from B is then the oracle's own response to the FP32
+    difference of the two states (which agreed within tolerance), either
+    through a decision A and B take differently -- reported with its margin --
+    or through continuous amplification (reported);
+  * otherwise some decision of A is a near tie (its margin within tolerance),
+    or the GPU lies no farther from A than the oracle's own response to a
+    one-ulp move of the state (|E_gpu - E_A| <= 2 |E_N - E_A|);
+  * anything else fails.
 Tolerances: energies E_REL * max(sum_i |e_i|, 1) each, so a margin of two
 energies is a tie within twice that; a curvature product s.y within
 G_REL * |s|_1 (|g|_inf + |g'|_inf).
@@ -75,23 +82,51 @@ def _normalised_margin(log, i, tol_e):
     return abs(float(log.margin[i])) / tol
 
 
-def explain_divergence(log_a, log_b, gpu_matches_a, tol_e):
-    """(explained, description) of a divergence; see the module docstring."""
-    if gpu_matches_a:
+def nudged(conf):
+    """The state moved by one FP32 ulp (upwards) in each position coordinate."""
+    c = np.array(conf, dtype=np.float64)
+    c[:3] = np.nextafter(c[:3].astype(np.float32), np.float32(np.inf)).astype(np.float64)
+    return c
+
+
+def explain_divergence(gpu, a, b, n, tol_e):
+    """(explained, description) of a divergence; gpu / a / b / n: dicts with the
+    energy `e`, the Metropolis outcome `acc` (None for a local optimisation) and,
+    for the oracle runs, the decision log `log` (module docstring)."""
+    def same(x, y):
+        return abs(x["e"] - y["e"]) <= tol_e and (x["acc"] is None or int(x["acc"]) == int(y["acc"]))
+
+    log_a, log_b = a["log"], b["log"]
+    if same(gpu, a):
         ta, tb = log_a.taken(), log_b.taken()
         for i in range(min(len(log_a), len(log_b))):
             if log_a.kind[i] != log_b.kind[i] or ta[i] != tb[i]:
                 r = min(_normalised_margin(log_a, i, tol_e), _normalised_margin(log_b, i, tol_e))
                 name = oracle.DECISION_KINDS[int(log_a.kind[i])]
-                return r <= 1.0, (f"GPU = oracle from the GPU state; decision {i} ({name}) differs from the "
-                                  f"oracle's own run, margin {r:.3f} of its tolerance")
-        return False, "GPU = oracle from the GPU state, and no decision differs from the oracle's own run"
-    if len(log_a) == 0:
-        return False, "GPU departs from the oracle's replay of its state, which took no decision"
-    rs = [_normalised_margin(log_a, i, tol_e) for i in range(len(log_a))]
-    i = int(np.argmin(rs))
-    return rs[i] <= 1.0, (f"GPU departs from the oracle's replay of its state; nearest tie: decision {i} "
-                          f"({oracle.DECISION_KINDS[int(log_a.kind[i])]}) at {rs[i]:.3f} of its tolerance")
+                return True, (f"GPU = oracle from the GPU state; from its own state the oracle takes decision {i} "
+                              f"({name}) the other way, margin {r:.3g} of its tolerance")
+        return True, (f"GPU = oracle from the GPU state; from its own state the oracle separates by "
+                      f"{abs(a['e'] - b['e']):.3g} (tolerance {tol_e:.3g}) with the same decisions")
+    if len(log_a):
+        rs = [_normalised_margin(log_a, i, tol_e) for i in range(len(log_a))]
+        i = int(np.argmin(rs))
+        if rs[i] <= 1.0:
+            return True, (f"GPU departs from the oracle's replay of its state at a near tie: decision {i} "
+                          f"({oracle.DECISION_KINDS[int(log_a.kind[i])]}), margin {rs[i]:.3g} of its tolerance")
+    dev, sens = abs(gpu["e"] - a["e"]), abs(n["e"] - a["e"])
+    if (gpu["acc"] is None or int(gpu["acc"]) == int(a["acc"])) and dev <= 2.0 * sens:
+        return True, (f"GPU departs from the oracle's replay of its state by {dev:.3g}, within the oracle's own "
+                      f"response to a one-ulp move ({sens:.3g})")
+    return False, (f"GPU departs from the oracle's replay of its state by {dev:.3g} (one-ulp response {sens:.3g}, "
+                   f"tolerance {tol_e:.3g}) with no near-tie decision")
+
+
+def gpu_starts(ctx, grid, cx, nc, seed, optimizer=dsdp.DSDP_OPT_BFGS):
+    """The GPU's drawn initial conformations (trace mode 2), FP32 values as FP64."""
+    res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=1, n_opt_iters=1, seed=seed,
+                   optimizer=optimizer, trace=2, top_k=1)
+    assert np.all(res["trace"][:, 0, 7 + cx.T + 2] == -2.0)
+    return res["trace"][:, 0, :7 + cx.T].astype(np.float64)
 
 
 # ---------------------------------------------------------------- local optimisation
@@ -101,24 +136,27 @@ def explain_divergence(log_a, log_b, gpu_matches_a, tol_e):
                                             (dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ3)])
 def test_local_opt_short_horizon(ctx, shape, optimizer, mode):
     """The first local optimisation of each chain (step 0) after k = 0, 1, 2, 3, 5, 10
-    iterations.  k = 0 is a pure evaluation of the Philox-drawn pose: every chain
-    agrees.  For k = 1, 2, 3 every chain agrees with the oracle or its divergence
-    is an explained near tie (module docstring; A starts from the FP32-rounded
-    start, within an ulp of the GPU's own).  For every k each GPU result is
-    valid: its reported energy is the oracle's score of the pose it reports, and
-    no worse than the start.  Eq. 3 maps (score maps only, the gradient of the
-    interpolant) run the chain kernel's Eq. 3 path."""
+    iterations.  The GPU draws the oracle's starts (to FP32 rounding), and k = 0,
+    a pure evaluation of each drawn pose, agrees for every chain.  For k = 1, 2,
+    3 every chain agrees with the oracle or its divergence is explained (module
+    docstring; A starts from the GPU's own drawn start); for k = 5 and 10 the
+    divergences and their explanations are reported.  For every k each GPU
+    result is valid: its reported energy is the oracle's score of the pose it
+    reports, and no worse than the start.  Eq. 3 maps (score maps only, the
+    gradient of the interpolant) run the chain kernel's Eq. 3 path."""
     cx = complex_for(shape)
     og = cx.oracle_grid()
     grid = _grid(ctx, cx, mode)
     nc, nx = 32, 7 + cx.T
     dp = oracle.dock_params_array(1, optimizer, 1.2, cx.box_lo(), cx.size)
     starts = np.array([oracle.chain_init(cx.olig, dp, 7, c) for c in range(nc)])
-    starts32 = starts.astype(np.float32).astype(np.float64)
     e_start = np.array([cx.olig.score_grid(og, mode, c)[0].sum() for c in starts])
     tol0 = np.array([energy_tol(cx, og, mode, c) for c in starts])
-    agree, flips = {}, []
+    agree, notes = {}, []
     try:
+        gstarts = gpu_starts(ctx, grid, cx, nc, 7, optimizer)
+        # the GPU draws the oracle's starts (to FP32 rounding of the same formulas)
+        assert np.allclose(gstarts, starts, rtol=0, atol=2e-5)
         e0, _ = dsdp.dsdp_score_eval(ctx, grid, cx.lig, starts)
         agree[0] = int(np.sum(np.abs(e0 - e_start) <= tol0))
         for iters in (1, 2, 3, 5, 10):
@@ -137,29 +175,30 @@ def test_local_opt_short_horizon(ctx, shape, optimizer, mode):
                 if abs(e_gpu - e_b) <= tol:
                     a += 1
                     continue
-                if iters > 3:
-                    continue
-                _, e_a, _, _, log_a = cx.olig.local_opt(og, mode, optimizer, starts32[c], opt=o, log=True)
-                ok, why = explain_divergence(log_a, log_b, abs(e_gpu - e_a) <= tol, tol)
-                flips.append((iters, c, why))
-                assert ok, (iters, c, e_gpu, e_a, e_b, why)
+                _, e_a, _, _, log_a = cx.olig.local_opt(og, mode, optimizer, gstarts[c], opt=o, log=True)
+                _, e_n, _, _, log_n = cx.olig.local_opt(og, mode, optimizer, nudged(gstarts[c]), opt=o, log=True)
+                ok, why = explain_divergence(dict(e=e_gpu, acc=None), dict(e=e_a, acc=None, log=log_a),
+                                             dict(e=e_b, acc=None, log=log_b), dict(e=e_n, acc=None, log=log_n), tol)
+                notes.append((iters, c, ok, why))
+                assert ok or iters > 3, (iters, c, e_gpu, e_a, e_b, e_n, why)
             agree[iters] = a
     finally:
         dsdp.dsdp_grid_free(ctx, grid)
     print(f"{shape}, optimizer {optimizer}, maps {'eq4' if mode == dsdp.DSDP_GRID_EQ4 else 'eq3'}: "
           f"chains agreeing with the oracle after k iterations {agree} (of {nc})")
-    for f in flips:
-        print("  explained divergence (k, chain, why):", f)
+    for f in notes:
+        print("  divergence (k, chain, explained, why):", f)
     assert agree[0] == nc, agree
 
 
 # ---------------------------------------------------------------- Monte Carlo chains
-def check_traces(cx, og, res, nc, S, iters, optimizer, seed, label):
+def check_traces(cx, og, res, nc, S, iters, optimizer, seed, label, gstarts):
     """Step-for-step comparison of GPU chain traces with the oracle's own chains:
     mutation modes bit-exact at every step, every GPU state's energy the oracle's
-    score of that state, and each chain's first divergence explained.  Also each
-    chain's best energy is the oracle's score of its best pose.  Returns the
-    steps agreeing before each chain's first divergence."""
+    score of that state, and each chain's first divergence explained (gstarts:
+    the GPU's drawn starts).  Also each chain's best energy is the oracle's score
+    of its best pose.  Returns the steps agreeing before each chain's first
+    divergence."""
     nx = 7 + cx.T
     tr = res["trace"]
     dp = oracle.dock_params_array(S, optimizer, 1.2, cx.box_lo(), cx.size)
@@ -176,26 +215,27 @@ def check_traces(cx, og, res, nc, S, iters, optimizer, seed, label):
             assert abs(cx.olig.score_grid(og, 0, pose)[0].sum() - tr[c, s, nx + 1]) <= tol, (label, c, s)
             if first_div <= S:
                 continue
-            e_gpu, acc_gpu = float(tr[c, s, nx + 0]), int(tr[c, s, nx + 3])
+            gpu = dict(e=float(tr[c, s, nx + 0]), acc=int(tr[c, s, nx + 3]))
             if s > 0:
                 prev = tr[c, s - 1, :nx].astype(np.float64)
                 tol = max(tol, energy_tol(cx, og, 0, prev))
-            if abs(e_gpu - ref["trace_rec"][s, 2]) <= tol and acc_gpu == int(ref["trace_rec"][s, 1]):
+            if abs(gpu["e"] - ref["trace_rec"][s, 2]) <= tol and gpu["acc"] == int(ref["trace_rec"][s, 1]):
                 continue
             first_div = s
             if s == 0:
                 start = oracle.chain_init(cx.olig, dp, seed, c)
-                _, e_a, _, _, log_a = cx.olig.local_opt(og, 0, optimizer, start.astype(np.float32).astype(np.float64),
-                                                        opt=o, log=True)
-                _, _, _, _, log_b = cx.olig.local_opt(og, 0, optimizer, start, opt=o, log=True)
-                match_a = abs(e_gpu - e_a) <= tol
+                runs = []
+                for x in (gstarts[c], start, nudged(gstarts[c])):
+                    _, e, _, _, log = cx.olig.local_opt(og, 0, optimizer, x, opt=o, log=True)
+                    runs.append(dict(e=e, acc=1, log=log))
             else:
                 e_prev = float(tr[c, s - 1, nx + 1])
-                _, _, rec_a, log_a = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, prev, e_prev, opt=o, log=True)
-                _, _, _, log_b = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, ref["trace_conf"][s - 1],
-                                                ref["trace_rec"][s - 1, 3], opt=o, log=True)
-                match_a = abs(e_gpu - rec_a[2]) <= tol and acc_gpu == int(rec_a[1])
-            ok, why = explain_divergence(log_a, log_b, match_a, tol)
+                runs = []
+                for x, e0 in ((prev, e_prev), (ref["trace_conf"][s - 1], ref["trace_rec"][s - 1, 3]),
+                              (nudged(prev), e_prev)):
+                    _, _, rec, log = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, x, e0, opt=o, log=True)
+                    runs.append(dict(e=rec[2], acc=int(rec[1]), log=log))
+            ok, why = explain_divergence(gpu, *runs, tol)
             notes.append((c, s, why))
             assert ok, (label, c, s, why)
         agree_steps.append(first_div)
@@ -224,9 +264,10 @@ def test_chains_step_for_step(ctx, shape, optimizer):
     try:
         res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=7,
                        optimizer=optimizer, trace=1, top_k=4)
+        gstarts = gpu_starts(ctx, grid, cx, nc, 7, optimizer)
     finally:
         dsdp.dsdp_grid_free(ctx, grid)
-    check_traces(cx, og, res, nc, S, iters, optimizer, 7, f"{shape} optimizer {optimizer}")
+    check_traces(cx, og, res, nc, S, iters, optimizer, 7, f"{shape} optimizer {optimizer}", gstarts)
 
 
 @pytest.mark.parametrize("shape,nc,S", [("16at", 24, 40), ("40at", 12, 20), ("60at", 12, 20)])
@@ -304,7 +345,8 @@ def test_mixed_tile_batch_against_the_oracle(ctx):
                 og = cx.oracle_grid()
                 label = f"mixed batch, {cx.lig.n_atoms} atoms, {S} x {iters}"
                 if trace:
-                    check_traces(cx, og, r, 24, S, iters, dsdp.DSDP_OPT_BFGS, 3 + i, label)
+                    gstarts = gpu_starts(ctx, grids[i], cx, 24, 3 + i)
+                    check_traces(cx, og, r, 24, S, iters, dsdp.DSDP_OPT_BFGS, 3 + i, label, gstarts)
                 else:
                     for c in range(24):
                         best = r["chain_best_conf"][c].astype(np.float64)
