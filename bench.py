@@ -728,6 +728,38 @@ def _timed_plan(dsdp, torch, items, dtype, sptr, steps, optimizer=0):
     return a.elapsed_time(b) * 1e-3 / steps
 
 
+def run_voxel_features(dsdp, torch, synth, dev, sptr, reps=20):
+    """Receptor voxel features (36^3 x 18, the binding-site network's input) of
+    4,000- and 8,000-atom receptors: ms per receptor (CUDA events, `reps`
+    launches after one untimed); the work is the surface test, n x 98 points
+    against each atom's neighbours."""
+    out = {}
+    work = torch.empty(dsdp.dsdp_voxel_work_bytes(), dtype=torch.uint8, device=dev)
+    vox = torch.empty((36, 36, 36, 18), dtype=torch.float32, device=dev)
+    for n in (4000, 8000):
+        rec = synth.receptor(n, 7)
+        radius, feats = synth.receptor_voxel_inputs(rec)
+        c = synth.protein_center(rec)
+        d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (rec.xyz, radius, feats)]
+
+        def launch():
+            dsdp.dsdp_voxelize_device(n, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), c, vox.data_ptr(),
+                                      work.data_ptr(), work.numel(), sptr)
+
+        launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            launch()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[f"atoms_{n}"] = dict(ms_per_receptor=ms, receptors_per_s=1e3 / ms,
+                                 surface_atoms=int(vox[..., 17].sum().item()))
+    return out
+
+
 def run_configs(args, rank, dev, steps=2):
     """The other workloads of the method, each timed as grid builds + one plan
     launch (chains, FP64 rescoring, top-k) on one stream:
@@ -796,6 +828,7 @@ def run_configs(args, rank, dev, steps=2):
     one = _timed_plan(dsdp, torch, items[:1], dsdp.DSDP_MAP_F32, sptr, 3)
     sec = _timed_plan(dsdp, torch, items, dsdp.DSDP_MAP_F32, sptr, steps)
     evals = sum(int(k["evals"].sum().item()) for _, k in items)
+    out["voxel_features"] = run_voxel_features(dsdp, torch, synth, dev, sptr)
     out["plain_2k"] = dict(one_system_ms=1e3 * one, batched_systems_per_s=len(items) / sec,
                            evals_per_s=evals / sec, systems_per_launch=len(items),
                            workload="2,000-atom receptor, 20 A box (54^3 x 8 FP32 maps), 20-atom ligand / 4 "

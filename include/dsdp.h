@@ -413,6 +413,37 @@ dsdp_status dsdp_plan_destroy(dsdp_ctx* ctx, dsdp_plan* plan);
 dsdp_status dsdp_gather_bench_device(const dsdp_grid_view* grid, const float* d_points, const uint8_t* d_types,
                                      int32_t n_points, int32_t repeats, float* d_out, void* stream);
 
+/* ------------------------------------------------------------------ receptor voxel features
+ * The binding-site network's input (Sec. 2, "Protein-ligand binding site
+ * prediction"): the protein as 36 x 36 x 36 voxels with 18 channels over a 70 A
+ * cube centred on it; S and Se share one element channel and the freed channel
+ * marks the protein surface.  The network itself is not part of this library.
+ *   - Voxel k of an axis covers [c - 35 + k 70/36, c - 35 + (k + 1) 70/36): an
+ *     atom's voxel is floor((x - (c - 35)) * (36/70)), computed in FP32
+ *     (c - 35 rounded to FP32 first); atoms outside the cube are dropped.
+ *   - Channels 0..16: sums of the caller's 17 per-atom features over the
+ *     voxel's atoms.  Channel 17: the voxel's number of surface atoms, atom i
+ *     being on the surface when a test point x_i + (r_i + 1.4) u of its
+ *     solvent-accessible sphere (98 directions u: the primitive integer
+ *     vectors of {-2..2}^3, normalised) lies outside the sphere of radius
+ *     r_j + 1.4 of every other atom (Shrake and Rupley).
+ *   - Sums are exact and independent of the atom order: each feature is
+ *     rounded to a multiple of 2^-24 and accumulated as a 64-bit integer; a
+ *     channel is the sum times 2^-24 rounded to FP32.
+ * Arguments: d_xyz [n_atoms][3], d_radius [n_atoms] (van der Waals radii, A),
+ * d_features [n_atoms][17], all FP32 device arrays; center (host, A); d_out
+ * [36][36][36][18] FP32 (z, y, x, channel) device; d_work: device scratch of
+ * at least dsdp_voxel_work_bytes() bytes, 8-byte aligned, owned by the caller.
+ * Enqueued on `stream`; DSDP_ERR_INVALID_ARG for a negative count, NULL
+ * arrays, a short or misaligned work buffer or a non-finite centre. */
+#define DSDP_VOXEL_N 36
+#define DSDP_VOXEL_FEATURES 17
+#define DSDP_VOXEL_CHANNELS 18
+uint64_t dsdp_voxel_work_bytes(void);
+dsdp_status dsdp_voxelize_device(int32_t n_atoms, const float* d_xyz, const float* d_radius,
+                                 const float* d_features, const double center[3], float* d_out, void* d_work,
+                                 uint64_t work_bytes, void* stream);
+
 /* ------------------------------------------------------------------ no-allocation postprocess
  * The paper has no counterpart to this call; it serves callers that cannot
  * allocate device memory when they need the postprocess: code holding an

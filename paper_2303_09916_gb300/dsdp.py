@@ -142,6 +142,9 @@ _sig = {
     "dsdp_gather_bench_device": (C.c_int32, [P(dsdp_grid_view), C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                              C.c_void_p, C.c_void_p]),
     "dsdp_rescore_topk_noalloc": (C.c_int32, [P(dsdp_job_device), C.c_void_p]),
+    "dsdp_voxel_work_bytes": (C.c_uint64, []),
+    "dsdp_voxelize_device": (C.c_int32, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_double), C.c_void_p,
+                                         C.c_void_p, C.c_uint64, C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -439,6 +442,21 @@ def dsdp_gather_bench_device(view: dsdp_grid_view, d_points: int, d_types: int, 
                              d_out: int, stream: int = 0):
     _check(_lib.dsdp_gather_bench_device(C.byref(view), int(d_points), int(d_types), int(n_points), int(repeats),
                                          int(d_out), stream or None))
+
+
+DSDP_VOXEL_N, DSDP_VOXEL_FEATURES, DSDP_VOXEL_CHANNELS = 36, 17, 18
+
+
+def dsdp_voxel_work_bytes() -> int:
+    return int(_lib.dsdp_voxel_work_bytes())
+
+
+def dsdp_voxelize_device(n_atoms: int, d_xyz: int, d_radius: int, d_features: int, center, d_out: int, d_work: int,
+                         work_bytes: int, stream: int = 0):
+    """Receptor voxel features [36][36][36][18] into d_out (see include/dsdp.h)."""
+    c = (C.c_double * 3)(*[float(v) for v in center])
+    _check(_lib.dsdp_voxelize_device(int(n_atoms), int(d_xyz) or None, int(d_radius) or None, int(d_features) or None,
+                                     c, int(d_out) or None, int(d_work) or None, int(work_bytes), stream or None))
 
 
 def dsdp_rescore_topk_noalloc(job: dsdp_job_device, stream: int = 0):
