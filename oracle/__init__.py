@@ -34,9 +34,11 @@ _lib = None
 N_MAP_TYPES = 8
 XS_NAMES = ["C_H", "C_P", "N_P", "N_D", "N_A", "O_A", "O_DA", "S_P", "N_DA"]
 
-# [max_iters, c1, shrink, max_trials, min_curvature, bb_alpha0, bb_alpha_min, bb_alpha_max]
+# [max_iters, c1, shrink, max_trials, min_curvature, bb_alpha0, bb_alpha_min, bb_alpha_max, step_scale,
+#  grad_perturb].  Sensitivity probes for the tests (not part of the method): step_scale multiplies every
+# step the optimisers take (1: exact); grad_perturb adds delta |g|_inf p_i to every gradient (0: exact).
 DEFAULT_OPT = dict(max_iters=100, c1=1e-4, shrink=0.5, max_trials=10, min_curvature=1e-10,
-                   bb_alpha0=1e-3, bb_alpha_min=1e-4, bb_alpha_max=0.1)
+                   bb_alpha0=1e-3, bb_alpha_min=1e-4, bb_alpha_max=0.1, step_scale=1.0, grad_perturb=0.0)
 
 
 def build(force: bool = False) -> str:
@@ -122,7 +124,8 @@ def _opt_array(opt=None):
     if opt:
         o.update(opt)
     return np.array([o["max_iters"], o["c1"], o["shrink"], o["max_trials"], o["min_curvature"],
-                     o["bb_alpha0"], o["bb_alpha_min"], o["bb_alpha_max"]], dtype=np.float64)
+                     o["bb_alpha0"], o["bb_alpha_min"], o["bb_alpha_max"], o["step_scale"], o["grad_perturb"]],
+                    dtype=np.float64)
 
 
 def constants():

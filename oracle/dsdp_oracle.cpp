@@ -632,7 +632,25 @@ struct OptSettings {
   double bb_alpha0 = 1e-3;
   double bb_alpha_min = 1e-4;
   double bb_alpha_max = 0.1;
+  // Every step the optimisers take is multiplied by this factor; 1 (exact) by
+  // default.  Tests set it to 1 +- 2^-24 to measure the search's own response
+  // to a one-ulp FP32 rounding of its steps (a sensitivity probe, not part of
+  // the method).
+  double step_scale = 1.0;
+  // Every gradient the optimisers see gets delta |g|_inf p_i added, p_i =
+  // ((7 i + 3) mod 5 - 2) / 2; 0 (exact) by default.  Tests set it to the FP32
+  // gradient error measured on the GPU to measure the search's own response to
+  // gradients of that accuracy (a sensitivity probe, not part of the method).
+  double grad_perturb = 0.0;
 };
+
+// The gradient probe of OptSettings::grad_perturb (no-op at 0).
+void perturb_gradient(const OptSettings& st, int n, double* g) {
+  if (st.grad_perturb == 0.0) return;
+  double gm = 0.0;
+  for (int i = 0; i < n; ++i) gm = std::max(gm, std::fabs(g[i]));
+  for (int i = 0; i < n; ++i) g[i] += st.grad_perturb * gm * (double)((7 * i + 3) % 5 - 2) * 0.5;
+}
 
 struct OptResult {
   double e;
@@ -670,6 +688,7 @@ OptResult bfgs(Objective& f, double* x, const OptSettings& st) {
   for (int i = 0; i < n; ++i) H[i * n + i] = 1.0;
   OptResult R{0.0, 0, 0};
   double e = f.eval(x, g.data());
+  perturb_gradient(st, n, g.data());
   R.evals = 1;
   for (int it = 0; it < st.max_iters; ++it) {
     for (int i = 0; i < n; ++i) {
@@ -682,9 +701,10 @@ OptResult bfgs(Objective& f, double* x, const OptSettings& st) {
     bool accepted = false;
     for (int trial = 0; trial < st.max_trials; ++trial) {
       for (int i = 0; i < nx; ++i) xt[i] = x[i];
-      for (int i = 0; i < n; ++i) s[i] = alpha * d[i];
+      for (int i = 0; i < n; ++i) s[i] = alpha * d[i] * st.step_scale;
       f.step(xt.data(), s.data());
       et = f.eval(xt.data(), gt.data());
+      perturb_gradient(st, n, gt.data());
       ++R.evals;
       if (st.log) st.log->push_back(Decision{0, et - (e + st.c1 * alpha * gd), 0.0});
       if (et <= e + st.c1 * alpha * gd) {
@@ -721,13 +741,15 @@ OptResult barzilai_borwein(Objective& f, double* x, const OptSettings& st) {
   std::vector<double> g(n), gn(n), s(n), xbest(x, x + nx);
   OptResult R{0.0, 0, 0};
   double e = f.eval(x, g.data());
+  perturb_gradient(st, n, g.data());
   R.evals = 1;
   double ebest = e;
   double alpha = st.bb_alpha0;
   for (int it = 0; it < st.max_iters; ++it) {
-    for (int i = 0; i < n; ++i) s[i] = -alpha * g[i];
+    for (int i = 0; i < n; ++i) s[i] = -alpha * g[i] * st.step_scale;
     f.step(x, s.data());
     const double en = f.eval(x, gn.data());
+    perturb_gradient(st, n, gn.data());
     ++R.evals;
     double sy = 0.0, ss = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -1274,7 +1296,8 @@ void orc_score_exact(void* h, int n_rec, const double* rec_xyz, const int* rec_t
 
 void orc_apply_step(void* h, double* conf, const double* s) { apply_step(*(Ligand*)h, conf, s); }
 
-// opt_params: [max_iters, c1, shrink, max_trials, min_curvature, bb_alpha0, bb_alpha_min, bb_alpha_max]
+// opt_params: [max_iters, c1, shrink, max_trials, min_curvature, bb_alpha0, bb_alpha_min, bb_alpha_max,
+//              step_scale, grad_perturb]
 static OptSettings opt_from(const double* p) {
   OptSettings s;
   s.max_iters = (int)p[0];
@@ -1285,6 +1308,8 @@ static OptSettings opt_from(const double* p) {
   s.bb_alpha0 = p[5];
   s.bb_alpha_min = p[6];
   s.bb_alpha_max = p[7];
+  s.step_scale = p[8];
+  s.grad_perturb = p[9];
   return s;
 }
 

@@ -9,18 +9,22 @@ clashes, BFGS updates), after which trajectories separate.  Every separation
 from the oracle's own run is therefore explained or the test fails.  At a
 chain's first divergence the step is replayed on the oracle from the GPU's
 exact state before it (A; the GPU's drawn start for the first local
-optimisation, recorded with trace mode 2), from the oracle's own state (B), and
-from the GPU's state moved by one FP32 ulp in position (N), each recording the
-margin of every decision it takes (the Armijo test, Barzilai-Borwein's best
-iterate and curvature test, BFGS's curvature test, the Metropolis acceptance):
+optimisation, recorded with trace mode 2) and from the oracle's own state (B),
+recording the margin of every decision (the Armijo test, Barzilai-Borwein's
+best iterate and curvature test, BFGS's curvature test, the Metropolis
+acceptance), and from A's state under FP32-sized perturbations (the probes:
+the position moved by one FP32 ulp; every step scaled by 1 +- 2^-24; every
+gradient perturbed by +- G_FP32 of its largest component, the FP32 gradient
+error the score tests bound):
   * the GPU reproduces A: it did what the oracle does from the GPU's state.
     The separation from B is then the oracle's own response to the FP32
     difference of the two states (which agreed within tolerance), either
     through a decision A and B take differently -- reported with its margin --
     or through continuous amplification (reported);
   * otherwise some decision of A is a near tie (its margin within tolerance),
-    or the GPU lies no farther from A than the oracle's own response to a
-    one-ulp move of the state (|E_gpu - E_A| <= 2 |E_N - E_A|);
+    or the GPU lies no farther from A than twice the oracle's largest response
+    to the probes (the search amplifies FP32-sized differences that much:
+    BFGS from a clash is the usual case);
   * anything else fails.
 Tolerances: energies E_REL * max(sum_i |e_i|, 1) each, so a margin of two
 energies is a tie within twice that; a curvature product s.y within
@@ -38,7 +42,7 @@ if not torch.cuda.is_available():
 
 from paper_2303_09916_gb300 import dsdp  # noqa: E402
 
-from gpu_util import E_REL, G_REL, Complex  # noqa: E402
+from gpu_util import E_REL, G_FP32, G_REL, Complex  # noqa: E402
 
 # (receptor atoms, box edge, ligand atoms, torsions, seed): one and two atoms per lane
 SHAPES = {"16at": (1500, 14.0, 16, 4, 5), "40at": (2500, 18.0, 40, 10, 6), "60at": (2500, 20.0, 60, 15, 8)}
@@ -89,10 +93,22 @@ def nudged(conf):
     return c
 
 
-def explain_divergence(gpu, a, b, n, tol_e):
-    """(explained, description) of a divergence; gpu / a / b / n: dicts with the
-    energy `e`, the Metropolis outcome `acc` (None for a local optimisation) and,
-    for the oracle runs, the decision log `log` (module docstring)."""
+PROBES = [dict(), dict(step_scale=1.0 + 2.0 ** -24), dict(step_scale=1.0 - 2.0 ** -24),
+          dict(grad_perturb=G_FP32), dict(grad_perturb=-G_FP32)]
+
+
+def probe_runs(run, x):
+    """run(x, opt_extra) -> dict(e, acc, log) for the state x moved by one ulp and
+    for the optimiser probes from x."""
+    out = [run(nudged(x), {})]
+    out += [run(x, p) for p in PROBES[1:]]
+    return out
+
+
+def explain_divergence(gpu, a, b, probes, tol_e):
+    """(explained, description) of a divergence; gpu / a / b / probes: dicts with
+    the energy `e`, the Metropolis outcome `acc` (None for a local optimisation)
+    and, for the oracle runs, the decision log `log` (module docstring)."""
     def same(x, y):
         return abs(x["e"] - y["e"]) <= tol_e and (x["acc"] is None or int(x["acc"]) == int(y["acc"]))
 
@@ -113,11 +129,14 @@ def explain_divergence(gpu, a, b, n, tol_e):
         if rs[i] <= 1.0:
             return True, (f"GPU departs from the oracle's replay of its state at a near tie: decision {i} "
                           f"({oracle.DECISION_KINDS[int(log_a.kind[i])]}), margin {rs[i]:.3g} of its tolerance")
-    dev, sens = abs(gpu["e"] - a["e"]), abs(n["e"] - a["e"])
-    if (gpu["acc"] is None or int(gpu["acc"]) == int(a["acc"])) and dev <= 2.0 * sens:
-        return True, (f"GPU departs from the oracle's replay of its state by {dev:.3g}, within the oracle's own "
-                      f"response to a one-ulp move ({sens:.3g})")
-    return False, (f"GPU departs from the oracle's replay of its state by {dev:.3g} (one-ulp response {sens:.3g}, "
+    dev = abs(gpu["e"] - a["e"])
+    sens = max(abs(p["e"] - a["e"]) for p in probes)
+    acc_ok = gpu["acc"] is None or int(gpu["acc"]) == int(a["acc"]) or any(
+        int(p["acc"]) == int(gpu["acc"]) for p in probes)
+    if acc_ok and dev <= 2.0 * sens:
+        return True, (f"GPU departs from the oracle's replay of its state by {dev:.3g}, within twice the oracle's "
+                      f"own response to FP32-sized perturbations ({sens:.3g})")
+    return False, (f"GPU departs from the oracle's replay of its state by {dev:.3g} (probe response {sens:.3g}, "
                    f"tolerance {tol_e:.3g}) with no near-tie decision")
 
 
@@ -175,10 +194,12 @@ def test_local_opt_short_horizon(ctx, shape, optimizer, mode):
                 if abs(e_gpu - e_b) <= tol:
                     a += 1
                     continue
-                _, e_a, _, _, log_a = cx.olig.local_opt(og, mode, optimizer, gstarts[c], opt=o, log=True)
-                _, e_n, _, _, log_n = cx.olig.local_opt(og, mode, optimizer, nudged(gstarts[c]), opt=o, log=True)
-                ok, why = explain_divergence(dict(e=e_gpu, acc=None), dict(e=e_a, acc=None, log=log_a),
-                                             dict(e=e_b, acc=None, log=log_b), dict(e=e_n, acc=None, log=log_n), tol)
+                def run(x, extra):
+                    _, e, _, _, log = cx.olig.local_opt(og, mode, optimizer, x, opt=dict(o, **extra), log=True)
+                    return dict(e=e, acc=None, log=log)
+
+                ok, why = explain_divergence(dict(e=e_gpu, acc=None), run(gstarts[c], {}),
+                                             dict(e=e_b, acc=None, log=log_b), probe_runs(run, gstarts[c]), tol)
                 notes.append((iters, c, ok, why))
                 assert ok or iters > 3, (iters, c, e_gpu, e_a, e_b, e_n, why)
             agree[iters] = a
@@ -223,19 +244,22 @@ def check_traces(cx, og, res, nc, S, iters, optimizer, seed, label, gstarts):
                 continue
             first_div = s
             if s == 0:
-                start = oracle.chain_init(cx.olig, dp, seed, c)
-                runs = []
-                for x in (gstarts[c], start, nudged(gstarts[c])):
-                    _, e, _, _, log = cx.olig.local_opt(og, 0, optimizer, x, opt=o, log=True)
-                    runs.append(dict(e=e, acc=1, log=log))
+                def run(x, extra):
+                    _, e, _, _, log = cx.olig.local_opt(og, 0, optimizer, x, opt=dict(o, **extra), log=True)
+                    return dict(e=e, acc=1, log=log)
+
+                a_state, b_run = gstarts[c], run(oracle.chain_init(cx.olig, dp, seed, c), {})
             else:
                 e_prev = float(tr[c, s - 1, nx + 1])
-                runs = []
-                for x, e0 in ((prev, e_prev), (ref["trace_conf"][s - 1], ref["trace_rec"][s - 1, 3]),
-                              (nudged(prev), e_prev)):
-                    _, _, rec, log = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, x, e0, opt=o, log=True)
-                    runs.append(dict(e=rec[2], acc=int(rec[1]), log=log))
-            ok, why = explain_divergence(gpu, *runs, tol)
+
+                def run(x, extra, e0=e_prev):
+                    _, _, rec, log = oracle.mc_step(cx.olig, og, 0, dp, seed, c, s, x, e0, opt=dict(o, **extra),
+                                                    log=True)
+                    return dict(e=rec[2], acc=int(rec[1]), log=log)
+
+                a_state = prev
+                b_run = run(ref["trace_conf"][s - 1], {}, ref["trace_rec"][s - 1, 3])
+            ok, why = explain_divergence(gpu, run(a_state, {}), b_run, probe_runs(run, a_state), tol)
             notes.append((c, s, why))
             assert ok, (label, c, s, why)
         agree_steps.append(first_div)

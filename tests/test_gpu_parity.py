@@ -22,7 +22,7 @@ if not torch.cuda.is_available():
 
 from paper_2303_09916_gb300 import dsdp  # noqa: E402
 
-from gpu_util import E_REL, G_REL, Complex, vertex_ambiguity, vertex_scales  # noqa: E402
+from gpu_util import E_REL, G_FP32, G_REL, Complex, vertex_ambiguity, vertex_scales  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -103,9 +103,16 @@ def scoring_complex():
     return Complex(2000, 16.0, 24, 6, seed=3)
 
 
-def _compare_scores(cx, grid_o, mode, confs, e, g, flags=3):
+def _compare_scores(cx, grid_o, mode, confs, e, g, flags=3, label=""):
+    """Element-wise comparison with the oracle at the stated tolerances (term
+    scale for energies, gradient norm for gradients).  Also reports, and bounds,
+    the errors relative to the result itself: |dE| / max(|E|, 1) and
+    ||dg||_inf / max(||g||_inf, 1e-2) -- how much of the budget the FP32
+    arithmetic (with the ex2.approx and __sincosf intrinsics) really uses: on
+    Eq. 4 maps the gradient stays within G_FP32, the size of the gradient probe
+    the chain tests use."""
     skipped = 0
-    worst_e = worst_g = 0.0
+    worst_e = worst_er = worst_g = 0.0
     for i, c in enumerate(confs):
         if cx.conf_is_ambiguous(grid_o, mode, c):
             skipped += 1
@@ -117,11 +124,17 @@ def _compare_scores(cx, grid_o, mode, confs, e, g, flags=3):
         dg = np.abs(g[i] - gref).max()
         gs = max(np.abs(gref).max(), 1e-2)
         worst_e = max(worst_e, de / scale)
+        worst_er = max(worst_er, de / max(abs(eref), 1.0))
         worst_g = max(worst_g, dg / gs)
         assert de <= E_REL * scale, (i, e[i], eref, scale)
         assert dg <= G_REL * gs, (i, g[i], gref)
     assert skipped <= len(confs) // 4, skipped
-    return worst_e, worst_g
+    print(f"score errors {label} mode {mode} flags {flags}: max |dE| / sum|e_i| {worst_e:.2e}, "
+          f"|dE| / max(|E|, 1) {worst_er:.2e}, |dg|_inf / |g|_inf {worst_g:.2e} ({skipped} skipped)")
+    assert worst_er <= E_REL, worst_er
+    if mode == dsdp.DSDP_GRID_EQ4:
+        assert worst_g <= G_FP32, worst_g
+    return worst_e, worst_er, worst_g
 
 
 @pytest.mark.parametrize("mode", [dsdp.DSDP_GRID_EQ4, dsdp.DSDP_GRID_EQ3])

@@ -434,3 +434,22 @@ def test_mc_step_log_ends_with_the_metropolis_decision():
         assert log.margin[-1] == pytest.approx((rec[2] - e_cur) + 1.2 * math.log(u), rel=1e-12, abs=1e-12)
         assert bool(log.taken()[-1]) == bool(rec[1])
         assert (log.kind == 0).sum() == int(rec[4]) - 1  # Armijo tests: every evaluation after the first
+
+
+def test_sensitivity_probes_move_the_first_step_as_stated():
+    """The test-only probes of the optimisers: step_scale multiplies each step,
+    grad_perturb adds delta |g|_inf p_i (p_0 = 1/2) to each gradient; on a 1-D
+    quadratic the first Armijo margin follows in closed form, and the defaults
+    leave every result unchanged."""
+    a, b, x0, c1 = 4.0, 1.0, 2.0, 1e-4
+    f = lambda x: 0.5 * a * x * x - b * x
+    g0 = a * x0 - b
+    for scale, delta in ((1.0, 0.0), (1.0 + 2 ** -24, 0.0), (1.0, 1e-3), (0.75, 0.25)):
+        gp = g0 + delta * abs(g0) * 0.5
+        *_, log = oracle.opt_test(0, 0, np.array([x0]), np.array([[a]]), np.array([b]),
+                                  opt=dict(max_iters=1, step_scale=scale, grad_perturb=delta), log=True)
+        expect = f(x0 - gp * scale) - (f(x0) - c1 * gp * gp)
+        assert log.margin[0] == pytest.approx(expect, rel=1e-12, abs=1e-12), (scale, delta)
+    ref = oracle.opt_test(1, 0, np.array([-1.2, 1.0, -0.5]), opt=dict(max_iters=50))
+    same = oracle.opt_test(1, 0, np.array([-1.2, 1.0, -0.5]), opt=dict(max_iters=50, step_scale=1.0, grad_perturb=0.0))
+    assert np.array_equal(ref[0], same[0]) and ref[1:] == same[1:]
