@@ -420,8 +420,9 @@ def run_device(args, rank, world, dev, dist):
     slots = [make_slot() for _ in range(args.pipeline_depth if args.pipeline else 1)]
     plan = dsdp.dsdp_plan_create(None, slots[0]["jobs"], 0, 0)
     build_grids(slots[0], sptr)
-    if args.tile_config < 0:
-        tile_config = dsdp.dsdp_plan_autotune(plan, sptr, 2)  # register budget, chains per CTA, work queue
+    autotune_ms = None
+    if args.tile_config < 0:  # register budget, chains per CTA, work queue
+        tile_config, autotune_ms = dsdp.dsdp_plan_autotune(plan, sptr, 2, with_times=True)
     else:
         dsdp.dsdp_plan_destroy(None, plan)
         plan = dsdp.dsdp_plan_create(None, slots[0]["jobs"], plan_flags(dsdp, args.tile_config),
@@ -507,7 +508,8 @@ def run_device(args, rank, world, dev, dist):
     gather_gbs = gather_microbench(dsdp, torch, dev, jobs[0].grid, dtype, stream)  # the first system's maps
     for pl in plans:
         dsdp.dsdp_plan_destroy(None, pl)
-    return dict(tile_config=tile_config, elapsed_ms=elapsed_ms, serial_ms=serial_ms, grid_ms=grid_ms, chain_ms=chain_ms,
+    return dict(tile_config=tile_config, autotune_ms=autotune_ms, elapsed_ms=elapsed_ms, serial_ms=serial_ms,
+                grid_ms=grid_ms, chain_ms=chain_ms,
                 rescore_ms=rescore_ms,
                 total_evals=total_evals, flops=flops, mufu=mufu, gather_bytes=gather_bytes, clocks=clk,
                 launches_per_step=args.batch + n_plan_kernels, results_ok=results_ok, gather_gbs=gather_gbs)
@@ -681,7 +683,7 @@ def run_uneven_graph(args, dev, steps=3):
         keeps.append(keep)
     build_grid(dsdp, grid, dsdp.DSDP_MAP_F32, sptr)
     plan = dsdp.dsdp_plan_create(None, jobs, 0, 0)
-    chosen = dsdp.dsdp_plan_autotune(plan, sptr, 2)
+    chosen, tune_ms = dsdp.dsdp_plan_autotune(plan, sptr, 2, with_times=True)
     cap = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
     torch.cuda.synchronize()
@@ -703,6 +705,7 @@ def run_uneven_graph(args, dev, steps=3):
     return dict(ligands_per_s=len(jobs) / (ms * 1e-3), ms_per_launch=ms, evals_per_s=evals / (ms * 1e-3),
                 ligand_atoms=f"{min(atoms)}-{max(atoms)}", chains_per_ligand=cfg.n_chains,
                 chain_kernel=describe_tile_config(chosen), launch="captured CUDA graph",
+                autotune_ms_per_launch={describe_tile_config(k): round(v, 3) for k, v in sorted(tune_ms.items())},
                 results_ok=ok)
 
 
@@ -829,6 +832,35 @@ def run_configs(args, rank, dev, steps=2):
     sec = _timed_plan(dsdp, torch, items, dsdp.DSDP_MAP_F32, sptr, steps)
     evals = sum(int(k["evals"].sum().item()) for _, k in items)
     out["voxel_features"] = run_voxel_features(dsdp, torch, synth, dev, sptr)
+    # ---- atoms per lane: ligands of 32 atoms run one atom per lane, 33 atoms two
+    apl = {}
+    for n_lig in (32, 33):
+        items = []
+        for seed, rec, _ in sysl[:16]:
+            lig = synth.ligand(n_lig, T_LIG, seed, center=rec.pocket_center)
+            items.append(make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dsdp.DSDP_MAP_F32,
+                                         N_CHAINS, N_STEPS, N_ITERS, TOP_K))
+        plan = dsdp.dsdp_plan_create(None, [j for j, _ in items], dsdp.DSDP_PLAN_NO_RESCORE, 0)
+        try:
+            for _, keep in items:
+                build_grid(dsdp, keep["grid"], dsdp.DSDP_MAP_F32, sptr)
+            chosen = dsdp.dsdp_plan_autotune(plan, sptr, 1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            dsdp.dsdp_plan_launch(plan, sptr)
+            b.record()
+            torch.cuda.synchronize()
+        finally:
+            dsdp.dsdp_plan_destroy(None, plan)
+        evals = sum(int(k["evals"].sum().item()) for _, k in items)
+        pairs = sum(k["info"]["n_pairs"] for _, k in items) / len(items)
+        sec = a.elapsed_time(b) * 1e-3
+        apl[f"atoms_{n_lig}"] = dict(atoms_per_lane=1 if n_lig <= 32 else 2, evals_per_s=evals / sec,
+                                     ns_per_eval=1e9 * sec / evals,
+                                     mean_intra_pairs=pairs, chain_kernel=describe_tile_config(chosen))
+    out["atoms_per_lane"] = dict(apl, note="16 typical-4k receptors; the same 8-torsion ligand shape at 32 atoms "
+                                          "(one atom per lane) and 33 (two per lane); chain stage only")
     out["plain_2k"] = dict(one_system_ms=1e3 * one, batched_systems_per_s=len(items) / sec,
                            evals_per_s=evals / sec, systems_per_launch=len(items),
                            workload="2,000-atom receptor, 20 A box (54^3 x 8 FP32 maps), 20-atom ligand / 4 "
@@ -1251,6 +1283,8 @@ def main():
                    "chains": N_CHAINS, "mc_steps": N_STEPS, "opt_iters": N_ITERS, "optimizer": args.optimizer,
                    "top_k": TOP_K, "l2": "flushed before each step (256 MB write on the step's stream); each step builds 2.1 GB of maps", "parallelism": f"replicas x{world}",
                    "chain_kernel": describe_tile_config(r["tile_config"]),
+                   "autotune_ms_per_launch": ({describe_tile_config(k): round(v, 3) for k, v in
+                                               sorted(r["autotune_ms"].items())} if r["autotune_ms"] else None),
                    "pipeline": (f"{args.pipeline_depth} streams: consecutive steps overlap (own maps and outputs "
                                 "per stream)"
                                 if args.pipeline else "none: steps back to back on one stream")},

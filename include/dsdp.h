@@ -386,8 +386,10 @@ dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_devic
  * persistent work queue, keeps the fastest for this plan and records it for
  * later plans of the same shape (process-wide).  *chosen = 1 + variant
  * + 4 * log2(W) + 12 * persistent (1 .. 24; the first part is the plan's
- * tile_config).  Synchronises the stream. */
-dsdp_status dsdp_plan_autotune(dsdp_plan* plan, void* stream, int32_t repeats, int32_t* chosen);
+ * tile_config).  ms_by_config: NULL, or 24 floats receiving the measured chain
+ * stage time (ms per launch) of configuration chosen - 1, -1 where a
+ * configuration was not run.  Synchronises the stream. */
+dsdp_status dsdp_plan_autotune(dsdp_plan* plan, void* stream, int32_t repeats, int32_t* chosen, float* ms_by_config);
 /* Enqueue the plan's kernels on `stream` (chains, then FP64 rescoring and
  * top-k).  No allocation and no host synchronisation: a launch can be
  * captured into a CUDA graph and replayed.  Different plans may run at once

@@ -422,8 +422,11 @@ extern "C" dsdp_status dsdp_plan_launch(dsdp_plan* P, void* stream) {
   return dsdp_plan_launch_stage(P, DSDP_STAGE_ALL, stream);
 }
 
-extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t repeats, int32_t* chosen) {
+extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t repeats, int32_t* chosen,
+                                          float* ms_by_config) {
   if (!P) return set_error(DSDP_ERR_INVALID_ARG, "plan is NULL");
+  if (ms_by_config)
+    for (int i = 0; i < 24; ++i) ms_by_config[i] = -1.f;
   if (repeats < 1) repeats = 1;
   const cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t a, b;
@@ -460,6 +463,7 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, a, b);
+      if (ms_by_config) ms_by_config[var + 4 * (w == 4 ? 2 : w - 1) + 12 * pers] = ms / repeats;
       if (ms < best) {
         best = ms;
         best_var = var;

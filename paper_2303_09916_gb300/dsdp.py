@@ -137,7 +137,7 @@ _sig = {
     "dsdp_plan_launch": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "dsdp_plan_launch_stage": (C.c_int32, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "dsdp_plan_kernel_count": (C.c_int32, [C.c_void_p]),
-    "dsdp_plan_autotune": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, P(C.c_int32)]),
+    "dsdp_plan_autotune": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, P(C.c_int32), P(C.c_float)]),
     "dsdp_plan_destroy": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "dsdp_gather_bench_device": (C.c_int32, [P(dsdp_grid_view), C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                              C.c_void_p, C.c_void_p]),
@@ -416,10 +416,15 @@ def dsdp_plan_create(ctx, jobs, flags=0, tile_config=0):
     return out.value
 
 
-def dsdp_plan_autotune(plan, stream: int = 0, repeats: int = 1) -> int:
+def dsdp_plan_autotune(plan, stream: int = 0, repeats: int = 1, with_times: bool = False):
+    """The chosen configuration (1 + variant + 4 log2 W + 12 persistent); with
+    with_times also {configuration: ms per chain launch} of every one measured."""
     chosen = C.c_int32()
-    _check(_lib.dsdp_plan_autotune(plan, stream or None, int(repeats), C.byref(chosen)))
-    return chosen.value
+    ms = (C.c_float * 24)()
+    _check(_lib.dsdp_plan_autotune(plan, stream or None, int(repeats), C.byref(chosen), ms))
+    if not with_times:
+        return chosen.value
+    return chosen.value, {k + 1: float(ms[k]) for k in range(24) if ms[k] >= 0}
 
 
 def dsdp_plan_launch(plan, stream: int = 0):
