@@ -1292,6 +1292,7 @@ def main():
                    "ms_per_step": r["serial_ms"] / args.steps,
                    "note": "the same steps on one stream (stage_ms and the rooflines are from this pass)"},
         "evals_per_s": world * r["total_evals"] * args.steps / (r["elapsed_ms"] * 1e-3),
+        "evals_per_step": r["total_evals"],
         "stage_ms": {"grid_build": r["grid_ms"], "chains": r["chain_ms"], "rescore_topk": r["rescore_ms"]},
         "roofline": chain_roofline(r["gather_bytes"], r["flops"], r["mufu"], per_launch_s, r["gather_gbs"], peaks,
                                    peaks_src, sm_mhz, capture),
