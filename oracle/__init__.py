@@ -296,7 +296,8 @@ class Ligand:
         return c, out[0], int(out[1]), int(out[2]), Decisions(buf, cnt.value)
 
 
-DECISION_KINDS = {0: "armijo", 1: "bb_best", 2: "metropolis", 3: "bfgs_curvature", 4: "bb_curvature"}
+DECISION_KINDS = {0: "armijo", 1: "bb_best", 2: "metropolis", 3: "bfgs_curvature", 4: "bb_curvature",
+                  5: "eq3_cell_face"}
 
 
 class Decisions:
@@ -317,12 +318,14 @@ class Decisions:
     def taken(self):
         """The branch of each decision: True for accept / update / new best."""
         return np.where((self.kind == 0), self.margin <= 0,
-                        np.where((self.kind == 1) | (self.kind == 2), self.margin < 0, self.margin > 0))
+                        np.where((self.kind == 1) | (self.kind == 2), self.margin < 0,
+                                 np.where(self.kind == 5, True, self.margin > 0)))
 
 
 def _log_buffer(opt_arr):
-    # at most max_iters x (max_trials + 1) + 1 decisions per local optimisation, + 1 Metropolis
-    cap = int(opt_arr[0]) * (int(opt_arr[3]) + 2) + 8
+    # per local optimisation at most max_iters x (max_trials + 1) + 1 decisions and one cell-face
+    # record per evaluation (Eq. 3), + 1 Metropolis
+    cap = 2 * int(opt_arr[0]) * (int(opt_arr[3]) + 2) + 8
     return np.zeros((cap, 3)), ctypes.c_int()
 
 

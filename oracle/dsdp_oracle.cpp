@@ -611,6 +611,9 @@ struct Objective {
 //     (equivalent to E' < E or u < exp(-(E' - E) / T) for u in [0, 1))
 //   3 BFGS curvature condition: y.s - min_curvature; H is updated iff > 0
 //   4 Barzilai-Borwein curvature: s.y; the BB1 step is taken iff > 0
+//   5 cell choice of an Eq. 3 evaluation: the smallest distance (A) of an atom
+//     inside the grid to a face of its cell, where Eq. 3's gradient jumps (one
+//     record per evaluation on Eq. 3 maps; Eq. 4's gradient is continuous there)
 // scale: |s|_1 (|g|_inf + |g'|_inf) for kinds 3 and 4 -- the bound on how far
 // s.y moves when each gradient component moves by a fraction of its norm --,
 // 0 otherwise (the energies' own scale applies).
@@ -787,12 +790,27 @@ struct DockObjective : Objective {
   const Ligand* L;
   const Grid* grid;
   int mode;
+  std::vector<Decision>* log = nullptr;  // kind 5 records on Eq. 3 maps (recording only)
   DockObjective(const Ligand* l, const Grid* g, int m) : L(l), grid(g), mode(m) {
     nx = 7 + l->T;
     nd = 6 + l->T;
   }
   double eval(const double* x, double* g) override {
-    const Terms t = evaluate(*L, grid, mode, nullptr, x, 3, g);
+    Pose P;
+    const Terms t = evaluate(*L, grid, mode, nullptr, x, 3, g, log && mode == 1 ? &P : nullptr);
+    if (log && mode == 1) {
+      double dmin = 1e300;
+      for (const V3& a : P.atom) {
+        const double r[3] = {a.x, a.y, a.z};
+        for (int k = 0; k < 3; ++k) {
+          const double u = (r[k] - grid->origin[k]) / grid->h;
+          if (!(u > 0.0 && u < grid->n[k] - 1)) continue;  // on the wall: no cell face
+          const double f = u - std::floor(u);
+          dmin = std::min(dmin, std::min(f, 1.0 - f) * grid->h);
+        }
+      }
+      log->push_back(Decision{5, dmin, 0.0});
+    }
     return t.inter + t.intra;
   }
   void step(double* x, const double* s) override { apply_step(*L, x, s); }
@@ -1343,6 +1361,7 @@ void orc_local_opt_log(void* h, const double* maps, const int* n, const double* 
   OptSettings st = opt_from(opt_params);
   std::vector<Decision> log;
   st.log = &log;
+  obj.log = &log;
   const OptResult r = optimizer == 0 ? bfgs(obj, conf, st) : barzilai_borwein(obj, conf, st);
   out[0] = r.e, out[1] = (double)r.evals, out[2] = r.iters;
   *n_log = copy_log(log, log_out, log_cap);
@@ -1461,6 +1480,7 @@ void orc_mc_step_log(void* h, const double* maps, const int* n, const double* or
   std::vector<Decision> log;
   ds.opt.log = &log;
   DockObjective obj(&L, &G, mode);
+  obj.log = &log;
   ChainRng rng{{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)}, chain};
   std::vector<double> best(7 + L.T);
   double e_best = -1e300;

@@ -453,3 +453,23 @@ def test_sensitivity_probes_move_the_first_step_as_stated():
     ref = oracle.opt_test(1, 0, np.array([-1.2, 1.0, -0.5]), opt=dict(max_iters=50))
     same = oracle.opt_test(1, 0, np.array([-1.2, 1.0, -0.5]), opt=dict(max_iters=50, step_scale=1.0, grad_perturb=0.0))
     assert np.array_equal(ref[0], same[0]) and ref[1:] == same[1:]
+
+
+def test_eq3_cell_face_records_are_the_nearest_face_distances():
+    """On Eq. 3 maps the decision log holds, for every evaluation, the smallest
+    distance of an atom inside the grid to a face of its cell (where Eq. 3's
+    gradient jumps); the first is that of the starting pose, computed here from
+    its coordinates; Eq. 4 maps record none."""
+    s, lig, rec_xyz, rec_t = _tiny_complex(3, n_lig=9, T=3, n_rec=120)
+    grid = oracle.grid_build(rec_xyz, rec_t, np.zeros(3), np.array([12.0, 12.0, 12.0]), 0.5)
+    c0 = _random_conf(lig, np.random.default_rng(4), spread=1.0)
+    _, _, evals, _, log = lig.local_opt(grid, 1, 0, c0, opt=dict(max_iters=5), log=True)
+    faces = log.margin[log.kind == 5]
+    assert len(faces) == evals
+    u = (lig.coords(c0) - grid.origin) / grid.h
+    inside = (u > 0) & (u < grid.n - 1)
+    f = u - np.floor(u)
+    expect = (np.minimum(f, 1 - f) * grid.h)[inside].min()
+    assert faces[0] == pytest.approx(expect, rel=1e-12)
+    *_, log4 = lig.local_opt(grid, 0, 0, c0, opt=dict(max_iters=5), log=True)
+    assert not np.any(log4.kind == 5)
