@@ -832,6 +832,10 @@ def run_configs(args, rank, dev, steps=2):
     sec = _timed_plan(dsdp, torch, items, dsdp.DSDP_MAP_F32, sptr, steps)
     evals = sum(int(k["evals"].sum().item()) for _, k in items)
     out["voxel_features"] = run_voxel_features(dsdp, torch, synth, dev, sptr)
+    out["plain_2k"] = dict(one_system_ms=1e3 * one, batched_systems_per_s=len(items) / sec,
+                           evals_per_s=evals / sec, systems_per_launch=len(items),
+                           workload="2,000-atom receptor, 20 A box (54^3 x 8 FP32 maps), 20-atom ligand / 4 "
+                                    "torsions, 64 chains x 100 steps, top-9 FP64 rescoring")
     # ---- atoms per lane: ligands of 32 atoms run one atom per lane, 33 atoms two
     apl = {}
     for n_lig in (32, 33):
@@ -861,10 +865,6 @@ def run_configs(args, rank, dev, steps=2):
                                      mean_intra_pairs=pairs, chain_kernel=describe_tile_config(chosen))
     out["atoms_per_lane"] = dict(apl, note="16 typical-4k receptors; the same 8-torsion ligand shape at 32 atoms "
                                           "(one atom per lane) and 33 (two per lane); chain stage only")
-    out["plain_2k"] = dict(one_system_ms=1e3 * one, batched_systems_per_s=len(items) / sec,
-                           evals_per_s=evals / sec, systems_per_launch=len(items),
-                           workload="2,000-atom receptor, 20 A box (54^3 x 8 FP32 maps), 20-atom ligand / 4 "
-                                    "torsions, 64 chains x 100 steps, top-9 FP64 rescoring")
     return out
 
 
