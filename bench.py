@@ -19,6 +19,16 @@ rescoring and top-k.
          / dsdp_dock_poll) with host arrays, copies included; two steps in
          flight (the next step's requests go in before this step's results
          are read back)
+  roofline  dock_chains_kernel against the maximum of its three bounds per
+         launch: corner-gather bytes at the measured HBM copy peak, FP32 FMA
+         work at the FP32 peak, special-function work at the MUFU peak; the
+         binding one gives `bound`, `achieved` and `frac` (also the fraction of
+         the L2-gather microbenchmark, --gather-bench alone)
+  the same line also carries the other workloads of the method: one job per
+  launch, the uneven batch under a CUDA graph, BF16 / FP16 maps with their
+  error, Barzilai-Borwein, the plain-2k workload, receptor voxel features,
+  the atoms-per-lane boundary, a short Poisson serving run, the search-region
+  and grid-mode variants, and the autotuner's time for every configuration
   --impl reference   the FP64 CPU oracle on the host cores (whole systems)
 
 N > 1 (torchrun): independent replicas, one per GPU; value sums all ranks'
