@@ -39,32 +39,45 @@ constexpr int kPointsPerLane = 4;  // 128 slots for the 98 directions
 constexpr float kProbe = 1.4f;
 constexpr float kFix = 16777216.0f;  // 2^24
 
-// Direction m (0..97) of the surface test, in the order a, b, c = -2..2.
-__device__ float3 sas_direction(int m) {
-  int seen = 0;
+// The 98 test directions as integer vectors (a, b, c) in {-2..2}^3 with
+// gcd(|a|, |b|, |c|) = 1, built at compile time; a lane normalises its own.
+struct SasDirs {
+  signed char v[98][3];
+};
+constexpr int gcd_abs(int x, int y) {
+  x = x < 0 ? -x : x;
+  y = y < 0 ? -y : y;
+  while (y) {
+    const int t = x % y;
+    x = y;
+    y = t;
+  }
+  return x;
+}
+constexpr SasDirs make_sas_dirs() {
+  SasDirs d{};
+  int m = 0;
   for (int a = -2; a <= 2; ++a)
     for (int b = -2; b <= 2; ++b)
       for (int c = -2; c <= 2; ++c) {
-        if (a == 0 && b == 0 && c == 0) continue;
-        int g = abs(a), y = abs(b);
-        while (y) {
-          const int t = g % y;
-          g = y;
-          y = t;
-        }
-        y = abs(c);
-        while (y) {
-          const int t = g % y;
-          g = y;
-          y = t;
-        }
-        if (g != 1) continue;
-        if (seen++ == m) {
-          const float len = __fsqrt_rn((float)(a * a + b * b + c * c));
-          return make_float3(__fdiv_rn((float)a, len), __fdiv_rn((float)b, len), __fdiv_rn((float)c, len));
-        }
+        if ((a == 0 && b == 0 && c == 0) || gcd_abs(gcd_abs(a, b), c) != 1) continue;
+        d.v[m][0] = (signed char)a;
+        d.v[m][1] = (signed char)b;
+        d.v[m][2] = (signed char)c;
+        ++m;
       }
-  return make_float3(0.f, 0.f, 0.f);
+  return d;
+}
+static_assert(make_sas_dirs().v[97][0] == 2 && make_sas_dirs().v[97][1] == 2 && make_sas_dirs().v[97][2] == 1,
+              "98 primitive directions");
+__constant__ SasDirs c_sas_dirs = make_sas_dirs();
+
+// Unit test direction m (0..97): the integer vector over its FP32 length
+// (correctly rounded square root and division).
+__device__ __forceinline__ float3 sas_direction(int m) {
+  const int a = c_sas_dirs.v[m][0], b = c_sas_dirs.v[m][1], c = c_sas_dirs.v[m][2];
+  const float len = __fsqrt_rn((float)(a * a + b * b + c * c));
+  return make_float3(__fdiv_rn((float)a, len), __fdiv_rn((float)b, len), __fdiv_rn((float)c, len));
 }
 
 __global__ void __launch_bounds__(256) voxel_atoms_kernel(int n, const float* __restrict__ xyz,
