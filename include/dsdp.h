@@ -373,16 +373,16 @@ enum {
  * 4 log2(W): register budget (variant 0: 128 registers, 16 warps per SM; 1: 96,
  * 20 warps; 2: 80, 24 warps; 3: 72, 28 warps) and W = 1, 2 or 4.  Budgets 80
  * and 72 are compiled for ligands of up to 32 atoms only (one atom per lane);
- * ligands above 32 atoms run at 128 or 96 (variants 2 and 3 take 96), and a
- * map-format group that mixes ligands of up to 32 and of more than 32 atoms
- * runs one kernel holding both tile sizes, compiled for 128 registers only.
- * Results do not depend on the configuration. */
+ * ligands above 32 atoms run at 128 or 96 (variants 2 and 3 take 96), and so
+ * does a map-format group that mixes ligands of up to 32 and of more than 32
+ * atoms (one kernel holding both tile sizes).  Results do not depend on the
+ * configuration. */
 dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsdp_job_device* jobs, uint32_t flags,
                              int32_t tile_config, dsdp_plan** out);
 /* Autotuner: runs the plan's chain stage `repeats` times for each register
  * budget the plan's kernels are compiled for (128 and 96; also 80 and 72 when
- * every ligand has at most 32 atoms; 128 only when every group mixes tile
- * sizes), each tile of W = 1, 2, 4 chains per CTA, with and without the
+ * a group holds only ligands of at most 32 atoms), each tile of W = 1, 2, 4
+ * chains per CTA, with and without the
  * persistent work queue, keeps the fastest for this plan and records it for
  * later plans of the same shape (process-wide).  *chosen = 1 + variant
  * + 4 * log2(W) + 12 * persistent (1 .. 24; the first part is the plan's

@@ -10,9 +10,9 @@ namespace dsdp {
 // warps per SM, no spills), variant 1 at 96 (20 warps), 2 at 80 (24 warps) and
 // 3 at 72 (28 warps), each with a few more bytes spilled; the autotuner picks
 // per plan by measurement.  Variants 2 and 3 are compiled for the
-// one-atom-per-lane tiles only (two atoms per lane take variants 0 and 1, mixed
-// tiles variant 0; a plan asking for more falls back to the nearest budget
-// compiled).  The bounds are stated for CTAs of up to 4 warps (chains); CTAs of
+// one-atom-per-lane tiles only (two atoms per lane and mixed tiles take
+// variants 0 and 1; a plan asking for more falls back to the 96-register
+// kernel).  The bounds are stated for CTAs of up to 4 warps (chains); CTAs of
 // 1 or 2 warps get the same register cap.
 constexpr int kMaxChainWarps = 4;
 template <int VAR>
@@ -145,8 +145,8 @@ cudaError_t launch_chains_impl(const ChainLaunch& a, cudaStream_t st) {
     }
   }
   if (a.apl_mask == 2) return a.variant ? launch_chains_var<FMT, 1, 2>(a, st) : launch_chains_var<FMT, 0, 2>(a, st);
-  // mixed tiles: the 128-register budget only
-  return launch_chains_var<FMT, 0, 3>(a, st);
+  // mixed tiles: the 128- and 96-register budgets
+  return a.variant ? launch_chains_var<FMT, 1, 3>(a, st) : launch_chains_var<FMT, 0, 3>(a, st);
 }
 
 template <int FMT>

@@ -438,9 +438,9 @@ extern "C" dsdp_status dsdp_plan_autotune(dsdp_plan* P, void* stream, int32_t re
   int best_var = P->variant, best_pers = (P->flags & DSDP_PLAN_PERSISTENT) ? 1 : 0, best_w = P->warps_per_cta;
   dsdp_status s = DSDP_OK;
   // register budgets compiled: 128, 96, 80, 72 for one atom per lane, 128 and
-  // 96 for two, 128 only for mixed tiles (launch_chains_impl)
-  int n_var = 1;
-  for (const dsdp_plan::Group& g : P->groups) n_var = std::max(n_var, g.apl_mask == 1 ? 4 : g.apl_mask == 2 ? 2 : 1);
+  // 96 for two and for mixed tiles (launch_chains_impl)
+  int n_var = 2;
+  for (const dsdp_plan::Group& g : P->groups) n_var = std::max(n_var, g.apl_mask == 1 ? 4 : 2);
   for (int w = 1; w <= 4 && s == DSDP_OK; w *= 2) {
     e = plan_use_warps(P, w);
     if (e != cudaSuccess) {
