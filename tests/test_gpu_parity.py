@@ -65,6 +65,13 @@ def test_grid_build_f32_matches_oracle(ctx, ragged):
     g_err = np.abs(maps[..., 1:] - ref[..., 1:]).max(-1)
     g_tol = G_REL * np.maximum(scale[..., 1], 1e-2)
     assert np.all(g_err[ok] <= g_tol[ok]), (g_err / g_tol)[ok].max()
+    # errors relative to the vertex values themselves: what the FP32 sums (with
+    # the ex2.approx intrinsic) really use of the term-scale budget
+    e_rel = (e_err / np.maximum(np.abs(ref[..., 0]), 1.0))[ok].max()
+    g_rel = (g_err / np.maximum(np.abs(ref[..., 1:]).max(-1), 1e-2))[ok].max()
+    print(f"grid vertices: max |dE| / sum|f| {(e_err / np.maximum(scale[..., 0], 1.0))[ok].max():.2e}, "
+          f"|dE| / max(|E|, 1) {e_rel:.2e}, |dg|_inf / |g|_inf {g_rel:.2e}")
+    assert e_rel <= E_REL and g_rel <= G_REL, (e_rel, g_rel)
 
 
 @pytest.mark.parametrize("dtype", [dsdp.DSDP_MAP_BF16, dsdp.DSDP_MAP_F16])
