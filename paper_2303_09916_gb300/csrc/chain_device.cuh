@@ -19,6 +19,7 @@ struct LigView {
   const uint2* pair_rec;  // after the staged prefix: read from the global blob only
   const uint2* steps;
   const int32_t* torsion_body;
+  const int16_t* lane_map;  // [32][2]: atom in slot s of lane l (-1 empty); lane l holds atom l up to 32 atoms
   int n_atoms, T, n_bodies, n_pairs, n_steps, rounds;
 };
 
@@ -31,6 +32,7 @@ __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
   v.pair_rec = reinterpret_cast<const uint2*>(b + v.h->off_pairs);
   v.steps = reinterpret_cast<const uint2*>(b + v.h->off_steps);
   v.torsion_body = reinterpret_cast<const int32_t*>(b + v.h->off_torsion_body);
+  v.lane_map = reinterpret_cast<const int16_t*>(b + v.h->off_lane_map);
   v.n_atoms = v.h->n_atoms;
   v.T = v.h->n_torsions;
   v.n_bodies = v.h->n_bodies;
@@ -40,8 +42,9 @@ __device__ __forceinline__ LigView view_blob(const uint8_t* b) {
   return v;
 }
 
-// Per-lane ligand data: atom slots lane * APL + s and, on lane b < n_bodies,
-// body b's record; re-read from the staged blob (shared memory) where used.
+// Per-lane ligand data: the atoms of the lane's slots (atom lane with one atom
+// per lane; the blob's lane map with two) and, on lane b < n_bodies, body b's
+// record; re-read from the staged blob (shared memory) where used.
 template <int APL>
 struct LaneLig {
   int n_atoms, nb, T, tbody;
@@ -166,13 +169,15 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   // ---- atom positions
   float3 pos[APL];
   int type[APL];
+  int atom[APL];  // the slot's atom, -1 when empty
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
-    const int i = lane * APL + s;
-    const float4 a = L.atom[i < N ? i : N - 1];
+    atom[s] = APL == 1 ? (lane < N ? lane : -1) : (int)L.lane_map[2 * lane + s];
+    const int i = atom[s];
+    const float4 a = L.atom[i >= 0 ? i : 0];
     const int packed = __float_as_int(a.w);
     type[s] = packed & 0xff;
-    const int b = i < N ? (packed >> 8) & 0xff : 0;
+    const int b = i >= 0 ? (packed >> 8) & 0xff : 0;
     const Quat Qb = shflq(Q, b);
     const float3 Ob = shfl3(O, b);
     pos[s] = Ob + qrot(Qb, make_float3(a.x, a.y, a.z));
@@ -257,7 +262,7 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   // ---- inter: trilinear score and gradient (Eq. 2, Eq. 4 / Eq. 3)
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
-    if ((flags & DSDP_TERM_INTER) && lane * APL + s < N) {
+    if ((flags & DSDP_TERM_INTER) && atom[s] >= 0) {
       float3 gi;
       // the cell is located here, where it is used: holding it across the intra
       // block miscompiled the two-atoms-per-lane kernels (gradient x channel lost)
@@ -268,17 +273,38 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
   const float E = warp_sum(e_lane);
   // ---- back-propagation: inclusive prefix sums over atoms (depth-first
   //      order) of (g_i, (r_i - p) x g_i); a subtree is a contiguous range.
+  //      With two atoms per lane the lane map is not in atom order: each slot
+  //      first parks its raw terms at its atom's place, and lane l then scans
+  //      atoms 2l and 2l + 1 of the atom order.
+  if (APL == 2) {
+#pragma unroll
+    for (int s = 0; s < APL; ++s) {
+      if (atom[s] < 0) continue;
+      const float3 t = cross3(pos[s] - c.p, g[s]);
+      W.pre[2 * atom[s]] = make_float4(g[s].x, g[s].y, g[s].z, t.x);
+      W.pre[2 * atom[s] + 1] = make_float4(t.y, t.z, 0.f, 0.f);
+    }
+    __syncwarp();
+  }
   float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float raw[APL][6];
 #pragma unroll
   for (int s = 0; s < APL; ++s) {
-    if (lane * APL + s >= N) continue;
-    const float3 t = cross3(pos[s] - c.p, g[s]);
-    v[0] += g[s].x;
-    v[1] += g[s].y;
-    v[2] += g[s].z;
-    v[3] += t.x;
-    v[4] += t.y;
-    v[5] += t.z;
+    const int i = lane * APL + s;  // atom order
+#pragma unroll
+    for (int k = 0; k < 6; ++k) raw[s][k] = 0.f;
+    if (i >= N) continue;
+    if (APL == 1) {
+      const float3 t = cross3(pos[s] - c.p, g[s]);
+      raw[s][0] = g[s].x, raw[s][1] = g[s].y, raw[s][2] = g[s].z;
+      raw[s][3] = t.x, raw[s][4] = t.y, raw[s][5] = t.z;
+    } else {
+      const float4 h0 = W.pre[2 * i], h1 = W.pre[2 * i + 1];
+      raw[s][0] = h0.x, raw[s][1] = h0.y, raw[s][2] = h0.z;
+      raw[s][3] = h0.w, raw[s][4] = h1.x, raw[s][5] = h1.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] += raw[s][k];
   }
   float inc[6];
 #pragma unroll
@@ -291,8 +317,9 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
       if (lane >= o) inc[k] += t;
     }
   }
+  if (APL == 2) __syncwarp();  // every raw value read before the prefix overwrites it
   {
-    // this lane's atoms: exclusive prefix of the lane plus its own slots
+    // this lane's atoms (atom order): exclusive prefix of the lane plus its own slots
     float run[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) run[k] = inc[k] - v[k];
@@ -300,13 +327,8 @@ __device__ __forceinline__ float eval_conf(const MapView& M, const LigView& L, c
     for (int s = 0; s < APL; ++s) {
       const int i = lane * APL + s;
       if (i >= N) continue;
-      const float3 t = cross3(pos[s] - c.p, g[s]);
-      run[0] += g[s].x;
-      run[1] += g[s].y;
-      run[2] += g[s].z;
-      run[3] += t.x;
-      run[4] += t.y;
-      run[5] += t.z;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) run[k] += raw[s][k];
       W.pre[2 * i] = make_float4(run[0], run[1], run[2], run[3]);
       W.pre[2 * i + 1] = make_float4(run[4], run[5], 0.f, 0.f);
     }

@@ -10,8 +10,9 @@ constexpr uint32_t kBlobMagic = 0x50445344u;  // "DSDP"
 constexpr int kMaxAtoms = DSDP_MAX_LIGAND_ATOMS;
 constexpr int kMaxBodies = DSDP_MAX_TORSIONS + 1;
 constexpr int kMaxDim = 6 + DSDP_MAX_TORSIONS;  // gradient / step dimension
-// Atoms per lane of a warp holding one conformation: internal atom i sits in
-// lane i / APL, slot i % APL.
+// Atoms per lane of a warp holding one conformation: up to 32 atoms internal
+// atom i sits in lane i; above, each lane has two slots and the blob's lane map
+// says which atom sits where.
 __host__ __device__ constexpr int atoms_per_lane(int n_atoms) { return n_atoms <= 32 ? 1 : 2; }
 
 // Intra-pair step table: the pairs are split into steps in which every lane
@@ -57,6 +58,9 @@ struct BlobHeader {
   int32_t pair_hyd_begin;  // pairs [pair_hyd_begin, pair_hb_begin) carry the hydrophobic term,
   uint32_t stage_bytes;    // prefix the FP32 kernels stage into shared memory (the FP64 geometry follows it)
   int32_t pair_hb_begin;   //   pairs [pair_hb_begin, n_pairs) the H-bond term, the others neither
+  uint32_t off_lane_map;   // int16[32][2]: internal atom in slot s of lane l (-1: empty); atom i in lane i
+                           //   up to 32 atoms, a degree-balanced assignment above (see assign_lanes)
+  uint32_t pad_[3];
 };
 static_assert(sizeof(BlobHeader) % 16 == 0, "blob header alignment");
 

@@ -42,6 +42,7 @@ struct Prepared {
   std::vector<uint32_t> pairs;      // i | j << 8 | (type_i * 8 + type_j) << 16
   std::vector<uint32_t> steps;       // [n_steps][32][2] step table (see kStepIdleNrs)
   int n_steps = 0;
+  std::vector<int16_t> lane_map;     // [32][2] internal atom in slot s of lane l, -1 empty
   std::vector<int> torsion_body;
   float root_ref[3];
 };
@@ -55,10 +56,41 @@ struct Prepared {
 // extra vertex joined to the lanes of odd degree: |out - in| <= 1), then
 // coloured with max(out, in) colours by alternating-path recolouring (Konig's
 // edge-colouring theorem for bipartite multigraphs); a colour is a step.
+// Atoms to lanes.  Up to 32 atoms: atom i in lane i.  Above (two slots per
+// lane), the lane's pair count bounds the schedule (half of the busiest lane's
+// pairs), so the 64 - n atoms with the most intra pairs get a lane of their own
+// and the others share lanes two by two, the one with the most pairs left with
+// the one with the fewest (ties by atom index); slot 0 holds the first.
+void assign_lanes(int n, const std::vector<int>& pi, const std::vector<int>& pj, std::vector<int16_t>& lane_map,
+                  std::vector<int>& lane_of, std::vector<int>& slot_of) {
+  lane_map.assign(64, (int16_t)-1);
+  lane_of.assign(n, 0);
+  slot_of.assign(n, 0);
+  if (atoms_per_lane(n) == 1) {
+    for (int a = 0; a < n; ++a) lane_map[2 * a] = (int16_t)a, lane_of[a] = a;
+    return;
+  }
+  std::vector<int> deg(n, 0), order(n);
+  for (size_t p = 0; p < pi.size(); ++p) ++deg[pi[p]], ++deg[pj[p]];
+  for (int a = 0; a < n; ++a) order[a] = a;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg[a] > deg[b]; });
+  const int singles = 64 - n;
+  int lane = 0;
+  for (int k = 0; k < singles; ++k, ++lane) lane_map[2 * lane] = (int16_t)order[k];
+  for (int lo = singles, hi = n - 1; lo < hi; ++lo, --hi, ++lane) {
+    lane_map[2 * lane] = (int16_t)order[lo];
+    lane_map[2 * lane + 1] = (int16_t)order[hi];
+  }
+  for (int l = 0; l < 32; ++l)
+    for (int s = 0; s < 2; ++s)
+      if (lane_map[2 * l + s] >= 0) lane_of[lane_map[2 * l + s]] = l, slot_of[lane_map[2 * l + s]] = s;
+}
+
 void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>& pj, const std::vector<int>& pc,
-                      const std::vector<float>& pn, std::vector<uint32_t>& table, int& n_steps) {
-  const int apl = atoms_per_lane(n), P = (int)pi.size(), V = 32, X = 32;  // X: the extra vertex
-  auto lane_of = [&](int a) { return a / apl; };
+                      const std::vector<float>& pn, const std::vector<int>& lane_of_atom,
+                      const std::vector<int>& slot_of_atom, std::vector<uint32_t>& table, int& n_steps) {
+  const int P = (int)pi.size(), V = 32, X = 32;  // X: the extra vertex
+  auto lane_of = [&](int a) { return lane_of_atom[a]; };
   // ---- orientation: act[p] = the active atom of pair p
   std::vector<int> act(P, -1);
   {
@@ -204,7 +236,7 @@ void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>&
       if (c < delta && A(v, c) >= 0) {
         const int p = A(v, c), a = act[p], b = a == pi[p] ? pj[p] : pi[p];
         x = (x & ~31u) | (uint32_t)lane_of(b);
-        x |= (uint32_t)(a % apl) << 10;
+        x |= (uint32_t)slot_of_atom[a] << 10;
         x |= pc[p] == 1 ? 1u << 12 : 0u;
         x |= pc[p] == 2 ? 1u << 13 : 0u;
         nrs = pn[p];
@@ -212,7 +244,7 @@ void build_pair_steps(int n, const std::vector<int>& pi, const std::vector<int>&
       if (c < delta && B(v, c) >= 0) {
         const int p = B(v, c), a = act[p], b = a == pi[p] ? pj[p] : pi[p];
         x = (x & ~(31u << 5)) | ((uint32_t)lane_of(a) << 5);
-        x |= (uint32_t)(b % apl) << 11;
+        x |= (uint32_t)slot_of_atom[b] << 11;
       }
       x |= step_bits;
       table[((size_t)st * V + v) * 2] = x;
@@ -448,7 +480,9 @@ dsdp_status prepare(const dsdp_ligand* L, Prepared& out) {
       const int tp = out.pairs[p] >> 16;
       pn[p] = (float)-(radius[tp / DSDP_NUM_MAP_TYPES] + radius[tp % DSDP_NUM_MAP_TYPES]);
     }
-    build_pair_steps(n, pi, pj, pc, pn, out.steps, out.n_steps);
+    std::vector<int> lane_of, slot_of;
+    assign_lanes(n, pi, pj, out.lane_map, lane_of, slot_of);
+    build_pair_steps(n, pi, pj, pc, pn, lane_of, slot_of, out.steps, out.n_steps);
   }
   double s2 = 0.0;
   for (int i = 0; i < n; ++i)
@@ -490,6 +524,8 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
   off = align16(off + 4 * (size_t)p.T);
   h.off_steps = (uint32_t)off;
   off = align16(off + 8 * 32 * (size_t)p.n_steps);
+  h.off_lane_map = (uint32_t)off;
+  off = align16(off + 2 * 64);
   h.stage_bytes = (uint32_t)off;  // the chain kernels stage only this prefix
   h.off_pairs = (uint32_t)off;
   off = align16(off + 8 * (size_t)p.P);
@@ -539,6 +575,7 @@ extern "C" dsdp_status dsdp_ligand_pack(const dsdp_ligand* ligand, void* blob, u
     }
   }
   if (p.n_steps) memcpy(b + h.off_steps, p.steps.data(), 4 * p.steps.size());
+  memcpy(b + h.off_lane_map, p.lane_map.data(), 2 * 64);
   if (p.T) memcpy(b + h.off_torsion_body, p.torsion_body.data(), 4 * (size_t)p.T);
   memcpy(b + h.off_atom64, p.local64.data(), 8 * 3 * (size_t)p.n);
   memcpy(b + h.off_body64, p.body64.data(), 8 * 6 * (size_t)p.B);

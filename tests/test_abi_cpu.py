@@ -35,10 +35,10 @@ def test_status_strings_and_version():
 
 
 def _parse_blob(blob):
-    hdr = struct.unpack_from("<2I5if3fi5Ii3IiIi", blob, 0)
+    hdr = struct.unpack_from("<2I5if3fi5Ii3IiIiI", blob, 0)
     keys = ["magic", "bytes", "n_atoms", "T", "n_bodies", "n_pairs", "rounds", "gyr", "rx", "ry", "rz", "root_atom",
             "off_atom", "off_user", "off_body", "off_pairs", "off_steps", "n_steps", "off_tb", "off_a64", "off_b64",
-            "hyd_begin", "stage_bytes", "hb_begin"]
+            "hyd_begin", "stage_bytes", "hb_begin", "off_lane_map"]
     h = dict(zip(keys, hdr))
     n, P = h["n_atoms"], h["n_pairs"]
     user = np.frombuffer(blob, dtype=np.int32, count=n, offset=h["off_user"])
@@ -52,6 +52,7 @@ def _parse_blob(blob):
     steps = np.frombuffer(blob, dtype=np.uint32, count=2 * 32 * h["n_steps"], offset=h["off_steps"]).reshape(
         h["n_steps"], 32, 2)
     brec = np.frombuffer(blob, dtype=np.int32, count=12 * h["n_bodies"], offset=h["off_body"]).reshape(-1, 12)
+    h["lane_map"] = np.frombuffer(blob, dtype=np.int16, count=64, offset=h["off_lane_map"]).reshape(32, 2)
     return h, user, body, pairs, steps, brec
 
 
@@ -69,7 +70,13 @@ def _check_steps(h, pairs, steps):
     """The intra-pair step table: every pair computed exactly once, no lane active
     or passive twice in a step, reaction forces routed back to the right lane."""
     n, P = h["n_atoms"], h["n_pairs"]
-    apl = 1 if n <= 32 else 2
+    lmap = h["lane_map"]
+    # every atom in exactly one slot; up to 32 atoms atom i alone in lane i
+    placed = sorted(int(a) for a in lmap.ravel() if a >= 0)
+    assert placed == list(range(n))
+    if n <= 32:
+        assert all(lmap[i, 0] == (i if i < n else -1) and lmap[i, 1] == -1 for i in range(32))
+    lane_of = {int(a): lane for lane in range(32) for a in lmap[lane] if a >= 0}
     assert h["n_steps"] % 2 == 0
     want = {(int(p & 0xFF), int((p >> 8) & 0xFF)): k for k, p in enumerate(pairs)}
     cls = _pair_class(h["types"][pairs & 0xFF], h["types"][(pairs >> 8) & 0xFF])
@@ -82,10 +89,10 @@ def _check_steps(h, pairs, steps):
         passive_of = {}
         step_cls = 0
         for lane in np.nonzero(active)[0]:
-            a = int(lane) * apl + int(act_slot[lane])
+            a = int(lmap[lane, act_slot[lane]])
             pl = int(partner[lane])
-            b = pl * apl + int(pas_slot[pl])
-            assert a < n and b < n and a != b
+            b = int(lmap[pl, pas_slot[pl]])
+            assert 0 <= a < n and 0 <= b < n and a != b
             assert pl not in passive_of, "lane passive twice in one step"
             passive_of[pl] = int(lane)
             assert int(pred[pl]) == lane, "reaction force not routed to the passive lane"
@@ -109,10 +116,23 @@ def _check_steps(h, pairs, steps):
     # the packed loop takes steps two at a time, so an odd count gets a pad
     deg = np.zeros(32, int)
     for p in pairs:
-        deg[(p & 0xFF) // apl] += 1
-        deg[((p >> 8) & 0xFF) // apl] += 1
+        deg[lane_of[int(p & 0xFF)]] += 1
+        deg[lane_of[int((p >> 8) & 0xFF)]] += 1
     bound = int(np.max((deg + 1) // 2))
     assert h["n_steps"] == bound + (bound & 1)
+    if n > 32:
+        # two atoms per lane: the 64 - n atoms with the most pairs alone in their lanes,
+        # the others paired most with fewest, so no lane carries more pairs than
+        # the busiest single atom and the largest pair sum of that pairing
+        adeg = np.zeros(n, int)
+        for p in pairs:
+            adeg[int(p & 0xFF)] += 1
+            adeg[int((p >> 8) & 0xFF)] += 1
+        order = sorted(range(n), key=lambda a: -adeg[a])  # stable: ties by atom index
+        shared = order[64 - n:]
+        want = max([adeg[a] for a in order[:64 - n]] +
+                   [adeg[shared[k]] + adeg[shared[-1 - k]] for k in range(len(shared) // 2)])
+        assert deg.max() == want
 
 
 @pytest.mark.parametrize("n,t,seed", [(8, 2, 0), (20, 4, 1), (30, 8, 2), (45, 12, 3), (60, 15, 4), (10, 0, 5),
