@@ -719,13 +719,17 @@ def run_uneven_graph(args, dev, steps=3):
                 results_ok=ok)
 
 
-def _timed_plan(dsdp, torch, items, dtype, sptr, steps, optimizer=0):
+def _timed_plan(dsdp, torch, items, dtype, sptr, steps, optimizer=0, tuned=None):
     """Grid builds + one plan launch (chains, FP64 rescoring, top-k) of all the
-    items, timed over `steps` repetitions after one untimed run: seconds per step."""
+    items, timed over `steps` repetitions after one untimed run: seconds per step.
+    tuned: a dict that receives the launch configuration the autotuner picks
+    (the plan is autotuned first), or None (the plan's default configuration)."""
     plan = dsdp.dsdp_plan_create(None, [j for j, _ in items], 0, 0)
     try:
         for _, keep in items:
             build_grid(dsdp, keep["grid"], dtype, sptr)
+        if tuned is not None:
+            tuned["chain_kernel"] = describe_tile_config(dsdp.dsdp_plan_autotune(plan, sptr, 1))
         dsdp.dsdp_plan_launch(plan, sptr)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -776,8 +780,8 @@ def run_voxel_features(dsdp, torch, synth, dev, sptr, reps=20):
 def run_configs(args, rank, dev, steps=2):
     """The other workloads of the method, each timed as grid builds + one plan
     launch (chains, FP64 rescoring, top-k) on one stream:
-      map_dtype: the typical-4k batch with BF16 and FP16 maps (FP32
-        accumulation).  Error stated per dtype: each chain's best search energy
+      map_dtype: the typical-4k batch with FP32, BF16 and FP16 maps (FP32
+        accumulation), each plan autotuned first.  Error stated per dtype: each chain's best search energy
         against the same pose scored on FP32 maps by the FP32 score kernel (which
         matches the FP64 oracle within 1e-4 of the term scale), relative to
         max(|E|, 1), median / p95 / max over all chains; and the top-1 FP64
@@ -798,9 +802,10 @@ def run_configs(args, rank, dev, steps=2):
     for name, dtype in (("f32", dsdp.DSDP_MAP_F32), ("bf16", dsdp.DSDP_MAP_BF16), ("f16", dsdp.DSDP_MAP_F16)):
         items = [make_device_job(dsdp, torch, dev, rec, lig, seed, BOX, SPACING, dtype, N_CHAINS, N_STEPS, N_ITERS,
                                  TOP_K) for seed, rec, lig in sysl]
-        sec = _timed_plan(dsdp, torch, items, dtype, sptr, steps)
+        tuned = {}
+        sec = _timed_plan(dsdp, torch, items, dtype, sptr, steps, tuned=tuned)
         evals = sum(int(k["evals"].sum().item()) for _, k in items)
-        runs[name] = (items, dict(systems_per_s=len(items) / sec, evals_per_s=evals / sec))
+        runs[name] = (items, dict(systems_per_s=len(items) / sec, evals_per_s=evals / sec, **tuned))
     f32_items = runs["f32"][0]
     for name in ("bf16", "f16"):
         items, row = runs[name]
