@@ -133,8 +133,7 @@ __device__ __forceinline__ void body_frames(const LigView& L, const Conf& c, Qua
     Q = c.q;
     O = c.p;
   } else if (child) {
-    float s, co;
-    __sincosf(0.5f * tb, &s, &co);  // |theta / 2| <= pi / 2: absolute error < 4e-7
+    const float s = sin_ftz(0.5f * tb), co = cos_ftz(0.5f * tb);  // |theta / 2| <= pi / 2: absolute error < 4e-7
     Q = Quat{co, s * b1.x, s * b1.y, s * b1.z};
     O = make_float3(b0.x, b0.y, b0.z);
     ptr = __float_as_int(b0.w);

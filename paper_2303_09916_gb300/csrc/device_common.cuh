@@ -68,6 +68,26 @@ __device__ __forceinline__ float3 unit_ball(const ChainStream& s, uint32_t step)
 }
 
 // ------------------------------------------------------------------ small math
+// Hardware approximations (PTX ISA rsqrt.approx, sin.approx, cos.approx) in
+// their .ftz forms: subnormal inputs and results flush to zero.  Every caller
+// passes normal numbers (or zero), where the .ftz and non-.ftz forms return the
+// same value; the .ftz forms skip the subnormal scaling the non-.ftz ones add
+// around each instruction (45 warp instructions per ligand evaluation).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_ftz(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_ftz(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 struct Quat {
   float w, x, y, z;
 };
@@ -91,13 +111,18 @@ __device__ __forceinline__ float3 qrot(const Quat& q, const float3& v) {
 }
 
 __device__ __forceinline__ Quat qnormalize(const Quat& q) {
-  const float inv = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  const float inv = rsqrt_ftz(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
   return Quat{q.w * inv, q.x * inv, q.y * inv, q.z * inv};
 }
 
 // Unit quaternion of a rotation vector w: (cos(|w|/2), sin(|w|/2) w/|w|).  Below
 // |w| = 1/16 the Taylor series of cos(x/2) and sin(x/2)/x is used (truncation
-// error < 1e-12), above it sincosf.
+// error < 1e-12).  Above it, h = |w|/2 = a2 rsqrt(a2) / 2 is reduced to
+// [-pi, pi] by h - 2 pi n, n = rint(h / 2 pi), with 2 pi split in two FP32
+// parts (Cody & Waite) so that the reduction adds no error of its own for the
+// angles a line search tries, and the hardware sin / cos approximations (absolute
+// error a few 1e-7 on [-pi, pi]) take the reduced angle.  Every caller
+// normalises the product it forms with the result.
 __device__ __forceinline__ Quat quat_from_rotvec(float wx, float wy, float wz) {
   const float a2 = wx * wx + wy * wy + wz * wz;
   float c, k;
@@ -105,10 +130,14 @@ __device__ __forceinline__ Quat quat_from_rotvec(float wx, float wy, float wz) {
     c = 1.f + a2 * (-1.f / 8.f + a2 * (1.f / 384.f));
     k = 0.5f + a2 * (-1.f / 48.f + a2 * (1.f / 3840.f));
   } else {
-    const float angle = sqrtf(a2);
-    float s;
-    sincosf(0.5f * angle, &s, &c);
-    k = s / angle;
+    constexpr float kTwoPiHi = 6.28318548f;     // 2 pi rounded to FP32
+    constexpr float kTwoPiLo = -1.74845553e-7f;  // 2 pi - kTwoPiHi
+    const float r = rsqrt_ftz(a2);
+    const float h = 0.5f * (a2 * r);
+    const float n = rintf(h * (1.f / kTwoPiHi));
+    const float hr = fmaf(-n, kTwoPiLo, fmaf(-n, kTwoPiHi, h));
+    c = cos_ftz(hr);
+    k = sin_ftz(hr) * r;
   }
   return Quat{c, wx * k, wy * k, wz * k};
 }
@@ -192,7 +221,7 @@ __device__ __forceinline__ void vina_pair_x2(float2 r2, float2 nrs, uint32_t cls
   // 1e-30 keeps an idle slot's r2 = 0 finite (r2 ir = 0 there); real pairs are
   // Angstroms apart, where it changes nothing
   const float2 rp = __fadd2_rn(r2, splat2(1e-30f));
-  const float2 ir = make_float2(rsqrtf(rp.x), rsqrtf(rp.y));
+  const float2 ir = make_float2(rsqrt_ftz(rp.x), rsqrt_ftz(rp.y));
   float2 d = __ffma2_rn(r2, ir, nrs);
   d.x = r2.x < kCutoff * kCutoff ? d.x : kFarD;
   d.y = r2.y < kCutoff * kCutoff ? d.y : kFarD;

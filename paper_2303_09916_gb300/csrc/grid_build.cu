@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) grid_build_kernel(int n_rec, const f
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < kCutoff * kCutoff)) continue;
         // a vertex on an atom (r = 0) takes no gradient from it: ir is finite there and d* = 0
-        const float ir = rsqrtf(fmaxf(r2, 1e-30f));
+        const float ir = rsqrt_ftz(fmaxf(r2, 1e-30f));
         const float r = r2 * ir;
         const int tj = min(__float_as_int(a.w), 8);
         const float Rj = c_xs_radius[tj];
