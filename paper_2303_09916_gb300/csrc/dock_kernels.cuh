@@ -33,6 +33,17 @@ template <>
 struct ChainOcc<3> {
   static constexpr int kMinBlocks = 7;  // 73 -> 72 registers
 };
+// The minimum CTAs per SM a kernel is compiled for.  Variant 1 of the
+// one-atom-per-lane tiles takes none (0: the launch bound then names only the
+// CTA size): the compiler's own allocation for it is 96 registers without
+// spills (tests/test_kernel_registers_cpu.py checks every variant's count), and
+// that kernel ran the 32-system typical-4k chain stage in 67.4 ms against 69.0
+// for the same budget reached through a bound of 5 CTAs per SM (three runs
+// each): the bound changes how the compiler schedules, not the register count.
+template <int VAR, int APLS>
+__host__ __device__ constexpr int chain_min_blocks() {
+  return (VAR == 1 && APLS == 1) ? 0 : ChainOcc<VAR>::kMinBlocks;
+}
 
 // Chains: a CTA runs one tile of up to W chains of one job; W = blockDim / 32.
 // The job's ligand blob is staged into shared memory once per tile; ligands of
@@ -42,7 +53,7 @@ struct ChainOcc<3> {
 // single-tile kernel keeps its register allocation to itself).
 // persistent != 0: CTAs pull tiles from *tile_counter until none are left.
 template <int FMT, int VAR, int APLS>
-__global__ void __launch_bounds__(32 * kMaxChainWarps, ChainOcc<VAR>::kMinBlocks) dock_chains_kernel(const DevJob* __restrict__ jobs,
+__global__ void __launch_bounds__(32 * kMaxChainWarps, (chain_min_blocks<VAR, APLS>())) dock_chains_kernel(const DevJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles, int n_tiles,
                                                           int* tile_counter, int persistent, int blob_smem,
                                                           ScratchLayout lay) {
