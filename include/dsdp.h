@@ -368,8 +368,10 @@ enum {
  * chains of one job (W = 1, 2 or 4) and stages that job's ligand once.
  * tile_config: 0 = automatic (the choice dsdp_plan_autotune recorded for a plan
  * of the same shape -- map formats, atoms per lane, chain count rounded up to
- * a power of two -- else the 128-register kernel with W = 1, or W = 4 when a
- * ligand has more than 32 atoms); 1 .. 12 = a fixed choice 1 + variant +
+ * a power of two -- else the 96-register kernel for plans of at least
+ * 32 x (SM count) chains and the 128-register kernel for smaller ones, with
+ * W = 1, or W = 4 when a ligand has more than 32 atoms); 1 .. 12 = a fixed
+ * choice 1 + variant +
  * 4 log2(W): register budget (variant 0: 128 registers, 16 warps per SM; 1: 96,
  * 20 warps; 2: 80, 24 warps; 3: 72, 28 warps) and W = 1, 2 or 4.  Budgets 80
  * and 72 are compiled for ligands of up to 32 atoms only (one atom per lane);

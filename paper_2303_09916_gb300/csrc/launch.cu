@@ -313,8 +313,17 @@ extern "C" dsdp_status dsdp_plan_create(dsdp_ctx* ctx, int32_t n_jobs, const dsd
     P->tune_key = tune_key(fmt_mask, apl_max, total_chains);
     int var = 0, pers = (flags & DSDP_PLAN_PERSISTENT) ? 1 : 0;
     if (tile_config == 0) {
-      // without a recorded choice: ligands above 32 atoms stage large blobs, which
-      // tiles of 4 chains share (measured faster on mixed batches); else 1 chain
+      // without a recorded choice: the 96-register kernel for plans of at least
+      // two waves of 16 chains per SM, whose 20 resident warps per SM then issue
+      // more per cycle (32 typical-4k systems 69.0 against 72.4 ms per launch at
+      // 1 chain per CTA; the uneven 10-60-atom batch 307 - 309 against 317 - 319
+      // ms at 4), else the 128-register kernel, whose fewer instructions per
+      // evaluation win when the chains run latency-bound on a part-filled GPU
+      // (one typical-4k system 17.3 against 19.1 ms; 32 plain-2k systems of 64
+      // chains 1,011 against 938 systems/s).  Ligands above 32 atoms stage large
+      // blobs, which tiles of 4 chains share (measured faster on mixed
+      // batches); else 1 chain.
+      var = total_chains >= (size_t)(2 * 16 * P->sms) ? 1 : 0;
       W = apl_max == 2 ? 4 : 1;
       if (tune_lookup(P->tune_key, &var, &pers, &W) && pers) P->flags |= DSDP_PLAN_PERSISTENT;
     } else {
