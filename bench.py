@@ -10,7 +10,7 @@ rescoring and top-k.
 
   value  systems/s with inputs resident on the device (device-pointer API,
          caller-owned memory), timed with CUDA events over exactly K steps;
-         consecutive steps rotate over three streams (--pipeline-depth), each with its own
+         consecutive steps rotate over four streams (--pipeline-depth), each with its own
          maps, outputs and plan, so that a step's grid builds and chains fill
          the SMs the previous step's last wave of chains leaves idle
          (--no-pipeline: one stream).  `serial` is the same K steps on one
@@ -79,7 +79,7 @@ def parse():
                    help="copies x steps sweep of the typical-4k system (the paper's Table 1 grid) and print its JSON line")
     p.add_argument("--no-pipeline", dest="pipeline", action="store_false",
                    help="time the device-resident steps on one stream only (no overlap of consecutive steps)")
-    p.add_argument("--pipeline-depth", type=int, default=3, help="streams (steps in flight) of the pipelined pass")
+    p.add_argument("--pipeline-depth", type=int, default=4, help="streams (steps in flight) of the pipelined pass")
     p.add_argument("--tile-config", type=int, default=-1,
                    help="chain kernel launch configuration: -1 autotune (default); 1..24 fixed, numbered as the "
                         "autotuner reports them: 1 + variant (0: 128 registers, 1: 96, 2: 80, 3: 72) + 4 log2(chains "
