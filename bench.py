@@ -26,8 +26,9 @@ rescoring and top-k.
          the L2-gather microbenchmark, --gather-bench alone)
   the same line also carries the other workloads of the method: one job per
   launch, the uneven batch under a CUDA graph, BF16 / FP16 maps with their
-  error, Barzilai-Borwein, the plain-2k workload, receptor voxel features,
-  the atoms-per-lane boundary, a short Poisson serving run, the search-region
+  error, Barzilai-Borwein, the plain-2k workload, receptor voxel features
+  and grid maps at 4,000 and 8,000 atoms, the atoms-per-lane boundary, a
+  short Poisson serving run, the search-region
   and grid-mode variants, and the autotuner's time for every configuration
   --impl reference   the FP64 CPU oracle on the host cores (whole systems)
 
@@ -777,6 +778,41 @@ def run_voxel_features(dsdp, torch, synth, dev, sptr, reps=20):
     return out
 
 
+def run_grid_build(dsdp, torch, synth, dev, sptr, reps=10):
+    """Receptor grid maps (Eq. 1, Eq. 4 maps; 80^3 x 8 FP32 nodes of (E, grad E)
+    around the pocket) of 4,000- and 8,000-atom receptors: ms per receptor
+    (CUDA events, `reps` launches after one untimed).  Each 8 x 8 x 4 brick of
+    vertices scans every receptor atom for those within the cutoff of the
+    brick, then sums the pair terms of the ones it kept: the scan grows with
+    the receptor, the pair work with the atom density around the box."""
+    out = {}
+    for n in (4000, 8000):
+        rec = synth.receptor(n, 7)
+        box = dsdp.make_box(np.asarray(rec.pocket_center, dtype=np.float64), np.array([BOX] * 3), SPACING)
+        maps = torch.empty(dsdp.dsdp_grid_map_bytes(box, dsdp.DSDP_MAP_F32, dsdp.DSDP_GRID_EQ4), dtype=torch.uint8,
+                           device=dev)
+        xyz = torch.from_numpy(rec.xyz.copy()).to(dev)
+        typ = torch.from_numpy(rec.xs_type.copy()).to(dev)
+
+        def launch():
+            dsdp.dsdp_grid_build_device(n, xyz.data_ptr(), typ.data_ptr(), box, dsdp.DSDP_MAP_F32,
+                                        dsdp.DSDP_GRID_EQ4, maps.data_ptr(), maps.numel(), sptr)
+
+        launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            launch()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        vertices = maps.numel() // (8 * 16)  # 8 map types x (E, grad E) FP32 per vertex
+        out[f"atoms_{n}"] = dict(ms_per_receptor=ms, receptors_per_s=1e3 / ms, vertices=vertices,
+                                 vertices_per_s=vertices * 1e3 / ms)
+    return out
+
+
 def run_configs(args, rank, dev, steps=2):
     """The other workloads of the method, each timed as grid builds + one plan
     launch (chains, FP64 rescoring, top-k) on one stream:
@@ -847,6 +883,7 @@ def run_configs(args, rank, dev, steps=2):
     sec = _timed_plan(dsdp, torch, items, dsdp.DSDP_MAP_F32, sptr, steps)
     evals = sum(int(k["evals"].sum().item()) for _, k in items)
     out["voxel_features"] = run_voxel_features(dsdp, torch, synth, dev, sptr)
+    out["grid_build"] = run_grid_build(dsdp, torch, synth, dev, sptr)
     out["plain_2k"] = dict(one_system_ms=1e3 * one, batched_systems_per_s=len(items) / sec,
                            evals_per_s=evals / sec, systems_per_launch=len(items),
                            workload="2,000-atom receptor, 20 A box (54^3 x 8 FP32 maps), 20-atom ligand / 4 "
