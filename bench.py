@@ -16,9 +16,9 @@ rescoring and top-k.
          (--no-pipeline: one stream).  `serial` is the same K steps on one
          stream; the stage times and rooflines come from that pass
   e2e    systems/s through the host API (dsdp_grid_build / dsdp_dock_submit_many
-         / dsdp_dock_poll) with host arrays, copies included; two steps in
-         flight (the next step's requests go in before this step's results
-         are read back)
+         / dsdp_dock_poll) with host arrays, copies included; three steps
+         in flight (--e2e-window: the next steps' requests go in before this
+         step's results are read back)
   roofline  dock_chains_kernel against the maximum of its three bounds per
          launch: corner-gather bytes at the measured HBM copy peak, FP32 FMA
          work at the FP32 peak, special-function work at the MUFU peak; the
@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--optimizer", default="bfgs", choices=["bfgs", "bb"])
     p.add_argument("--map-dtype", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=6)
+    p.add_argument("--e2e-steps", type=int, default=9)
     p.add_argument("--e2e-batch-chains", type=int, default=-1,
                    help="the host API's largest batch in chains (dsdp_create_params.max_batch_chains): -1 = one "
                         "step's chains (default), 0 = the library's default")
@@ -81,6 +81,8 @@ def parse():
     p.add_argument("--no-pipeline", dest="pipeline", action="store_false",
                    help="time the device-resident steps on one stream only (no overlap of consecutive steps)")
     p.add_argument("--pipeline-depth", type=int, default=4, help="streams (steps in flight) of the pipelined pass")
+    p.add_argument("--e2e-window", type=int, default=3,
+                   help="steps in flight through the host API (the end-to-end pass; 1 with --no-pipeline)")
     p.add_argument("--tile-config", type=int, default=-1,
                    help="chain kernel launch configuration: -1 autotune (default); 1..24 fixed, numbered as the "
                         "autotuner reports them: 1 + variant (0: 128 registers, 1: 96, 2: 80, 3: 72) + 4 log2(chains "
@@ -88,6 +90,8 @@ def parse():
     args = p.parse_args()
     if args.pipeline_depth < 1:
         p.error("--pipeline-depth must be at least 1")
+    if args.e2e_window < 1:
+        p.error("--e2e-window must be at least 1")
     return args
 
 
@@ -1113,7 +1117,8 @@ def run_e2e(args, rank, dev):
     opt = dsdp.DSDP_OPT_BFGS if args.optimizer == "bfgs" else dsdp.DSDP_OPT_BB
     sysl = systems(rank, args.batch)
     blob_bytes = {seed: len(dsdp.dsdp_ligand_pack(lig)) for seed, rec, lig in sysl}  # counted, not timed
-    window = 2 if args.pipeline else 1  # steps in flight: the next step is submitted before this one is read back
+    # steps in flight: the next steps are submitted before this one is read back
+    window = args.e2e_window if args.pipeline else 1
     batch_chains = args.batch * N_CHAINS if args.e2e_batch_chains < 0 else args.e2e_batch_chains
     ctx = dsdp.dsdp_create(dev, n_streams=8, max_inflight_jobs=max(16, window * args.batch),
                            max_batch_chains=batch_chains)
