@@ -26,22 +26,12 @@ def _nvcc():
     return None
 
 
-@pytest.mark.slow
-def test_chain_kernel_register_budgets(tmp_path):
-    nvcc = _nvcc()
-    if nvcc is None:
-        pytest.skip("nvcc not found")
-    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xptxas", "-v",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", os.path.join(CSRC, "dock_fmt0.cu"),
-           "-o", str(tmp_path / "dock_fmt0.o")]
-    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
-    assert r.returncode == 0, r.stderr[-2000:]
-    found = {}
-    entry = None
-    for line in r.stderr.splitlines():
+def _report(stderr, fmt):
+    found, entry = {}, None
+    for line in stderr.splitlines():
         m = re.search(r"Compiling entry function '(\S+)'", line)
         if m:
-            k = re.search(r"dock_chains_kernelILi0ELi(\d)ELi(\d)E", m.group(1))
+            k = re.search(r"dock_chains_kernelILi%dELi(\d)ELi(\d)E" % fmt, m.group(1))
             entry = (int(k.group(1)), int(k.group(2))) if k else None
             continue
         if entry is None:
@@ -52,8 +42,28 @@ def test_chain_kernel_register_budgets(tmp_path):
         m = re.search(r"Used (\d+) registers", line)
         if m:
             found.setdefault(entry, {})["regs"] = int(m.group(1))
-    assert set(found) == set(BUDGET), sorted(found)
-    for key, regs in BUDGET.items():
-        assert found[key]["regs"] == regs, (key, found[key])
-        if key in NO_SPILLS:
-            assert found[key]["spill"] == 0, (key, found[key])
+    return found
+
+
+@pytest.mark.slow
+def test_chain_kernel_register_budgets(tmp_path):
+    """Every map format's translation unit (FP32 / BF16 / FP16 maps, Eq. 4 and
+    Eq. 3), compiled in parallel."""
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not found")
+    procs = {}
+    for fmt in range(6):
+        cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xptxas", "-v",
+               "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", os.path.join(CSRC, f"dock_fmt{fmt}.cu"),
+               "-o", str(tmp_path / f"dock_fmt{fmt}.o")]
+        procs[fmt] = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+    for fmt, proc in procs.items():
+        _, err = proc.communicate(timeout=900)
+        assert proc.returncode == 0, err[-2000:]
+        found = _report(err, fmt)
+        assert set(found) == set(BUDGET), (fmt, sorted(found))
+        for key, regs in BUDGET.items():
+            assert found[key]["regs"] == regs, (fmt, key, found[key])
+            if key in NO_SPILLS:
+                assert found[key]["spill"] == 0, (fmt, key, found[key])
