@@ -161,7 +161,8 @@ def gpu_starts(ctx, grid, cx, nc, seed, optimizer=dsdp.DSDP_OPT_BFGS):
 @pytest.mark.parametrize("shape", list(SHAPES))
 @pytest.mark.parametrize("optimizer,mode", [(dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ4),
                                             (dsdp.DSDP_OPT_BB, dsdp.DSDP_GRID_EQ4),
-                                            (dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ3)])
+                                            (dsdp.DSDP_OPT_BFGS, dsdp.DSDP_GRID_EQ3),
+                                            (dsdp.DSDP_OPT_BB, dsdp.DSDP_GRID_EQ3)])
 def test_local_opt_short_horizon(ctx, shape, optimizer, mode):
     """The first local optimisation of each chain (step 0) after k = 0, 1, 2, 3, 5, 10
     iterations.  The GPU draws the oracle's starts (to FP32 rounding), and k = 0,
@@ -301,6 +302,39 @@ def test_chains_step_for_step(ctx, shape, optimizer):
     finally:
         dsdp.dsdp_grid_free(ctx, grid)
     check_traces(cx, og, res, nc, S, iters, optimizer, 7, f"{shape} optimizer {optimizer}", gstarts)
+
+
+@pytest.mark.parametrize("shape", ["16at", "40at"])
+@pytest.mark.parametrize("dtype", [dsdp.DSDP_MAP_BF16, dsdp.DSDP_MAP_F16])
+def test_chains_step_for_step_reduced_precision_maps(ctx, shape, dtype):
+    """BF16 / FP16 maps (FP32 arithmetic on 16-bit stored nodes): the oracle docks
+    on the values the device stores -- downloaded as FP32, exact in FP64 -- so
+    the reduced-precision chain kernels are held to the same step-for-step
+    criterion as the FP32 ones (mutations bit-exact, every state's energy the
+    oracle's score, every divergence explained).  The stored values are the
+    FP32 maps rounded to the 16-bit format: within half a unit in its last
+    place (8 significand bits for BF16, 11 for FP16)."""
+    cx = complex_for(shape)
+    og = cx.oracle_grid()
+    f32 = np.ascontiguousarray(og.maps, dtype=np.float32)
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, dsdp.make_box(cx.center, cx.size, cx.spacing),
+                                    dtype, dsdp.DSDP_GRID_EQ4, f32)
+    S, nc, iters = 5, 16, 1
+    try:
+        stored = dsdp.dsdp_grid_download(ctx, grid).astype(np.float64)
+        ref = f32.astype(np.float64)
+        half_ulp = 2.0 ** -8 if dtype == dsdp.DSDP_MAP_BF16 else 2.0 ** -11
+        tiny = 2.0 ** -134 if dtype == dsdp.DSDP_MAP_BF16 else 2.0 ** -25  # half the subnormal spacing
+        assert np.all(np.abs(stored - ref) <= half_ulp * np.abs(ref) + tiny)
+        assert np.any(stored != ref)  # the maps were rounded
+        og_r = oracle.Grid(stored.reshape(og.maps.shape), og.n, og.origin, og.h)
+        res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=7,
+                       optimizer=dsdp.DSDP_OPT_BFGS, trace=1, top_k=4)
+        gstarts = gpu_starts(ctx, grid, cx, nc, 7)
+    finally:
+        dsdp.dsdp_grid_free(ctx, grid)
+    name = "bf16" if dtype == dsdp.DSDP_MAP_BF16 else "f16"
+    check_traces(cx, og_r, res, nc, S, iters, dsdp.DSDP_OPT_BFGS, 7, f"{shape} {name} maps", gstarts)
 
 
 @pytest.mark.parametrize("shape,nc,S", [("16at", 24, 40), ("40at", 12, 20), ("60at", 12, 20)])
