@@ -337,8 +337,21 @@ def test_chains_step_for_step_reduced_precision_maps(ctx, shape, dtype):
     check_traces(cx, og_r, res, nc, S, iters, dsdp.DSDP_OPT_BFGS, 7, f"{shape} {name} maps", gstarts)
 
 
-@pytest.mark.parametrize("shape,nc,S", [("16at", 24, 40), ("40at", 12, 20), ("60at", 12, 20)])
-def test_replay_one_step_transitions(ctx, shape, nc, S):
+def _stored_grid(ctx, cx, og, dtype):
+    """A device grid of the oracle's maps in `dtype`, and the oracle grid of the
+    values it stores (FP32 maps: the oracle's own)."""
+    if dtype == dsdp.DSDP_MAP_F32:
+        return _grid(ctx, cx), og
+    grid = dsdp.dsdp_grid_from_maps(ctx, cx.rec.xyz, cx.rec.xs_type, dsdp.make_box(cx.center, cx.size, cx.spacing),
+                                    dtype, dsdp.DSDP_GRID_EQ4, np.ascontiguousarray(og.maps, dtype=np.float32))
+    stored = dsdp.dsdp_grid_download(ctx, grid).astype(np.float64)
+    return grid, oracle.Grid(stored.reshape(og.maps.shape), og.n, og.origin, og.h)
+
+
+@pytest.mark.parametrize("shape,nc,S,dtype", [("16at", 24, 40, dsdp.DSDP_MAP_F32), ("40at", 12, 20, dsdp.DSDP_MAP_F32),
+                                              ("60at", 12, 20, dsdp.DSDP_MAP_F32),
+                                              ("16at", 24, 20, dsdp.DSDP_MAP_BF16)])
+def test_replay_one_step_transitions(ctx, shape, nc, S, dtype):
     """Long chains (100 BFGS iterations per local optimisation): re-seed the oracle
     with the GPU state at each step start and replay one step.  The mutation must
     match exactly, the Metropolis decision must follow from the GPU's own
@@ -349,12 +362,12 @@ def test_replay_one_step_transitions(ctx, shape, nc, S):
     replay, or the GPU within twice the oracle's own response to five
     FP32-sized probes of that state) and at most 2 % of all steps may stay
     unexplained: after 100 BFGS iterations the response to a perturbation
-    depends on its direction, and five probes only sample it."""
+    depends on its direction, and five probes only sample it.  With BF16 maps
+    the oracle replays on the values the device stores."""
     import math
 
     cx = complex_for(shape)
-    og = cx.oracle_grid()
-    grid = _grid(ctx, cx)
+    grid, og = _stored_grid(ctx, cx, cx.oracle_grid(), dtype)
     iters = 100
     try:
         res = _run_job(ctx, grid, cx.lig, cx.T, n_chains=nc, n_mc_steps=S, n_opt_iters=iters, seed=11, trace=1,
@@ -402,7 +415,8 @@ def test_replay_one_step_transitions(ctx, shape, nc, S):
             kinds[kind] += 1
             if not ok:
                 unexplained.append((c, s, why))
-    print(f"{shape} replay: GPU vs oracle candidate energies agree on {n_match}/{n_steps} steps; "
+    print(f"{shape} {'bf16 ' if dtype == dsdp.DSDP_MAP_BF16 else ''}replay: GPU vs oracle candidate energies agree "
+          f"on {n_match}/{n_steps} steps; "
           f"oracle vs oracle nudged by one FP32 ulp: {n_base}/{n_steps}; the other steps: {kinds}")
     for u_ in unexplained:
         print("  unexplained (chain, step, why):", u_)
