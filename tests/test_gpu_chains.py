@@ -424,9 +424,12 @@ def test_replay_one_step_transitions(ctx, shape, nc, S, dtype):
     assert kinds["unexplained"] <= 0.02 * n_steps, kinds
 
 
-def test_mixed_tile_batch_against_the_oracle(ctx):
+@pytest.mark.parametrize("dtype", [dsdp.DSDP_MAP_F32, dsdp.DSDP_MAP_BF16])
+def test_mixed_tile_batch_against_the_oracle(ctx, dtype):
     """Ligands of 18, 33 and 60 atoms submitted together run in one batch: the
-    mixed-tile chain kernel (one- and two-atoms-per-lane chains in one launch).
+    mixed-tile chain kernel (one- and two-atoms-per-lane chains in one launch),
+    on FP32 maps and on BF16 maps (the serving workload's format; the oracle
+    then docks on the values the device stores).
     Short chains are checked step for step against the oracle (module
     docstring); longer ones on their results: every chain's best energy is the
     oracle's score of its best pose, and the top-k equals the oracle's FP64
@@ -434,7 +437,8 @@ def test_mixed_tile_batch_against_the_oracle(ctx):
     identical)."""
     shapes = [(1500, 16.0, 18, 5, 12), (1500, 16.0, 33, 9, 13), (2500, 20.0, 60, 15, 8)]
     cxs = [Complex(*s[:4], seed=s[4]) for s in shapes]
-    grids = [_grid(ctx, cx) for cx in cxs]
+    stored = [_stored_grid(ctx, cx, cx.oracle_grid(), dtype) for cx in cxs]
+    grids, ogs = [g for g, _ in stored], [o for _, o in stored]
     try:
         for S, iters, trace in ((5, 1, 1), (12, 30, 0)):
             params = [dsdp.make_params(n_chains=24, n_mc_steps=S, n_opt_iters=iters, seed=3 + i, trace=trace,
@@ -445,8 +449,9 @@ def test_mixed_tile_batch_against_the_oracle(ctx):
                    for j, cx, p in zip(ids, cxs, params)]
             assert dsdp.dsdp_get_stats(ctx)["batches"] - b0 == 1  # one launch holds all three
             for i, (cx, r) in enumerate(zip(cxs, res)):
-                og = cx.oracle_grid()
-                label = f"mixed batch, {cx.lig.n_atoms} atoms, {S} x {iters}"
+                og = ogs[i]
+                label = (f"mixed batch{' (bf16 maps)' if dtype == dsdp.DSDP_MAP_BF16 else ''}, {cx.lig.n_atoms} atoms, "
+                         f"{S} x {iters}")
                 if trace:
                     gstarts = gpu_starts(ctx, grids[i], cx, 24, 3 + i)
                     check_traces(cx, og, r, 24, S, iters, dsdp.DSDP_OPT_BFGS, 3 + i, label, gstarts)
